@@ -1,0 +1,184 @@
+/*
+ * spgemm.h - C ABI of the GB300 hash SpGEMM library (libspgemm_gb300.so).
+ *
+ * Computes C = A*B for sparse A (m x n) and B (n x k) in CSR form with
+ * Gustavson's row-wise algorithm (paper Sec. 2, Fig. "RowWise_SpGEMM"):
+ * row i of C accumulates a_ik * b_k* over the stored a_ik of row i of A,
+ * in a hash table keyed by column index (Sec. 4.2.1).  The work runs in two
+ * phases (Sec. 2, "two-phase method"; Sec. 4.2.1, Fig. "Hash_SpGEMM"):
+ * a symbolic phase counts the entries of every output row so that C can be
+ * allocated exactly, then a numeric phase computes the values.
+ *
+ * Call sequence:
+ *     spgemm_plan_create   -> per-row flop count and row binning (Sec. 4.1)
+ *     spgemm_symbolic      -> nnz per output row, C row_ptr, nnz(C) to host
+ *     (caller allocates C col_idx and vals for nnz(C) entries)
+ *     spgemm_numeric       -> C col_idx and vals, rows sorted if requested
+ *     spgemm_plan_destroy
+ * or the one-shot spgemm(), which takes a caller allocator.
+ *
+ * Memory and ownership:
+ *   - Every matrix pointer is a DEVICE pointer on the current CUDA device.
+ *   - The caller owns A, B and all C buffers.  A plan borrows A and B: they
+ *     must stay valid and unmodified until spgemm_numeric has completed on
+ *     the plan's stream.
+ *   - The plan owns its workspace (row flop, bins, row counts, heavy-row
+ *     bitmaps and tables), allocated stream-ordered from the device's
+ *     memory pool and released by spgemm_plan_destroy.
+ *   - All device work is ordered on the stream given to spgemm_plan_create
+ *     (a cudaStream_t passed as void*, NULL = legacy default stream).
+ *   - spgemm_plan_create and spgemm_symbolic each synchronise that stream
+ *     once, to read a few counters (bin sizes, nnz(C)) back to the host.
+ *
+ * Layout: CSR, 0-based, int32 row_ptr (nrows+1 entries) and col_idx.
+ * Column indices inside an input row may be in any order (Table
+ * "Summary of SpGEMM codes": Hash accepts any input order) but must be
+ * distinct.  Values are int64, float or double (spgemm_dtype); A, B and C
+ * share one value type.  Output rows are column-sorted when flags has
+ * SPGEMM_SORTED, otherwise their order is unspecified (Sec. 4.2.1: the
+ * results are sorted "if necessary").
+ *
+ * Arithmetic: plus-times.  int64 wraps modulo 2^64.  Floating-point sums
+ * are taken in an unspecified order (atomic accumulation), so results may
+ * differ in the last bits between runs; every structural entry is stored,
+ * including entries whose value sums to zero.
+ *
+ * Errors: every function returns an int status (spgemm_status); nothing
+ * aborts or throws across this boundary.  A device-side problem (a hash
+ * probe exceeding its table) sets a status read back at the next host
+ * synchronisation point of the plan.
+ */
+#ifndef SPGEMM_GB300_H
+#define SPGEMM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPGEMM_OK = 0,
+    SPGEMM_ERR_INVALID_ARGUMENT = -1, /* null pointer, dims mismatch, bad dtype/flags, negative size */
+    SPGEMM_ERR_INVALID_CSR = -2,      /* row_ptr not monotone or an index out of range (validated calls) */
+    SPGEMM_ERR_OUT_OF_MEMORY = -3,    /* workspace allocation failed */
+    SPGEMM_ERR_INDEX_OVERFLOW = -4,   /* nnz(C) does not fit int32 indexing */
+    SPGEMM_ERR_BAD_STATE = -5,        /* calls out of order (numeric before symbolic, ...) */
+    SPGEMM_ERR_DEVICE = -6,           /* CUDA error, or a device-side check failed */
+    SPGEMM_ERR_TIMEOUT = -7           /* a bounded device-side wait gave up */
+} spgemm_status;
+
+typedef enum { SPGEMM_I64 = 0, SPGEMM_F32 = 1, SPGEMM_F64 = 2 } spgemm_dtype;
+
+#define SPGEMM_UNSORTED 0u /* output columns in any order within a row */
+#define SPGEMM_SORTED 1u   /* output columns ascending within each row */
+#define SPGEMM_VALIDATE 2u /* check input CSR structure on the device first */
+
+/* A CSR operand (device pointers). */
+typedef struct {
+    int64_t nrows;
+    int64_t ncols;
+    int64_t nnz;
+    const int32_t *row_ptr; /* nrows+1 entries, row_ptr[0] == 0, row_ptr[nrows] == nnz */
+    const int32_t *col_idx; /* nnz entries in [0, ncols) */
+    const void *vals;       /* nnz entries of the plan's value type */
+} spgemm_csr;
+
+/* Statistics of a plan (host struct, filled by spgemm_plan_stats). */
+#define SPGEMM_MAX_BINS 24
+typedef struct {
+    int64_t m, n, k;           /* A is m x n, B is n x k */
+    int64_t total_flop;        /* sum over rows of flop[i] (Sec. 4.1) */
+    int64_t max_row_flop;      /* max over rows of flop[i] */
+    int64_t nnz_c;             /* nnz(C), valid after spgemm_symbolic */
+    int32_t n_sym_bins;        /* number of symbolic bins */
+    int32_t n_num_bins;        /* number of numeric bins */
+    int64_t sym_bin_rows[SPGEMM_MAX_BINS]; /* rows per symbolic bin */
+    int64_t num_bin_rows[SPGEMM_MAX_BINS]; /* rows (or row windows) per numeric bin */
+    int32_t sym_bin_table[SPGEMM_MAX_BINS]; /* table slots per bin (0 = bitmap or global table) */
+    int32_t num_bin_table[SPGEMM_MAX_BINS];
+    int64_t workspace_bytes;   /* device workspace currently held by the plan */
+    int32_t kernel_launches;   /* kernels launched by this plan so far */
+    int32_t state;             /* 0 planned, 1 symbolic done, 2 numeric done */
+} spgemm_stats;
+
+typedef struct spgemm_plan_s *spgemm_plan_t;
+
+/*
+ * Create a plan for C = A*B with value type `dtype` and `flags`
+ * (SPGEMM_SORTED / SPGEMM_UNSORTED, optionally | SPGEMM_VALIDATE).
+ * Runs the per-row flop pass, flop[i] = sum over stored a_ik of nnz(b_k*)
+ * (Sec. 4.1, Fig. "RowsToThreads", step 1), and bins the rows by the hash
+ * table size they need (GPU form of the load balancing of Sec. 4.1 and of
+ * the density binning of GPU codes, Sec. 2).  Requires A->ncols ==
+ * B->nrows.  Synchronises `stream` once.  On error *out is NULL.
+ */
+int spgemm_plan_create(spgemm_plan_t *out, const spgemm_csr *A, const spgemm_csr *B,
+                       int dtype, unsigned flags, void *stream);
+
+/*
+ * Symbolic phase (Sec. 4.2.1: "it is enough to insert keys to the hash
+ * table"): counts the distinct columns of every output row, writes the
+ * exclusive prefix sum to c_row_ptr (device, m+1 int32, caller-owned) and
+ * returns nnz(C) in *nnz_c (host).  Synchronises the stream once.  Returns
+ * SPGEMM_ERR_INDEX_OVERFLOW if nnz(C) > 2^31-1.
+ */
+int spgemm_symbolic(spgemm_plan_t plan, int32_t *c_row_ptr, int64_t *nnz_c);
+
+/*
+ * Numeric phase (Sec. 4.2.1; Fig. "Hash_SpGEMM", last step): accumulates
+ * c_ij = sum_k a_ik*b_kj in per-row tables and stores every row at
+ * c_row_ptr[i] .. c_row_ptr[i+1]-1 of c_col_idx (device, nnz(C) int32) and
+ * c_vals (device, nnz(C) values), column-sorted when the plan has
+ * SPGEMM_SORTED.  c_row_ptr must be the array filled by spgemm_symbolic.
+ * Asynchronous: results are ready when the plan's stream reaches this point.
+ */
+int spgemm_numeric(spgemm_plan_t plan, const int32_t *c_row_ptr, int32_t *c_col_idx, void *c_vals);
+
+/* Release the plan and its workspace (stream-ordered).  NULL is accepted. */
+int spgemm_plan_destroy(spgemm_plan_t plan);
+
+/* Device workspace held by the plan, in bytes. */
+int spgemm_plan_workspace_bytes(spgemm_plan_t plan, size_t *bytes);
+
+/* Copy the plan's statistics into *out (host). */
+int spgemm_plan_stats(spgemm_plan_t plan, spgemm_stats *out);
+
+/*
+ * Inspection of the intermediate results, for tests: copy flop[m] (int64),
+ * the symbolic row permutation perm[m] (int32; rows grouped by bin, bin b
+ * occupying sym_bin_offsets[b]..sym_bin_offsets[b+1]-1) and nnz_row[m]
+ * (int32, after spgemm_symbolic) into caller DEVICE buffers.
+ * sym_bin_offsets is a HOST array of n_sym_bins+1 int64.
+ */
+int spgemm_plan_row_flop(spgemm_plan_t plan, int64_t *flop_out);
+int spgemm_plan_sym_bins(spgemm_plan_t plan, int32_t *perm_out, int64_t *sym_bin_offsets);
+int spgemm_plan_row_nnz(spgemm_plan_t plan, int32_t *nnz_out);
+
+/* Allocator callback for spgemm(): returns a device pointer of `bytes`
+ * bytes (16-byte aligned) or NULL.  The caller owns what it returns. */
+typedef void *(*spgemm_alloc_fn)(size_t bytes, void *ctx);
+
+/*
+ * One-shot C = A*B: plan, symbolic, allocate C through `alloc`
+ * (row_ptr: (m+1)*4 bytes, col_idx: nnz*4 bytes, vals: nnz*sizeof(value)),
+ * numeric, destroy.  The three C pointers are returned through c_row_ptr,
+ * c_col_idx and c_vals.  Results are ready when `stream` reaches the end
+ * of the call's work.
+ */
+int spgemm(const spgemm_csr *A, const spgemm_csr *B, int dtype, unsigned flags, void *stream,
+           spgemm_alloc_fn alloc, void *alloc_ctx,
+           int32_t **c_row_ptr, int32_t **c_col_idx, void **c_vals, int64_t *nnz_c);
+
+/* Human-readable name of a status code (static string). */
+const char *spgemm_status_string(int status);
+
+/* Last CUDA error text recorded by the library on this thread ("" if none). */
+const char *spgemm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPGEMM_GB300_H */
