@@ -1,0 +1,435 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the GB300 hash SpGEMM (C = A*A on synthetic R-MAT).
+
+One step = one whole product through the C ABI: plan (row flop pass and
+binning), symbolic phase (counts, row_ptr scan, nnz(C) to the host), the
+allocation of C, and the numeric phase (accumulation and, in sorted mode,
+the per-row sort).  Inputs are resident in HBM when a step starts.  Inputs
+(about 23 MB) are smaller than L2, so a 256 MiB buffer is written between
+steps to flush L2; each step is timed alone with CUDA events on the
+launching stream, the flush outside the events.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle on
+the same workload instead (rank 0 only; other ranks exit at once).
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                        [--unsorted] [--impl reference]
+For N > 1 launch under torch.distributed.run: each rank runs an
+independent replica on its own GPU (weak scaling); timing takes the maximum
+over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SpGEMM GFLOP/s (2*flop per second)"
+# FP64 peak derived from unit counts and clocks: 152 SMs x 2 FP64 FMA per
+# clock per SM x 2070 MHz x 2 FLOP per FMA (= the nominal 1.25 TFLOP/s).
+FP64_PEAK_TFLOPS = 152 * 2 * 2.070e9 * 2 / 1e12
+HBM_FALLBACK_GBS = 6800.0
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def parse_args():
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--workload", default="rmat16_ef16_f64")
+    p.add_argument("--unsorted", action="store_true", help="time unsorted output as the headline")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-variant", action="store_true", help="skip timing the other sort mode")
+    return p.parse_args()
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def workload_accounting(A, B, nnz_c: int, vsize: int) -> dict:
+    """Algorithmic bytes of the whole path: A once, every touched row of B once,
+    C written once (row_ptr + col_idx + values)."""
+    flop = int(np.diff(B.row_ptr.astype(np.int64))[A.col_idx].sum())
+    touched = np.unique(A.col_idx)
+    b_rows = np.diff(B.row_ptr.astype(np.int64))[touched]
+    bytes_a = (A.nrows + 1) * 4 + A.nnz * (4 + vsize)
+    bytes_b = int(len(touched) * 8 + b_rows.sum() * (4 + vsize))
+    bytes_c = (A.nrows + 1) * 4 + nnz_c * (4 + vsize)
+    return dict(flop=flop, bytes_alg=bytes_a + bytes_b + bytes_c, bytes_a=bytes_a, bytes_b=bytes_b, bytes_c=bytes_c)
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms during the timed region."""
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={CLOCK_FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.dev), "-lms", "200"], stdout=self.out,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.out.close()
+
+    def summary(self) -> dict | None:
+        if self.proc is None or not self.path:
+            return None
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def source_digest() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1804_01698_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = rec.get(workload, {}).get(kernel)
+    if not e or e.get("source_digest") != source_digest():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def kernel_units(name: str, stats: dict) -> tuple[int, str]:
+    """Useful multiply-adds (products) one launch of `name` performs, from the
+    plan's per-bin flop totals."""
+    kind, _, size = name.rpartition("_")
+    if name == "num_bitmap":
+        return stats["num_bin_flop"][9], "numeric"
+    if name == "num_global":
+        return stats["num_bin_flop"][10], "numeric"
+    if name == "sym_bitmap":
+        return stats["sym_bin_flop"][10], "symbolic"
+    if name == "sym_global":
+        return stats["sym_bin_flop"][11], "symbolic"
+    if size.isdigit():
+        table = int(size)
+        if kind.startswith("num_"):
+            for b, t in enumerate(stats["num_bin_table"]):
+                if t == table:
+                    return stats["num_bin_flop"][b], "numeric"
+        if kind.startswith("sym_"):
+            for b, t in enumerate(stats["sym_bin_table"]):
+                if t == table:
+                    return stats["sym_bin_flop"][b], "symbolic"
+    return 0, "other"
+
+
+# ---------------------------------------------------------------------------- reference arm
+
+def run_reference(args) -> int:
+    import oracle
+    from paper_1804_01698_gb300 import inputs
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    A, B, sorted_default = inputs.workload(args.workload)
+    cores = len(os.sched_getaffinity(0))
+    flop = int(oracle.row_flop(A, B).sum())
+    for _ in range(args.warmup):
+        oracle.spgemm(A, B, nthreads=cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.spgemm(A, B, nthreads=cores)
+        times.append(time.perf_counter() - t0)
+    mean = sum(times) / len(times)
+    value = 2 * flop / mean / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if A.vals.dtype == np.float64 else "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "m": A.nrows, "n": A.ncols, "k": B.ncols, "nnz_a": A.nnz,
+                   "nnz_b": B.nnz, "flop": flop, "sorted": True},
+        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": "the whole product per step (dense-SPA Gustavson, rows split by RowsToThreads)"},
+        "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------- GPU arm
+
+def main() -> int:
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus:
+        print(json.dumps({"error": f"--gpus {args.gpus} needs WORLD_SIZE={args.gpus} (torch.distributed.run)"}))
+        return 2
+    if not torch.cuda.is_available():
+        print(json.dumps({"error": "no CUDA device"}))
+        return 2
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1804_01698_gb300 import binding as sg
+    from paper_1804_01698_gb300 import inputs
+
+    A, B, sorted_default = inputs.workload(args.workload)
+    sorted_output = sorted_default and not args.unsorted
+    vdtype = {np.dtype(np.float64): torch.float64, np.dtype(np.float32): torch.float32,
+              np.dtype(np.int64): torch.int64}[A.vals.dtype]
+    vsize = A.vals.dtype.itemsize
+    same = A is B
+    dev = torch.device("cuda", local_rank)
+    dA = sg.to_device(A, dev)
+    dB = dA if same else sg.to_device(B, dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def step(sorted_flag: bool, timing: bool):
+        plan = sg.Plan(dA, dB, sorted_flag, stream=stream, timing=timing)
+        nnz = plan.symbolic()
+        C = plan.numeric()
+        return plan, nnz, C
+
+    def timed_steps(sorted_flag: bool, k: int, w: int):
+        for _ in range(w):
+            plan, nnz, C = step(sorted_flag, False)
+            plan.destroy()
+            del C
+        barrier()
+        times, kt, launches, stats = [], {}, 0, None
+        t_wall0 = time.perf_counter()
+        for it in range(k):
+            flush.fill_(it & 0xFF)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan, nnz, C = step(sorted_flag, True)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            for name, (ms, n) in plan.kernel_times().items():
+                a, b = kt.get(name, (0.0, 0))
+                kt[name] = (a + ms, b + n)
+            stats = plan.stats()
+            if stats["status"] != 0:
+                raise RuntimeError(f"device error status {stats['status']}")
+            launches += stats["kernel_launches"]
+            plan.destroy()
+            del C
+        barrier()
+        wall = time.perf_counter() - t_wall0
+        return times, kt, launches, stats, nnz, wall
+
+    with ClockSampler(local_rank) as clocks:
+        times, kt, launches, stats, nnz_c, wall = timed_steps(sorted_output, args.steps, args.warmup)
+    clock_summary = clocks.summary()
+
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    acc = workload_accounting(A, B, nnz_c, vsize)
+    flop = acc["flop"]
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps * 2 * flop / (total_ms * 1e-3) / 1e9
+
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs")
+    hbm_src = "measured" if hbm_peak else "fallback"
+    hbm_peak = hbm_peak or HBM_FALLBACK_GBS
+
+    # dominant kernel and its roofline
+    dom = max(kt.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms_total, dom_launches) = dom
+    dom_ms = dom_ms_total / max(dom_launches, 1)
+    units, phase = kernel_units(dom_name, stats)
+    units_per_launch = units / max(dom_launches / args.steps, 1)
+    if phase == "numeric" and vdtype == torch.float64:
+        achieved = 2 * units_per_launch / (dom_ms * 1e-3) / 1e12
+        roofline = {"kernel": dom_name, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                    "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz x 2",
+                    "work_per_launch": f"{units_per_launch:.0f} multiply-adds (FP64 FMA)"}
+    else:
+        # bytes that kernel must move: the B entries it reads once per product
+        # are L2 hits; its HBM share is bounded by its output and input rows.
+        achieved_b = (units_per_launch * (4 + vsize)) / (dom_ms * 1e-3) / 1e9
+        roofline = {"kernel": dom_name, "bound": "hbm", "achieved": achieved_b, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved_b / hbm_peak, "peak_source": hbm_src,
+                    "work_per_launch": f"{units_per_launch:.0f} products x {4 + vsize} B"}
+    roofline["launch_ms"] = dom_ms
+    roofline["traffic"] = committed_traffic(dom_name, args.workload)
+    path_gbs = acc["bytes_alg"] / (ms_per_step * 1e-3) / 1e9
+    hbm_roofline = {"bytes_alg": acc["bytes_alg"], "achieved_gbs": path_gbs, "peak_gbs": hbm_peak,
+                    "frac": path_gbs / hbm_peak, "frac_of_8tbs": path_gbs / 8000.0, "peak_source": hbm_src}
+
+    phases = {name: round(ms / args.steps, 4) for name, (ms, n) in sorted(kt.items(), key=lambda kv: -kv[1][0])}
+
+    variant = None
+    if not args.no_variant:
+        vt, _, _, _, _, _ = timed_steps(not sorted_output, args.steps, 1)
+        vms = sum(vt) / len(vt)
+        variant = {"sorted": not sorted_output, "ms_per_step": vms, "value": 2 * flop / (vms * 1e-3) / 1e9}
+
+    # end to end through the public one-shot API, host buffers in and out
+    e2e = None
+    if not args.no_e2e:
+        def pin(x):
+            return torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+        hA = [pin(A.row_ptr), pin(A.col_idx), pin(A.vals)]
+        hB = hA if same else [pin(B.row_ptr), pin(B.col_idx), pin(B.vals)]
+        h_out = [torch.empty(A.nrows + 1, dtype=torch.int32).pin_memory(),
+                 torch.empty(nnz_c, dtype=torch.int32).pin_memory(),
+                 torch.empty(nnz_c, dtype=vdtype).pin_memory()]
+        h2d = sum(t.numel() * t.element_size() for t in hA) + (0 if same else sum(
+            t.numel() * t.element_size() for t in hB))
+        d2h = sum(t.numel() * t.element_size() for t in h_out)
+
+        def e2e_step():
+            dev_a = [t.to(dev, non_blocking=True) for t in hA]
+            dev_b = dev_a if same else [t.to(dev, non_blocking=True) for t in hB]
+            a = sg.DeviceCSR(A.nrows, A.ncols, *dev_a)
+            b = sg.DeviceCSR(B.nrows, B.ncols, *dev_b)
+            C = sg.spgemm(a, b, sorted_output, stream=stream)
+            h_out[0].copy_(C.row_ptr, non_blocking=True)
+            h_out[1].copy_(C.col_idx, non_blocking=True)
+            h_out[2].copy_(C.vals, non_blocking=True)
+
+        for _ in range(args.warmup):
+            e2e_step()
+        barrier()
+        et = []
+        for it in range(args.steps):
+            flush.fill_(it & 0xFF)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            e2e_step()
+            e1.record(stream)
+            e1.synchronize()
+            et.append(e0.elapsed_time(e1))
+        barrier()
+        ems = sum(et)
+        if world > 1:
+            t = torch.tensor([ems], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": world * args.steps * 2 * flop / (ems * 1e-3) / 1e9, "unit": "GFLOP/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ems / args.steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        cores = len(os.sched_getaffinity(0))
+        t0 = time.perf_counter()
+        oracle.spgemm(A, B, nthreads=cores)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 2 * flop / dt / 1e9, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+               "sample": "the whole product once (dense-SPA Gustavson, rows split by RowsToThreads)",
+               "seconds": dt}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {torch.float64: "f64", torch.float32: "f32", torch.int64: "int64"}[vdtype],
+            "data": "synthetic",
+            "config": {"workload": args.workload, "desc": inputs.WORKLOADS[args.workload]["desc"], "m": A.nrows,
+                       "n": A.ncols, "k": B.ncols, "nnz_a": A.nnz, "nnz_b": B.nnz, "flop": flop, "nnz_c": nnz_c,
+                       "sorted": sorted_output, "l2": "flushed between steps (256 MiB write, outside the events)",
+                       "replicas": world},
+            "roofline": roofline,
+            "hbm_roofline_path": hbm_roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches * world,
+            "clocks": clock_summary,
+            "phases_ms": phases,
+            "variant": variant,
+            "wall_s_timed_region": wall,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -44,15 +44,25 @@
  * including entries whose value sums to zero.
  *
  * Errors: every function returns an int status (spgemm_status); nothing
- * aborts or throws across this boundary.  A device-side problem (a hash
- * probe exceeding its table) sets a status read back at the next host
- * synchronisation point of the plan.
+ * aborts or throws across this boundary.  The kernels check, as they read
+ * them, that A's row_ptr is monotone within [0, nnz], that every column
+ * index lies inside its matrix and that every touched row of B has a
+ * monotone row_ptr; a violation skips the access and sets a device error
+ * word.  That word (and any hash probe that ran past its table) is read
+ * back at the plan's next host synchronisation: spgemm_plan_create,
+ * spgemm_symbolic, or spgemm_plan_stats after spgemm_numeric.
  */
 #ifndef SPGEMM_GB300_H
 #define SPGEMM_GB300_H
 
 #include <stddef.h>
 #include <stdint.h>
+
+#if defined(__GNUC__)
+#define SPGEMM_API __attribute__((visibility("default")))
+#else
+#define SPGEMM_API
+#endif
 
 #ifdef __cplusplus
 extern "C" {
@@ -73,7 +83,8 @@ typedef enum { SPGEMM_I64 = 0, SPGEMM_F32 = 1, SPGEMM_F64 = 2 } spgemm_dtype;
 
 #define SPGEMM_UNSORTED 0u /* output columns in any order within a row */
 #define SPGEMM_SORTED 1u   /* output columns ascending within each row */
-#define SPGEMM_VALIDATE 2u /* check input CSR structure on the device first */
+#define SPGEMM_VALIDATE 2u /* accepted; the device checks listed under Errors always run */
+#define SPGEMM_TIMING 4u   /* record CUDA events around every kernel (spgemm_plan_kernel_times) */
 
 /* A CSR operand (device pointers). */
 typedef struct {
@@ -101,6 +112,8 @@ typedef struct {
     int64_t workspace_bytes;   /* device workspace currently held by the plan */
     int32_t kernel_launches;   /* kernels launched by this plan so far */
     int32_t state;             /* 0 planned, 1 symbolic done, 2 numeric done */
+    int64_t sym_bin_flop[SPGEMM_MAX_BINS]; /* sum of flop[i] over the rows of each symbolic bin */
+    int64_t num_bin_flop[SPGEMM_MAX_BINS]; /* same for numeric bins (bitmap bin: its rows, once) */
 } spgemm_stats;
 
 typedef struct spgemm_plan_s *spgemm_plan_t;
@@ -114,7 +127,7 @@ typedef struct spgemm_plan_s *spgemm_plan_t;
  * the density binning of GPU codes, Sec. 2).  Requires A->ncols ==
  * B->nrows.  Synchronises `stream` once.  On error *out is NULL.
  */
-int spgemm_plan_create(spgemm_plan_t *out, const spgemm_csr *A, const spgemm_csr *B,
+SPGEMM_API int spgemm_plan_create(spgemm_plan_t *out, const spgemm_csr *A, const spgemm_csr *B,
                        int dtype, unsigned flags, void *stream);
 
 /*
@@ -124,7 +137,7 @@ int spgemm_plan_create(spgemm_plan_t *out, const spgemm_csr *A, const spgemm_csr
  * returns nnz(C) in *nnz_c (host).  Synchronises the stream once.  Returns
  * SPGEMM_ERR_INDEX_OVERFLOW if nnz(C) > 2^31-1.
  */
-int spgemm_symbolic(spgemm_plan_t plan, int32_t *c_row_ptr, int64_t *nnz_c);
+SPGEMM_API int spgemm_symbolic(spgemm_plan_t plan, int32_t *c_row_ptr, int64_t *nnz_c);
 
 /*
  * Numeric phase (Sec. 4.2.1; Fig. "Hash_SpGEMM", last step): accumulates
@@ -134,16 +147,28 @@ int spgemm_symbolic(spgemm_plan_t plan, int32_t *c_row_ptr, int64_t *nnz_c);
  * SPGEMM_SORTED.  c_row_ptr must be the array filled by spgemm_symbolic.
  * Asynchronous: results are ready when the plan's stream reaches this point.
  */
-int spgemm_numeric(spgemm_plan_t plan, const int32_t *c_row_ptr, int32_t *c_col_idx, void *c_vals);
+SPGEMM_API int spgemm_numeric(spgemm_plan_t plan, const int32_t *c_row_ptr, int32_t *c_col_idx, void *c_vals);
 
 /* Release the plan and its workspace (stream-ordered).  NULL is accepted. */
-int spgemm_plan_destroy(spgemm_plan_t plan);
+SPGEMM_API int spgemm_plan_destroy(spgemm_plan_t plan);
 
 /* Device workspace held by the plan, in bytes. */
-int spgemm_plan_workspace_bytes(spgemm_plan_t plan, size_t *bytes);
+SPGEMM_API int spgemm_plan_workspace_bytes(spgemm_plan_t plan, size_t *bytes);
 
-/* Copy the plan's statistics into *out (host). */
-int spgemm_plan_stats(spgemm_plan_t plan, spgemm_stats *out);
+/* Copy the plan's statistics into *out (host).  Synchronises the plan's
+ * stream and returns the device error status of all work issued so far
+ * (SPGEMM_OK, or the error the device checks recorded). */
+SPGEMM_API int spgemm_plan_stats(spgemm_plan_t plan, spgemm_stats *out);
+
+/* Time of every kernel the plan launched, summed by kernel name (plans
+ * created with SPGEMM_TIMING only).  Synchronises the stream.  Writes at
+ * most max_entries records and the number of distinct names to *n_out. */
+typedef struct {
+    char name[40];
+    float ms;          /* summed CUDA-event time on the plan's stream */
+    int32_t launches;  /* launches under this name */
+} spgemm_kernel_time;
+SPGEMM_API int spgemm_plan_kernel_times(spgemm_plan_t plan, spgemm_kernel_time *out, int max_entries, int *n_out);
 
 /*
  * Inspection of the intermediate results, for tests: copy flop[m] (int64),
@@ -152,9 +177,9 @@ int spgemm_plan_stats(spgemm_plan_t plan, spgemm_stats *out);
  * (int32, after spgemm_symbolic) into caller DEVICE buffers.
  * sym_bin_offsets is a HOST array of n_sym_bins+1 int64.
  */
-int spgemm_plan_row_flop(spgemm_plan_t plan, int64_t *flop_out);
-int spgemm_plan_sym_bins(spgemm_plan_t plan, int32_t *perm_out, int64_t *sym_bin_offsets);
-int spgemm_plan_row_nnz(spgemm_plan_t plan, int32_t *nnz_out);
+SPGEMM_API int spgemm_plan_row_flop(spgemm_plan_t plan, int64_t *flop_out);
+SPGEMM_API int spgemm_plan_sym_bins(spgemm_plan_t plan, int32_t *perm_out, int64_t *sym_bin_offsets);
+SPGEMM_API int spgemm_plan_row_nnz(spgemm_plan_t plan, int32_t *nnz_out);
 
 /* Allocator callback for spgemm(): returns a device pointer of `bytes`
  * bytes (16-byte aligned) or NULL.  The caller owns what it returns. */
@@ -167,15 +192,15 @@ typedef void *(*spgemm_alloc_fn)(size_t bytes, void *ctx);
  * c_col_idx and c_vals.  Results are ready when `stream` reaches the end
  * of the call's work.
  */
-int spgemm(const spgemm_csr *A, const spgemm_csr *B, int dtype, unsigned flags, void *stream,
+SPGEMM_API int spgemm(const spgemm_csr *A, const spgemm_csr *B, int dtype, unsigned flags, void *stream,
            spgemm_alloc_fn alloc, void *alloc_ctx,
            int32_t **c_row_ptr, int32_t **c_col_idx, void **c_vals, int64_t *nnz_c);
 
 /* Human-readable name of a status code (static string). */
-const char *spgemm_status_string(int status);
+SPGEMM_API const char *spgemm_status_string(int status);
 
 /* Last CUDA error text recorded by the library on this thread ("" if none). */
-const char *spgemm_last_error(void);
+SPGEMM_API const char *spgemm_last_error(void);
 
 #ifdef __cplusplus
 }

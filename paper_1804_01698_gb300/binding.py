@@ -1,0 +1,330 @@
+"""Thin Python binding of libspgemm_gb300.so (the C ABI of include/spgemm.h).
+
+Only argument marshalling happens here: torch tensors provide device memory
+and the CUDA stream, and every step of the product runs in the library's
+CUDA kernels.  The functions keep the C names:
+
+    spgemm_plan_create, spgemm_symbolic, spgemm_numeric, spgemm_plan_destroy,
+    spgemm_plan_stats, spgemm_plan_workspace_bytes, spgemm_plan_row_flop,
+    spgemm_plan_sym_bins, spgemm_plan_row_nnz, spgemm, spgemm_status_string
+
+Importing this module loads the library; it raises if the library has not
+been built (there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+_LIB = None
+
+SPGEMM_I64, SPGEMM_F32, SPGEMM_F64 = 0, 1, 2
+SPGEMM_UNSORTED, SPGEMM_SORTED, SPGEMM_VALIDATE, SPGEMM_TIMING = 0, 1, 2, 4
+MAX_BINS = 24
+
+_DTYPES = {torch.int64: SPGEMM_I64, torch.float32: SPGEMM_F32, torch.float64: SPGEMM_F64}
+_TORCH = {v: k for k, v in _DTYPES.items()}
+
+
+class SpgemmError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib = library()
+        msg = lib.spgemm_status_string(status).decode()
+        detail = lib.spgemm_last_error().decode()
+        super().__init__(f"{where}: {msg} ({status})" + (f": {detail}" if detail else ""))
+        self.status = status
+
+
+class CsrDesc(ctypes.Structure):
+    _fields_ = [("nrows", ctypes.c_int64), ("ncols", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p), ("vals", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64),
+                ("total_flop", ctypes.c_int64), ("max_row_flop", ctypes.c_int64), ("nnz_c", ctypes.c_int64),
+                ("n_sym_bins", ctypes.c_int32), ("n_num_bins", ctypes.c_int32),
+                ("sym_bin_rows", ctypes.c_int64 * MAX_BINS), ("num_bin_rows", ctypes.c_int64 * MAX_BINS),
+                ("sym_bin_table", ctypes.c_int32 * MAX_BINS), ("num_bin_table", ctypes.c_int32 * MAX_BINS),
+                ("workspace_bytes", ctypes.c_int64), ("kernel_launches", ctypes.c_int32), ("state", ctypes.c_int32),
+                ("sym_bin_flop", ctypes.c_int64 * MAX_BINS), ("num_bin_flop", ctypes.c_int64 * MAX_BINS)]
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("ms", ctypes.c_float), ("launches", ctypes.c_int32)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+EXPORTED = ("spgemm_plan_create", "spgemm_symbolic", "spgemm_numeric", "spgemm_plan_destroy",
+            "spgemm_plan_workspace_bytes", "spgemm_plan_stats", "spgemm_plan_row_flop", "spgemm_plan_sym_bins",
+            "spgemm_plan_row_nnz", "spgemm_plan_kernel_times", "spgemm", "spgemm_status_string",
+            "spgemm_last_error")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def library():
+    """Load the library (once).  Raises if it has not been built."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"the CUDA SpGEMM library is not built ({path}); run __graft_entry__.build() "
+                           "or python -m paper_1804_01698_gb300.build")
+    lib = ctypes.CDLL(path)
+    P, I64, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    lib.spgemm_plan_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(CsrDesc), ctypes.POINTER(CsrDesc), I32,
+                                       ctypes.c_uint, P]
+    lib.spgemm_symbolic.argtypes = [P, P, ctypes.POINTER(I64)]
+    lib.spgemm_numeric.argtypes = [P, P, P, P]
+    lib.spgemm_plan_destroy.argtypes = [P]
+    lib.spgemm_plan_workspace_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+    lib.spgemm_plan_stats.argtypes = [P, ctypes.POINTER(Stats)]
+    lib.spgemm_plan_row_flop.argtypes = [P, P]
+    lib.spgemm_plan_sym_bins.argtypes = [P, P, P]
+    lib.spgemm_plan_row_nnz.argtypes = [P, P]
+    lib.spgemm_plan_kernel_times.argtypes = [P, ctypes.POINTER(KernelTime), I32, ctypes.POINTER(I32)]
+    lib.spgemm.argtypes = [ctypes.POINTER(CsrDesc), ctypes.POINTER(CsrDesc), I32, ctypes.c_uint, P, ALLOC_FN, P,
+                           ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(I64)]
+    for name in EXPORTED:
+        getattr(lib, name).restype = ctypes.c_int
+    lib.spgemm_status_string.argtypes = [I32]
+    lib.spgemm_status_string.restype = ctypes.c_char_p
+    lib.spgemm_last_error.argtypes = []
+    lib.spgemm_last_error.restype = ctypes.c_char_p
+    _LIB = lib
+    return lib
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise SpgemmError(status, where)
+
+
+@dataclass
+class DeviceCSR:
+    """CSR matrix in device memory (torch tensors: int32 row_ptr/col_idx, values)."""
+
+    nrows: int
+    ncols: int
+    row_ptr: torch.Tensor
+    col_idx: torch.Tensor
+    vals: torch.Tensor
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col_idx.numel())
+
+    def desc(self) -> CsrDesc:
+        return CsrDesc(self.nrows, self.ncols, self.nnz, self.row_ptr.data_ptr(),
+                       self.col_idx.data_ptr() if self.nnz else None, self.vals.data_ptr() if self.nnz else None)
+
+    def to_host(self):
+        from .inputs import CSR
+        return CSR(self.nrows, self.ncols, self.row_ptr.cpu().numpy(), self.col_idx.cpu().numpy(),
+                   self.vals.cpu().numpy())
+
+
+def to_device(m, device="cuda", dtype=None, non_blocking=False) -> DeviceCSR:
+    """Copy a host CSR (paper_1804_01698_gb300.inputs.CSR) to the device."""
+    vals = torch.from_numpy(np.ascontiguousarray(m.vals))
+    if dtype is not None:
+        vals = vals.to(dtype)
+    rp = torch.from_numpy(np.ascontiguousarray(m.row_ptr, dtype=np.int32))
+    ci = torch.from_numpy(np.ascontiguousarray(m.col_idx, dtype=np.int32))
+    return DeviceCSR(m.nrows, m.ncols, rp.to(device, non_blocking=non_blocking),
+                     ci.to(device, non_blocking=non_blocking), vals.to(device, non_blocking=non_blocking))
+
+
+def _stream_ptr(stream) -> int | None:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream or None
+
+
+class Plan:
+    """A plan for C = A*B; methods mirror spgemm_symbolic / spgemm_numeric."""
+
+    def __init__(self, A: DeviceCSR, B: DeviceCSR, sorted_output: bool = True, stream=None, timing: bool = False):
+        self.lib = library()
+        if A.vals.dtype != B.vals.dtype or A.vals.dtype not in _DTYPES:
+            raise TypeError("A and B must share a value dtype among int64, float32, float64")
+        self.A, self.B = A, B
+        self.dtype = A.vals.dtype
+        self.device = A.row_ptr.device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        flags = (SPGEMM_SORTED if sorted_output else SPGEMM_UNSORTED) | (SPGEMM_TIMING if timing else 0)
+        self._a, self._b = A.desc(), B.desc()
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(self.lib.spgemm_plan_create(ctypes.byref(h), ctypes.byref(self._a), ctypes.byref(self._b),
+                                               _DTYPES[self.dtype], flags, _stream_ptr(self.stream)),
+                   "spgemm_plan_create")
+        self.handle = h
+        self.c_row_ptr = None
+        self.nnz_c = None
+
+    def symbolic(self) -> int:
+        self.c_row_ptr = torch.empty(self.A.nrows + 1, dtype=torch.int32, device=self.device)
+        nnz = ctypes.c_int64()
+        with torch.cuda.device(self.device):
+            _check(self.lib.spgemm_symbolic(self.handle, self.c_row_ptr.data_ptr(), ctypes.byref(nnz)),
+                   "spgemm_symbolic")
+        self.nnz_c = int(nnz.value)
+        return self.nnz_c
+
+    def numeric(self, c_col_idx: torch.Tensor | None = None, c_vals: torch.Tensor | None = None) -> DeviceCSR:
+        if c_col_idx is None:
+            c_col_idx = torch.empty(max(self.nnz_c, 0), dtype=torch.int32, device=self.device)
+        if c_vals is None:
+            c_vals = torch.empty(max(self.nnz_c, 0), dtype=self.dtype, device=self.device)
+        with torch.cuda.device(self.device):
+            _check(self.lib.spgemm_numeric(self.handle, self.c_row_ptr.data_ptr(),
+                                           c_col_idx.data_ptr() if self.nnz_c else None,
+                                           c_vals.data_ptr() if self.nnz_c else None), "spgemm_numeric")
+        return DeviceCSR(self.A.nrows, self.B.ncols, self.c_row_ptr, c_col_idx, c_vals)
+
+    def stats(self) -> dict:
+        s = Stats()
+        status = self.lib.spgemm_plan_stats(self.handle, ctypes.byref(s))
+        out = {name: getattr(s, name) for name, _ in Stats._fields_}
+        for key in ("sym_bin_rows", "sym_bin_table", "sym_bin_flop"):
+            out[key] = list(getattr(s, key))[: s.n_sym_bins]
+        for key in ("num_bin_rows", "num_bin_table", "num_bin_flop"):
+            out[key] = list(getattr(s, key))[: s.n_num_bins]
+        out["status"] = status
+        return out
+
+    def kernel_times(self) -> dict:
+        """{kernel name: (milliseconds, launches)} for plans created with timing=True."""
+        buf = (KernelTime * 64)()
+        n = ctypes.c_int()
+        _check(self.lib.spgemm_plan_kernel_times(self.handle, buf, 64, ctypes.byref(n)), "spgemm_plan_kernel_times")
+        return {buf[j].name.decode(): (float(buf[j].ms), int(buf[j].launches)) for j in range(min(n.value, 64))}
+
+    def workspace_bytes(self) -> int:
+        v = ctypes.c_size_t()
+        _check(self.lib.spgemm_plan_workspace_bytes(self.handle, ctypes.byref(v)), "spgemm_plan_workspace_bytes")
+        return int(v.value)
+
+    def row_flop(self) -> torch.Tensor:
+        out = torch.empty(self.A.nrows, dtype=torch.int64, device=self.device)
+        _check(self.lib.spgemm_plan_row_flop(self.handle, out.data_ptr()), "spgemm_plan_row_flop")
+        return out
+
+    def sym_bins(self):
+        s = Stats()
+        self.lib.spgemm_plan_stats(self.handle, ctypes.byref(s))
+        offs = (ctypes.c_int64 * (s.n_sym_bins + 1))()
+        perm = torch.empty(max(self.A.nrows, 1), dtype=torch.int32, device=self.device)
+        _check(self.lib.spgemm_plan_sym_bins(self.handle, perm.data_ptr(), offs), "spgemm_plan_sym_bins")
+        offsets = list(offs)
+        return perm[: offsets[-1]], offsets
+
+    def row_nnz(self) -> torch.Tensor:
+        out = torch.empty(self.A.nrows, dtype=torch.int32, device=self.device)
+        _check(self.lib.spgemm_plan_row_nnz(self.handle, out.data_ptr()), "spgemm_plan_row_nnz")
+        return out
+
+    def destroy(self):
+        if getattr(self, "handle", None):
+            self.lib.spgemm_plan_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def spgemm_plan_create(A: DeviceCSR, B: DeviceCSR, sorted_output: bool = True, stream=None,
+                       timing: bool = False) -> Plan:
+    return Plan(A, B, sorted_output, stream, timing)
+
+
+def spgemm_plan_kernel_times(plan: Plan) -> dict:
+    return plan.kernel_times()
+
+
+def spgemm_symbolic(plan: Plan) -> int:
+    return plan.symbolic()
+
+
+def spgemm_numeric(plan: Plan, c_col_idx=None, c_vals=None) -> DeviceCSR:
+    return plan.numeric(c_col_idx, c_vals)
+
+
+def spgemm_plan_destroy(plan: Plan) -> None:
+    plan.destroy()
+
+
+def spgemm_plan_stats(plan: Plan) -> dict:
+    return plan.stats()
+
+
+def spgemm_plan_workspace_bytes(plan: Plan) -> int:
+    return plan.workspace_bytes()
+
+
+def spgemm_plan_row_flop(plan: Plan) -> torch.Tensor:
+    return plan.row_flop()
+
+
+def spgemm_plan_sym_bins(plan: Plan):
+    return plan.sym_bins()
+
+
+def spgemm_plan_row_nnz(plan: Plan) -> torch.Tensor:
+    return plan.row_nnz()
+
+
+def spgemm_status_string(status: int) -> str:
+    return library().spgemm_status_string(status).decode()
+
+
+def spgemm(A: DeviceCSR, B: DeviceCSR, sorted_output: bool = True, stream=None) -> DeviceCSR:
+    """One-shot C = A*B through the C entry point spgemm(); C's buffers are
+    torch tensors allocated through the allocator callback."""
+    lib = library()
+    if A.vals.dtype != B.vals.dtype or A.vals.dtype not in _DTYPES:
+        raise TypeError("A and B must share a value dtype among int64, float32, float64")
+    device = A.row_ptr.device
+    keep: dict[int, torch.Tensor] = {}
+
+    def _alloc(nbytes, _ctx):
+        t = torch.empty(max(int(nbytes), 16), dtype=torch.uint8, device=device)
+        keep[t.data_ptr()] = t
+        return t.data_ptr()
+
+    cb = ALLOC_FN(_alloc)
+    a, b = A.desc(), B.desc()
+    rp, ci, cv = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    nnz = ctypes.c_int64()
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    with torch.cuda.device(device):
+        status = lib.spgemm(ctypes.byref(a), ctypes.byref(b), _DTYPES[A.vals.dtype],
+                            SPGEMM_SORTED if sorted_output else SPGEMM_UNSORTED, _stream_ptr(s), cb, None,
+                            ctypes.byref(rp), ctypes.byref(ci), ctypes.byref(cv), ctypes.byref(nnz))
+    _check(status, "spgemm")
+    n = int(nnz.value)
+    rpt = keep[rp.value][: (A.nrows + 1) * 4].view(torch.int32)
+    cit = keep[ci.value][: n * 4].view(torch.int32)
+    esz = torch.empty(0, dtype=A.vals.dtype).element_size()
+    cvt = keep[cv.value][: n * esz].view(A.vals.dtype)
+    return DeviceCSR(A.nrows, B.ncols, rpt, cit, cvt)

@@ -1,0 +1,180 @@
+// Device helpers shared by the SpGEMM kernels: the hash function of the
+// paper's Hash SpGEMM (Sec. 4.2.1), value-type accumulation, warp and block
+// reductions and scans, and the device error word.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sg {
+
+// Sec. 4.2.1: the key (a column index) is multiplied by a constant and the
+// remainder modulo the power-of-two table size picks the slot; collisions
+// are resolved by linear probing.  The constant is Knuth's multiplicative
+// hashing constant (TAOCP Vol. 3, Sec. 6.4), floor(2^32 / golden ratio).
+constexpr uint32_t kHashScale = 2654435761u;
+constexpr int32_t kEmpty = -1;  // Sec. 4.2.1: tables are initialised with -1
+
+__device__ __forceinline__ uint32_t hash_slot(int32_t col, uint32_t mask) {
+  return ((uint32_t)col * kHashScale) & mask;
+}
+
+// Bits of the device error word (DevCounters::err).
+enum : uint32_t {
+  kErrCsr = 1u,       // an index outside its matrix, or a malformed row_ptr
+  kErrProbe = 2u,     // a probe sequence visited the whole table without a slot
+  kErrOverflow = 4u,  // nnz(C) does not fit int32 indexing
+  kErrRetry = 8u,     // an atomic update retried past its bound
+};
+
+__device__ __forceinline__ void raise_err(uint32_t *err, uint32_t bit) { atomicOr(err, bit); }
+
+// Bound on compare-and-swap retries of one accumulation; contention on a
+// single slot is limited by the number of threads of a block, so this bound
+// is never reached by a correct kernel.
+constexpr int kMaxCasRetries = 1 << 20;
+
+// ---------------------------------------------------------------------------
+// Value types.  acc_shared/acc_global add a*b into *p with atomics; the f64
+// form folds the multiply into the add with one fused multiply-add inside a
+// compare-and-swap loop, because GB300's FP64 pipe is the scarce resource
+// and a separate multiply plus the hardware's own CAS-loop add would cost
+// two FP64 operations per product.
+template <typename T> struct Val;
+
+template <> struct Val<double> {
+  static __device__ __forceinline__ bool acc_shared(double *p, double a, double b) {
+    unsigned long long *q = reinterpret_cast<unsigned long long *>(p);
+    unsigned long long old = *reinterpret_cast<volatile unsigned long long *>(q);
+    for (int it = 0; it < kMaxCasRetries; ++it) {
+      unsigned long long assumed = old;
+      double nv = fma(a, b, __longlong_as_double((long long)assumed));
+      old = atomicCAS(q, assumed, (unsigned long long)__double_as_longlong(nv));
+      if (old == assumed) return true;
+    }
+    return false;
+  }
+  static __device__ __forceinline__ void acc_global(double *p, double a, double b) { atomicAdd(p, a * b); }
+};
+
+template <> struct Val<float> {
+  static __device__ __forceinline__ bool acc_shared(float *p, float a, float b) {
+    atomicAdd(p, a * b);
+    return true;
+  }
+  static __device__ __forceinline__ void acc_global(float *p, float a, float b) { atomicAdd(p, a * b); }
+};
+
+template <> struct Val<int64_t> {
+  static __device__ __forceinline__ bool acc_shared(int64_t *p, int64_t a, int64_t b) {
+    atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)a * (unsigned long long)b);
+    return true;
+  }
+  static __device__ __forceinline__ void acc_global(int64_t *p, int64_t a, int64_t b) {
+    atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)a * (unsigned long long)b);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Reductions and scans.
+template <typename T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T> __device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    T w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+template <typename T> __device__ __forceinline__ T warp_incl_scan(T v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T w = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += w;
+  }
+  return v;
+}
+
+// Block-wide sum; every thread of the block must call it.  `scratch` holds
+// at least 32 elements and is reused, so callers separate two calls with a
+// barrier (the function ends with one).
+template <typename T> __device__ __forceinline__ T block_sum(T v, T *scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  if (lane == 0) scratch[wid] = v;
+  __syncthreads();
+  T r = (threadIdx.x < nw) ? scratch[threadIdx.x] : T(0);
+  if (wid == 0) r = warp_sum(r);
+  if (threadIdx.x == 0) scratch[0] = r;
+  __syncthreads();
+  r = scratch[0];
+  __syncthreads();
+  return r;
+}
+
+// Block-wide exclusive scan; returns this thread's exclusive prefix and the
+// block total through *total.  Same calling rules as block_sum.
+template <typename T> __device__ __forceinline__ T block_excl_scan(T v, T *scratch, T *total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  T inc = warp_incl_scan(v);
+  if (lane == 31) scratch[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    T s = (lane < nw) ? scratch[lane] : T(0);
+    T si = warp_incl_scan(s);
+    if (lane < nw) scratch[lane] = si - s;
+    if (lane == 31) scratch[32] = si;
+  }
+  __syncthreads();
+  T r = scratch[wid] + inc - v;
+  *total = scratch[32];
+  __syncthreads();
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// The row loop shared by every phase (paper Fig. "RowWise_SpGEMM"): for
+// each stored a_ik of row i and each stored b_kj, call f(j, a_ik, b_kj).
+// A group of G lanes (a power of two dividing 32) takes one a_ik at a time
+// and strides over row k of B, so consecutive lanes read consecutive
+// entries of B (coalesced); groups take a_ik in turn.  U entries of B are
+// loaded before any is processed, to keep several loads in flight.
+// Columns of B outside [0, ncols) raise kErrCsr and are skipped.
+template <int U, bool NEED_VAL, typename T, typename F>
+__device__ __forceinline__ void for_row_products(int64_t a0, int64_t a1, int group, int ngroups, int lig, int G,
+                                                 const int32_t *__restrict__ aci, const T *__restrict__ av,
+                                                 const int32_t *__restrict__ brp, const int32_t *__restrict__ bci,
+                                                 const T *__restrict__ bv, int32_t ncols, uint32_t *err, F &&f) {
+  for (int64_t j = a0 + group; j < a1; j += ngroups) {
+    const int32_t kk = __ldg(aci + j);
+    T a = T(0);
+    if (NEED_VAL) a = __ldg(av + j);
+    const int32_t bs = __ldg(brp + kk), be = __ldg(brp + kk + 1);
+    for (int32_t q = bs + lig; q < be; q += G * U) {
+      int32_t c[U];
+      T v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int32_t qq = q + u * G;
+        c[u] = qq < be ? __ldg(bci + qq) : -1;
+        if (NEED_VAL) v[u] = qq < be ? __ldg(bv + qq) : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (q + u * G < be) {
+          if ((uint32_t)c[u] < (uint32_t)ncols) f(c[u], a, NEED_VAL ? v[u] : T(0));
+          else raise_err(err, kErrCsr);
+        }
+      }
+    }
+  }
+}
+
+}  // namespace sg

@@ -1,0 +1,164 @@
+// Plan object and kernel launchers of the GB300 hash SpGEMM (host side).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/spgemm.h"
+
+namespace sg {
+
+// ---------------------------------------------------------------------------
+// Row bins.  The paper balances rows over threads by flop (Sec. 4.1) and
+// sizes each thread's hash table from the largest flop of its rows
+// (Sec. 4.2.1); GPU hash SpGEMM instead bins rows by density and runs one
+// kernel per bin (Sec. 2).  Here a row goes to the smallest bin whose table
+// holds its key bound with the bin's load factor:
+//   symbolic bound  = min(flop_i, ncols(B))      (Fig. "Hash_SpGEMM")
+//   numeric  bound  = nnz(c_i*)                  (exact, from symbolic)
+// Warp bins: one warp per row, table in shared memory.
+// Block bins: one thread block per row, table in shared memory.
+// Heavy rows: a column bitmap in shared memory when ncols(B) is small
+// enough (BITMAP), otherwise a hash table in global memory (GLOBAL).
+enum BinKind { kWarp = 0, kBlock = 1, kBitmap = 2, kGlobal = 3 };
+
+struct BinCfg {
+  int kind;
+  int table;    // hash table slots (power of two), 0 for bitmap/global bins
+  int threads;  // threads per block
+  int64_t cap;  // largest bound this bin accepts
+};
+
+constexpr int kNumHashBins = 10;  // warp 64..1024, block 2048..32768
+constexpr int kSymBitmapBin = 10;
+constexpr int kSymGlobalBin = 11;
+constexpr int kNumSymBins = 12;
+constexpr int kNumBitmapBin = 9;   // numeric bins 0..8 are hash bins
+constexpr int kNumGlobalBin = 10;
+constexpr int kNumNumBins = 11;
+constexpr int kWarpsPerBlock = 4;  // warp bins: rows per block
+
+// Symbolic bins 0..9: tables 64 .. 32768 slots, load factor 1/2 for warp
+// tables and 3/4 for block tables (the bound overestimates the key count
+// by the compression ratio, so the true load is lower).
+extern const BinCfg kSymBins[kNumSymBins];
+// Numeric bins 0..8: tables 64 .. 16384 slots, same load factors.
+extern const BinCfg kNumBins[kNumNumBins];
+
+// Heavy-row threshold: rows whose bound exceeds the largest numeric block
+// table go to the heavy bins (the symbolic bitmap bin takes them early so
+// that its bitmaps can be reused by the numeric phase).
+constexpr int64_t kHeavyBound = 12288;       // 3/4 of 16384
+constexpr int64_t kBlockSymMax = 24576;      // 3/4 of 32768 (global-table inputs)
+constexpr int64_t kBitmapMaxCols = 1 << 18;  // bitmap + prefix <= 64 KB
+
+// Device counters of a plan (zeroed at creation).
+struct DevCounters {
+  unsigned long long sym_count[kNumSymBins];
+  unsigned long long sym_cursor[kNumSymBins];
+  unsigned long long num_count[kNumNumBins];
+  unsigned long long num_cursor[kNumNumBins];
+  unsigned long long sym_flop[kNumSymBins];
+  unsigned long long num_flop[kNumNumBins];
+  unsigned long long total_flop;
+  unsigned long long max_flop;
+  unsigned long long max_bound_global;  // largest symbolic bound in the global bin
+  unsigned long long nnz_c;
+  unsigned long long max_nnz_global;    // largest nnz in the numeric global bin
+  unsigned long long bm_items;          // numeric bitmap work items (row windows)
+  unsigned long long bm_cursor;
+  unsigned int err;
+  unsigned int pad;
+};
+
+// Kernel arguments common to all phases.
+struct Args {
+  int64_t m, n, k;
+  const int32_t *arp, *aci, *brp, *bci;
+  const void *av, *bv;
+  int G;  // lanes per stored a_ik
+  uint32_t *err;
+};
+
+}  // namespace sg
+
+struct spgemm_plan_s {
+  int64_t m, n, k, nnz_a, nnz_b;
+  const int32_t *arp, *aci, *brp, *bci;
+  const void *av, *bv;
+  int dtype;
+  unsigned flags;
+  cudaStream_t stream;
+  int device;
+  int state;  // 0 planned, 1 symbolic done, 2 numeric done
+  int G;
+  bool bitmap_ok;
+  int bm_words;
+
+  // workspace (device)
+  void *ws_fixed;  // counters + per-row arrays
+  size_t ws_fixed_bytes;
+  sg::DevCounters *dc;
+  int64_t *flop;
+  uint8_t *rbin;   // symbolic bin of each row (255 = none)
+  int32_t *perm;   // rows grouped by symbolic bin
+  int32_t *nnz_row;
+  uint8_t *rbin2;  // numeric bin of each row
+  int32_t *perm2;  // rows grouped by numeric bin
+  uint32_t *bitmaps;  // one bitmap per row of the symbolic bitmap bin
+  size_t bitmaps_bytes;
+  int2 *bm_items;     // numeric bitmap work items (bitmap index, window)
+  size_t bm_items_bytes;
+  void *gtab;         // global hash tables (heavy rows without bitmaps)
+  size_t gtab_bytes;
+  int64_t gtab_slots;  // table slots per block
+  int64_t gtab_blocks;
+
+  // host copies
+  sg::DevCounters *hc;  // pinned
+  int64_t sym_count[sg::kNumSymBins], sym_off[sg::kNumSymBins + 1];
+  int64_t num_count[sg::kNumNumBins], num_off[sg::kNumNumBins + 1];
+  int64_t sym_flop[sg::kNumSymBins], num_flop[sg::kNumNumBins];
+  int64_t total_flop, max_flop, nnz_c;
+  int64_t bm_cap;  // values per numeric bitmap window
+  int32_t launches;
+  const int32_t *c_rp;
+
+  // per-kernel CUDA events (SPGEMM_TIMING)
+  struct Timed {
+    std::string name;
+    cudaEvent_t start, stop;
+  };
+  std::vector<Timed> timed;
+};
+
+namespace sg {
+// Brackets one kernel launch with CUDA events when the plan records timings,
+// and counts the launch.
+struct KernelScope {
+  spgemm_plan_s *p;
+  int idx = -1;
+  KernelScope(spgemm_plan_s *plan, const std::string &name) : p(plan) {
+    p->launches++;
+    if (!(p->flags & SPGEMM_TIMING)) return;
+    spgemm_plan_s::Timed t{name, nullptr, nullptr};
+    if (cudaEventCreate(&t.start) != cudaSuccess || cudaEventCreate(&t.stop) != cudaSuccess) return;
+    cudaEventRecord(t.start, p->stream);
+    p->timed.push_back(t);
+    idx = (int)p->timed.size() - 1;
+  }
+  ~KernelScope() {
+    if (idx >= 0) cudaEventRecord(p->timed[idx].stop, p->stream);
+  }
+};
+
+// Launchers (return a cudaError_t from the launch).
+cudaError_t launch_symbolic(spgemm_plan_s *p);
+cudaError_t launch_numeric(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_ci, void *c_v);
+int64_t bitmap_capacity(int dtype, int bm_words);
+int max_smem_per_block();
+}  // namespace sg

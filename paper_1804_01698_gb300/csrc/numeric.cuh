@@ -1,0 +1,467 @@
+// Numeric phase (paper Sec. 4.2.1; Fig. "Hash_SpGEMM", step Numeric): the
+// keys are inserted again and a_ik*b_kj is added to the value of the key's
+// slot; the finished row is then stored, sorted by column "if necessary".
+//
+//   k_num_warp<T,S>   one warp per row, S-slot table (keys + values) in smem
+//   k_num_block<T,S>  one block per row, S-slot table in smem
+//   k_num_bitmap<T>   heavy rows with a column bitmap saved by the symbolic
+//                     phase: the rank of column j among the row's columns is
+//                     its output position, so values accumulate in a dense
+//                     array indexed by rank and come out sorted.  A row with
+//                     more entries than fit in shared memory is split into
+//                     windows of consecutive ranks (one block each).
+//   k_num_global<T>   heavy rows without bitmaps: hash table in global memory.
+//
+// Tables are sized from the exact row count found by the symbolic phase,
+// so they are smaller than the symbolic tables.
+#pragma once
+
+#include <string>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace sg {
+
+constexpr int kUN = 2;  // B entries (column + value) loaded ahead per lane
+
+// Finds or claims the slot of key c and accumulates a*b there.
+template <typename T, bool GLOBAL_MEM>
+__device__ __forceinline__ void insert_acc(int32_t *keys, T *vals, uint32_t mask, int32_t c, T a, T b,
+                                           uint32_t *err) {
+  uint32_t h = hash_slot(c, mask);
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    const int32_t old = atomicCAS(keys + h, kEmpty, c);
+    if (old == kEmpty || old == c) {
+      if (GLOBAL_MEM) {
+        Val<T>::acc_global(vals + h, a, b);
+      } else if (!Val<T>::acc_shared(vals + h, a, b)) {
+        raise_err(err, kErrRetry);
+      }
+      return;
+    }
+    h = (h + 1) & mask;
+  }
+  raise_err(err, kErrProbe);
+}
+
+template <typename T>
+__device__ __forceinline__ void swap_entry(uint32_t *keys, T *vals, int i, int l) {
+  const uint32_t ki = keys[i];
+  keys[i] = keys[l];
+  keys[l] = ki;
+  const T vi = vals[i];
+  vals[i] = vals[l];
+  vals[l] = vi;
+}
+
+// Bitonic sort of n (power of two) entries by unsigned key; empty slots
+// (-1 = 0xffffffff) sort last.  Threads t0, t0+tstride, ... take the n/2
+// compare-exchange pairs of each stage; `sync` separates the stages.
+template <typename T, typename Sync>
+__device__ __forceinline__ void bitonic_sort(uint32_t *keys, T *vals, int n, int t0, int tstride, Sync &&sync) {
+  for (int k = 2; k <= n; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = t0; t < (n >> 1); t += tstride) {
+        const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1));
+        const int l = i + j;
+        const bool asc = (i & k) == 0;
+        const uint32_t ki = keys[i], kl = keys[l];
+        if ((ki > kl) == asc) swap_entry(keys, vals, i, l);
+      }
+      sync();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <typename T, int S>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    k_num_warp(Args a, const int32_t *__restrict__ rows, int64_t nrows, const int32_t *__restrict__ c_rp,
+               int32_t *__restrict__ c_ci, T *__restrict__ c_v, int sorted) {
+  extern __shared__ __align__(16) unsigned char sm_num_warp[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+  if (w >= nrows) return;
+  int32_t *keys = reinterpret_cast<int32_t *>(sm_num_warp) + warp * S;
+  T *vals = reinterpret_cast<T *>(sm_num_warp + (size_t)kWarpsPerBlock * S * sizeof(int32_t)) + warp * S;
+  for (int s = lane; s < S; s += 32) {
+    keys[s] = kEmpty;
+    vals[s] = T(0);
+  }
+  __syncwarp();
+  const int32_t i = rows[w];
+  const int G = a.G;
+  for_row_products<kUN, true, T>(a.arp[i], a.arp[i + 1], lane / G, 32 / G, lane & (G - 1), G, a.aci,
+                                 (const T *)a.av, a.brp, a.bci, (const T *)a.bv, (int32_t)a.k, a.err,
+                                 [&](int32_t c, T av, T bv) { insert_acc<T, false>(keys, vals, S - 1, c, av, bv, a.err); });
+  __syncwarp();
+  const int32_t rp = c_rp[i];
+  const int32_t nnz = c_rp[i + 1] - rp;
+  if (sorted) {
+    bitonic_sort(reinterpret_cast<uint32_t *>(keys), vals, S, lane, 32, [] { __syncwarp(); });
+    for (int r = lane; r < nnz; r += 32) {
+      c_ci[rp + r] = keys[r];
+      c_v[rp + r] = vals[r];
+    }
+  } else {
+    int base = 0;
+    for (int s0 = 0; s0 < S; s0 += 32) {
+      const int s = s0 + lane;
+      const int32_t kk = keys[s];
+      const bool occ = kk != kEmpty;
+      const unsigned m = __ballot_sync(0xffffffffu, occ);
+      const int pos = base + __popc(m & ((1u << lane) - 1u));
+      if (occ && pos < nnz) {
+        c_ci[rp + pos] = kk;
+        c_v[rp + pos] = vals[s];
+      }
+      base += __popc(m);
+    }
+    if (lane == 0 && base != nnz) raise_err(a.err, kErrProbe);
+  }
+}
+
+// sort_mode: 0 unsorted, 1 bitonic sort of the table, 2 rank by column
+// bitmap (needs 2 * words * 4 bytes more shared memory).
+template <typename T, int S>
+__global__ void __launch_bounds__(1024, 1)
+    k_num_block(Args a, const int32_t *__restrict__ rows, const int32_t *__restrict__ c_rp,
+                int32_t *__restrict__ c_ci, T *__restrict__ c_v, int sort_mode, int words) {
+  extern __shared__ __align__(16) unsigned char sm_num_block[];
+  __shared__ int red[33];
+  __shared__ int cursor;
+  int32_t *keys = reinterpret_cast<int32_t *>(sm_num_block);
+  T *vals = reinterpret_cast<T *>(sm_num_block + (size_t)S * sizeof(int32_t));
+  for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    keys[s] = kEmpty;
+    vals[s] = T(0);
+  }
+  if (threadIdx.x == 0) cursor = 0;
+  __syncthreads();
+  const int32_t i = rows[blockIdx.x];
+  const int G = a.G;
+  for_row_products<kUN, true, T>(a.arp[i], a.arp[i + 1], threadIdx.x / G, blockDim.x / G, threadIdx.x & (G - 1), G,
+                                 a.aci, (const T *)a.av, a.brp, a.bci, (const T *)a.bv, (int32_t)a.k, a.err,
+                                 [&](int32_t c, T av, T bv) { insert_acc<T, false>(keys, vals, S - 1, c, av, bv, a.err); });
+  __syncthreads();
+  const int32_t rp = c_rp[i];
+  const int32_t nnz = c_rp[i + 1] - rp;
+  if (sort_mode == 1) {
+    bitonic_sort(reinterpret_cast<uint32_t *>(keys), vals, S, (int)threadIdx.x, (int)blockDim.x, [] { __syncthreads(); });
+    for (int r = threadIdx.x; r < nnz; r += blockDim.x) {
+      c_ci[rp + r] = keys[r];
+      c_v[rp + r] = vals[r];
+    }
+  } else if (sort_mode == 2) {
+    uint32_t *bm = reinterpret_cast<uint32_t *>(sm_num_block + (size_t)S * (sizeof(int32_t) + sizeof(T)));
+    int32_t *pre = reinterpret_cast<int32_t *>(bm + words);
+    for (int w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0u;
+    __syncthreads();
+    for (int s = threadIdx.x; s < S; s += blockDim.x) {
+      const int32_t kk = keys[s];
+      if (kk != kEmpty) atomicOr(bm + (kk >> 5), 1u << (kk & 31));
+    }
+    __syncthreads();
+    // exclusive prefix of popcounts: each thread owns a contiguous run of words
+    const int per = (words + blockDim.x - 1) / blockDim.x;
+    const int w0 = threadIdx.x * per, w1 = min(words, w0 + per);
+    int local = 0;
+    for (int w = w0; w < w1; ++w) local += __popc(bm[w]);
+    int tot;
+    int run = block_excl_scan(local, red, &tot);
+    for (int w = w0; w < w1; ++w) {
+      pre[w] = run;
+      run += __popc(bm[w]);
+    }
+    __syncthreads();
+    for (int s = threadIdx.x; s < S; s += blockDim.x) {
+      const int32_t kk = keys[s];
+      if (kk != kEmpty) {
+        const int r = pre[kk >> 5] + __popc(bm[kk >> 5] & ((1u << (kk & 31)) - 1u));
+        if (r < nnz) {
+          c_ci[rp + r] = kk;
+          c_v[rp + r] = vals[s];
+        }
+      }
+    }
+    if (threadIdx.x == 0 && tot != nnz) raise_err(a.err, kErrProbe);
+  } else {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int s0 = warp * 32; s0 < S; s0 += nw * 32) {
+      const int s = s0 + lane;
+      const int32_t kk = keys[s];
+      const bool occ = kk != kEmpty;
+      const unsigned m = __ballot_sync(0xffffffffu, occ);
+      int base = 0;
+      if (lane == 0 && m) base = atomicAdd(&cursor, __popc(m));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      const int pos = base + __popc(m & ((1u << lane) - 1u));
+      if (occ && pos < nnz) {
+        c_ci[rp + pos] = kk;
+        c_v[rp + pos] = vals[s];
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && cursor != nnz) raise_err(a.err, kErrProbe);
+  }
+}
+
+// Heavy rows with a saved column bitmap.  Item (t, wdw): bitmap t of the
+// symbolic bitmap bin (row bm_rows[t]), output ranks [wdw*cap, (wdw+1)*cap).
+template <typename T>
+__global__ void __launch_bounds__(1024, 1)
+    k_num_bitmap(Args a, const int32_t *__restrict__ bm_rows, const int2 *__restrict__ items,
+                 const uint32_t *__restrict__ bitmaps, int words, int cap, const int32_t *__restrict__ c_rp,
+                 int32_t *__restrict__ c_ci, T *__restrict__ c_v) {
+  extern __shared__ __align__(16) unsigned char sm_num_bm[];
+  __shared__ int red[33];
+  T *vals = reinterpret_cast<T *>(sm_num_bm);
+  uint32_t *bm = reinterpret_cast<uint32_t *>(sm_num_bm + (size_t)cap * sizeof(T));
+  int32_t *pre = reinterpret_cast<int32_t *>(bm + words);
+  const int2 item = items[blockIdx.x];
+  const int32_t i = bm_rows[item.x];
+  const int32_t rp = c_rp[i];
+  const int32_t nnz = c_rp[i + 1] - rp;
+  const int32_t lo = item.y * cap;
+  const int32_t hi = min(nnz, lo + cap);
+  const uint32_t *src = bitmaps + (size_t)item.x * words;
+  const int per = (words + blockDim.x - 1) / blockDim.x;
+  const int w0 = threadIdx.x * per, w1 = min(words, w0 + per);
+  int local = 0;
+  for (int w = w0; w < w1; ++w) {
+    const uint32_t b = src[w];
+    bm[w] = b;
+    local += __popc(b);
+  }
+  int tot;
+  int run = block_excl_scan(local, red, &tot);
+  for (int w = w0; w < w1; ++w) {
+    pre[w] = run;
+    run += __popc(bm[w]);
+  }
+  for (int r = threadIdx.x; r < hi - lo; r += blockDim.x) vals[r] = T(0);
+  __syncthreads();
+  const int G = a.G;
+  for_row_products<kUN, true, T>(a.arp[i], a.arp[i + 1], threadIdx.x / G, blockDim.x / G, threadIdx.x & (G - 1), G,
+                                 a.aci, (const T *)a.av, a.brp, a.bci, (const T *)a.bv, (int32_t)a.k, a.err,
+                                 [&](int32_t c, T av, T bv) {
+                                   const uint32_t word = bm[c >> 5];
+                                   const int r = pre[c >> 5] + __popc(word & ((1u << (c & 31)) - 1u));
+                                   if (r >= lo && r < hi) {
+                                     if (!Val<T>::acc_shared(vals + (r - lo), av, bv)) raise_err(a.err, kErrRetry);
+                                   }
+                                 });
+  __syncthreads();
+  // store ranks [lo, hi): each thread expands the set bits of its words
+  for (int w = threadIdx.x; w < words; w += blockDim.x) {
+    uint32_t b = bm[w];
+    int r = pre[w];
+    if (r >= hi || r + __popc(b) <= lo) continue;
+    while (b) {
+      const int bit = __ffs(b) - 1;
+      b &= b - 1u;
+      if (r >= lo && r < hi) {
+        c_ci[rp + r] = w * 32 + bit;
+        c_v[rp + r] = vals[r - lo];
+      }
+      ++r;
+    }
+  }
+  if (threadIdx.x == 0 && tot != nnz) raise_err(a.err, kErrProbe);
+}
+
+// Heavy rows without bitmaps: block b owns table b (S slots of keys and
+// values in global memory) and walks rows b, b+gridDim.x, ...  Sorted
+// output ranks the row's columns window by window with a shared-memory
+// bitmap of win_words words.
+template <typename T>
+__global__ void __launch_bounds__(1024, 1)
+    k_num_global(Args a, const int32_t *__restrict__ rows, int64_t nrows, int32_t *__restrict__ keys_all,
+                 T *__restrict__ vals_all, int64_t S, const int32_t *__restrict__ c_rp, int32_t *__restrict__ c_ci,
+                 T *__restrict__ c_v, int sorted, int win_words) {
+  extern __shared__ __align__(16) unsigned char sm_num_gl[];
+  __shared__ int red[33];
+  __shared__ int cursor;
+  int32_t *keys = keys_all + (size_t)blockIdx.x * S;
+  T *vals = vals_all + (size_t)blockIdx.x * S;
+  const uint32_t mask = (uint32_t)(S - 1);
+  const int G = a.G;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t r = blockIdx.x; r < nrows; r += gridDim.x) {
+    for (int64_t s = threadIdx.x; s < S; s += blockDim.x) {
+      keys[s] = kEmpty;
+      vals[s] = T(0);
+    }
+    if (threadIdx.x == 0) cursor = 0;
+    __syncthreads();
+    const int32_t i = rows[r];
+    for_row_products<kUN, true, T>(a.arp[i], a.arp[i + 1], threadIdx.x / G, blockDim.x / G, threadIdx.x & (G - 1),
+                                   G, a.aci, (const T *)a.av, a.brp, a.bci, (const T *)a.bv, (int32_t)a.k, a.err,
+                                   [&](int32_t c, T av, T bv) { insert_acc<T, true>(keys, vals, mask, c, av, bv, a.err); });
+    __syncthreads();
+    const int32_t rp = c_rp[i];
+    const int32_t nnz = c_rp[i + 1] - rp;
+    if (!sorted) {
+      for (int64_t s0 = (int64_t)warp * 32; s0 < S; s0 += (int64_t)nw * 32) {
+        const int64_t s = s0 + lane;
+        const int32_t kk = keys[s];
+        const bool occ = kk != kEmpty;
+        const unsigned m = __ballot_sync(0xffffffffu, occ);
+        int base = 0;
+        if (lane == 0 && m) base = atomicAdd(&cursor, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        const int pos = base + __popc(m & ((1u << lane) - 1u));
+        if (occ && pos < nnz) {
+          c_ci[rp + pos] = kk;
+          c_v[rp + pos] = vals[s];
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0 && cursor != nnz) raise_err(a.err, kErrProbe);
+    } else {
+      uint32_t *bm = reinterpret_cast<uint32_t *>(sm_num_gl);
+      int32_t *pre = reinterpret_cast<int32_t *>(bm + win_words);
+      const int64_t wcols = (int64_t)win_words * 32;
+      int base = 0;
+      for (int64_t c0 = 0; c0 < a.k; c0 += wcols) {
+        for (int w = threadIdx.x; w < win_words; w += blockDim.x) bm[w] = 0u;
+        __syncthreads();
+        for (int64_t s = threadIdx.x; s < S; s += blockDim.x) {
+          const int32_t kk = keys[s];
+          if (kk != kEmpty && kk >= c0 && kk < c0 + wcols) {
+            const int32_t o = (int32_t)(kk - c0);
+            atomicOr(bm + (o >> 5), 1u << (o & 31));
+          }
+        }
+        __syncthreads();
+        const int per = (win_words + blockDim.x - 1) / blockDim.x;
+        const int w0 = threadIdx.x * per, w1 = min(win_words, w0 + per);
+        int local = 0;
+        for (int w = w0; w < w1; ++w) local += __popc(bm[w]);
+        int tot;
+        int run = block_excl_scan(local, red, &tot);
+        for (int w = w0; w < w1; ++w) {
+          pre[w] = run;
+          run += __popc(bm[w]);
+        }
+        __syncthreads();
+        for (int64_t s = threadIdx.x; s < S; s += blockDim.x) {
+          const int32_t kk = keys[s];
+          if (kk != kEmpty && kk >= c0 && kk < c0 + wcols) {
+            const int32_t o = (int32_t)(kk - c0);
+            const int rr = base + pre[o >> 5] + __popc(bm[o >> 5] & ((1u << (o & 31)) - 1u));
+            if (rr < nnz) {
+              c_ci[rp + rr] = kk;
+              c_v[rp + rr] = vals[s];
+            }
+          }
+        }
+        base += tot;
+        __syncthreads();
+      }
+      if (threadIdx.x == 0 && base != nnz) raise_err(a.err, kErrProbe);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <typename K>
+static cudaError_t prep_num(K kernel, size_t smem) {
+  if (smem > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaSuccess;
+}
+
+template <typename T, int S>
+static cudaError_t num_warp(spgemm_plan_s *p, const Args &a, const int32_t *rows, int64_t n, const int32_t *c_rp,
+                            int32_t *c_ci, T *c_v) {
+  const size_t smem = (size_t)kWarpsPerBlock * S * (sizeof(int32_t) + sizeof(T));
+  cudaError_t e = prep_num(k_num_warp<T, S>, smem);
+  if (e != cudaSuccess) return e;
+  const int64_t blocks = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  {
+    KernelScope ks(p, "num_warp_" + std::to_string(S));
+    k_num_warp<T, S><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, p->stream>>>(
+        a, rows, n, c_rp, c_ci, c_v, (p->flags & SPGEMM_SORTED) ? 1 : 0);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T, int S>
+static cudaError_t num_block(spgemm_plan_s *p, const Args &a, const int32_t *rows, int64_t n, int threads,
+                             const int32_t *c_rp, int32_t *c_ci, T *c_v) {
+  size_t smem = (size_t)S * (sizeof(int32_t) + sizeof(T));
+  int mode = 0;
+  if (p->flags & SPGEMM_SORTED) {
+    const size_t extra = (size_t)p->bm_words * 8;
+    if (p->k <= kBitmapMaxCols && smem + extra <= (size_t)max_smem_per_block()) {
+      mode = 2;
+      smem += extra;
+    } else {
+      mode = 1;
+    }
+  }
+  cudaError_t e = prep_num(k_num_block<T, S>, smem);
+  if (e != cudaSuccess) return e;
+  {
+    KernelScope ks(p, "num_block_" + std::to_string(S));
+    k_num_block<T, S><<<(unsigned)n, threads, smem, p->stream>>>(a, rows, c_rp, c_ci, c_v, mode, p->bm_words);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_numeric_t(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_ci, T *c_v) {
+  Args a{p->m, p->n, p->k, p->arp, p->aci, p->brp, p->bci, p->av, p->bv, p->G, &p->dc->err};
+  cudaError_t e = cudaSuccess;
+  for (int b = 0; b < kNumNumBins && e == cudaSuccess; ++b) {
+    const int64_t n = p->num_count[b];
+    if (n == 0) continue;
+    const int32_t *rows = p->perm2 + p->num_off[b];
+    const BinCfg &c = kNumBins[b];
+    switch (b) {
+      case 0: e = num_warp<T, 64>(p, a, rows, n, c_rp, c_ci, c_v); break;
+      case 1: e = num_warp<T, 128>(p, a, rows, n, c_rp, c_ci, c_v); break;
+      case 2: e = num_warp<T, 256>(p, a, rows, n, c_rp, c_ci, c_v); break;
+      case 3: e = num_warp<T, 512>(p, a, rows, n, c_rp, c_ci, c_v); break;
+      case 4: e = num_warp<T, 1024>(p, a, rows, n, c_rp, c_ci, c_v); break;
+      case 5: e = num_block<T, 2048>(p, a, rows, n, c.threads, c_rp, c_ci, c_v); break;
+      case 6: e = num_block<T, 4096>(p, a, rows, n, c.threads, c_rp, c_ci, c_v); break;
+      case 7: e = num_block<T, 8192>(p, a, rows, n, c.threads, c_rp, c_ci, c_v); break;
+      case 8: e = num_block<T, 16384>(p, a, rows, n, c.threads, c_rp, c_ci, c_v); break;
+      case kNumBitmapBin: {
+        const size_t smem = (size_t)p->bm_cap * sizeof(T) + (size_t)p->bm_words * 8;
+        e = prep_num(k_num_bitmap<T>, smem);
+        if (e != cudaSuccess) break;
+        {
+          KernelScope ks(p, "num_bitmap");
+          k_num_bitmap<T><<<(unsigned)n, c.threads, smem, p->stream>>>(a, p->perm + p->sym_off[kSymBitmapBin],
+                                                                       p->bm_items, p->bitmaps, p->bm_words,
+                                                                       (int)p->bm_cap, c_rp, c_ci, c_v);
+        }
+        e = cudaGetLastError();
+        break;
+      }
+      case kNumGlobalBin: {
+        const int win_words = 8192;  // 2^18 columns per window: 32 KB bitmap + 32 KB prefix
+        const size_t smem = (p->flags & SPGEMM_SORTED) ? (size_t)win_words * 8 : 0;
+        e = prep_num(k_num_global<T>, smem);
+        if (e != cudaSuccess) break;
+        int32_t *keys = (int32_t *)p->gtab;
+        T *vals = reinterpret_cast<T *>((char *)p->gtab + (size_t)p->gtab_blocks * p->gtab_slots * sizeof(int32_t));
+        {
+          KernelScope ks(p, "num_global");
+          k_num_global<T><<<(unsigned)p->gtab_blocks, c.threads, smem, p->stream>>>(
+              a, rows, n, keys, vals, p->gtab_slots, c_rp, c_ci, c_v, (p->flags & SPGEMM_SORTED) ? 1 : 0, win_words);
+        }
+        e = cudaGetLastError();
+        break;
+      }
+      default: break;
+    }
+  }
+  return e;
+}
+
+}  // namespace sg

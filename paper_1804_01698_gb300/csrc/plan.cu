@@ -1,0 +1,814 @@
+// Host side of the GB300 hash SpGEMM: the C ABI of include/spgemm.h, the
+// plan object, and the small kernels around the two phases:
+//
+//   k_row_flop      flop[i] = sum over stored a_ik of nnz(b_k*)
+//                   (paper Sec. 4.1, Fig. "RowsToThreads", step 1), plus
+//                   the symbolic bin of every row and the input checks
+//   k_bin_scatter   rows grouped by bin (the GPU form of step 2 of
+//                   "RowsToThreads": instead of equal-flop row ranges per
+//                   thread, rows of similar size share one kernel)
+//   k_scan_*        exclusive scan of nnz(c_i*) into C's row_ptr
+//                   (Fig. "Hash_SpGEMM": rpts_C is allocated and filled
+//                   between the symbolic and the numeric phase)
+//   k_num_classify  numeric bins from the exact row counts
+//   k_bm_items_*    work items (row, rank window) of heavy bitmap rows
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace sg {
+
+const BinCfg kSymBins[kNumSymBins] = {
+    {kWarp, 64, kWarpsPerBlock * 32, 32},      {kWarp, 128, kWarpsPerBlock * 32, 64},
+    {kWarp, 256, kWarpsPerBlock * 32, 128},    {kWarp, 512, kWarpsPerBlock * 32, 256},
+    {kWarp, 1024, kWarpsPerBlock * 32, 512},   {kBlock, 2048, 256, 1536},
+    {kBlock, 4096, 512, 3072},                 {kBlock, 8192, 1024, 6144},
+    {kBlock, 16384, 1024, 12288},              {kBlock, 32768, 1024, 24576},
+    {kBitmap, 0, 1024, INT64_MAX},             {kGlobal, 0, 1024, INT64_MAX}};
+
+const BinCfg kNumBins[kNumNumBins] = {
+    {kWarp, 64, kWarpsPerBlock * 32, 32},      {kWarp, 128, kWarpsPerBlock * 32, 64},
+    {kWarp, 256, kWarpsPerBlock * 32, 128},    {kWarp, 512, kWarpsPerBlock * 32, 256},
+    {kWarp, 1024, kWarpsPerBlock * 32, 512},   {kBlock, 2048, 256, 1536},
+    {kBlock, 4096, 512, 3072},                 {kBlock, 8192, 1024, 6144},
+    {kBlock, 16384, 1024, 12288},              {kBitmap, 0, 1024, INT64_MAX},
+    {kGlobal, 0, 1024, INT64_MAX}};
+
+cudaError_t launch_numeric_f64(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_ci, void *c_v);
+cudaError_t launch_numeric_f32(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_ci, void *c_v);
+cudaError_t launch_numeric_i64(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_ci, void *c_v);
+
+__constant__ int64_t c_hash_caps[9] = {32, 64, 128, 256, 512, 1536, 3072, 6144, 12288};
+
+__device__ __forceinline__ int hash_bin_of(int64_t b) {
+#pragma unroll
+  for (int t = 0; t < 9; ++t)
+    if (b <= c_hash_caps[t]) return t;
+  return 9;
+}
+
+__device__ __forceinline__ int sym_bin_of(int64_t b, bool bitmap_ok) {
+  if (b <= 0) return 255;
+  const int t = hash_bin_of(b);
+  if (t < 9) return t;
+  if (bitmap_ok) return kSymBitmapBin;
+  if (b <= kBlockSymMax) return 9;
+  return kSymGlobalBin;
+}
+
+__device__ __forceinline__ int num_bin_of(int64_t nnz) {
+  if (nnz <= 0) return 255;
+  const int t = hash_bin_of(nnz);
+  return t < 9 ? t : kNumGlobalBin;
+}
+
+// 8 lanes per row of A, 32 rows per 256-thread block.
+__global__ void __launch_bounds__(256)
+    k_row_flop(Args a, int64_t nnz_a, int64_t nnz_b, int bitmap_ok, int64_t *__restrict__ flop,
+               uint8_t *__restrict__ rbin, int32_t *__restrict__ nnz_row, DevCounters *dc) {
+  __shared__ unsigned int hist[kNumSymBins];
+  __shared__ unsigned long long hflop[kNumSymBins];
+  __shared__ unsigned long long s_tot, s_max, s_maxg;
+  if (threadIdx.x < kNumSymBins) {
+    hist[threadIdx.x] = 0;
+    hflop[threadIdx.x] = 0;
+  }
+  if (threadIdx.x == 0) s_tot = s_max = s_maxg = 0;
+  __syncthreads();
+  const int sub = threadIdx.x & 7;
+  const int64_t row = (int64_t)blockIdx.x * 32 + (threadIdx.x >> 3);
+  int64_t f = 0;
+  if (row < a.m) {
+    int64_t r0 = a.arp[row], r1 = a.arp[row + 1];
+    if (!(0 <= r0 && r0 <= r1 && r1 <= nnz_a)) {
+      if (sub == 0) raise_err(a.err, kErrCsr);
+      r0 = r1 = 0;
+    }
+    for (int64_t j = r0 + sub; j < r1; j += 8) {
+      const int32_t kk = a.aci[j];
+      if ((uint64_t)(int64_t)kk >= (uint64_t)a.n) {
+        raise_err(a.err, kErrCsr);
+        continue;
+      }
+      const int64_t b0 = a.brp[kk], b1 = a.brp[kk + 1];
+      if (!(0 <= b0 && b0 <= b1 && b1 <= nnz_b)) {
+        raise_err(a.err, kErrCsr);
+        continue;
+      }
+      f += b1 - b0;
+    }
+  }
+  f += __shfl_xor_sync(0xffffffffu, f, 4);
+  f += __shfl_xor_sync(0xffffffffu, f, 2);
+  f += __shfl_xor_sync(0xffffffffu, f, 1);
+  if (sub == 0 && row < a.m) {
+    flop[row] = f;
+    const int64_t bound = f < a.k ? f : a.k;
+    const int bin = sym_bin_of(bound, bitmap_ok != 0);
+    rbin[row] = (uint8_t)bin;
+    if (bin == 255) {
+      nnz_row[row] = 0;
+    } else {
+      atomicAdd(&hist[bin], 1u);
+      atomicAdd(&hflop[bin], (unsigned long long)f);
+    }
+    if (bin == kSymGlobalBin) atomicMax(&s_maxg, (unsigned long long)bound);
+    atomicAdd(&s_tot, (unsigned long long)f);
+    atomicMax(&s_max, (unsigned long long)f);
+  }
+  __syncthreads();
+  if (threadIdx.x < kNumSymBins && hist[threadIdx.x]) {
+    atomicAdd(&dc->sym_count[threadIdx.x], hist[threadIdx.x]);
+    atomicAdd(&dc->sym_flop[threadIdx.x], hflop[threadIdx.x]);
+  }
+  if (threadIdx.x == 0) {
+    if (s_tot) atomicAdd(&dc->total_flop, s_tot);
+    atomicMax(&dc->max_flop, s_max);
+    atomicMax(&dc->max_bound_global, s_maxg);
+  }
+}
+
+struct Offsets {
+  long long v[16];
+};
+
+// Rows i with bin_of[i] != 255 go to perm[off[bin] + arbitrary rank].
+__global__ void __launch_bounds__(256)
+    k_bin_scatter(const uint8_t *__restrict__ bin_of, int64_t m, Offsets off, unsigned long long *cursor,
+                  int32_t *__restrict__ perm, int nbins) {
+  __shared__ unsigned int hist[16];
+  __shared__ unsigned long long base[16];
+  if (threadIdx.x < 16) hist[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = i < m ? bin_of[i] : 255;
+  unsigned int local = 0;
+  if (b < nbins) local = atomicAdd(&hist[b], 1u);
+  __syncthreads();
+  if (threadIdx.x < nbins && hist[threadIdx.x]) base[threadIdx.x] = atomicAdd(&cursor[threadIdx.x], hist[threadIdx.x]);
+  __syncthreads();
+  if (b < nbins) perm[off.v[b] + (long long)base[b] + local] = (int32_t)i;
+}
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 4;
+constexpr int kScanTile = kScanThreads * kScanPer;
+
+__global__ void __launch_bounds__(kScanThreads)
+    k_scan_reduce(const int32_t *__restrict__ x, int64_t m, long long *__restrict__ partial) {
+  __shared__ long long red[33];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+  long long s = 0;
+#pragma unroll
+  for (int u = 0; u < kScanPer; ++u)
+    if (base + u < m) s += x[base + u];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_spine(long long *partial, int64_t nblk, DevCounters *dc) {
+  __shared__ long long red[33];
+  long long carry = 0;
+  for (int64_t c0 = 0; c0 < nblk; c0 += kScanThreads) {
+    const int64_t t = c0 + threadIdx.x;
+    const long long v = t < nblk ? partial[t] : 0;
+    long long tot;
+    const long long ex = block_excl_scan(v, red, &tot);
+    if (t < nblk) partial[t] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) {
+    dc->nnz_c = (unsigned long long)carry;
+    if (carry > 2147483647LL) raise_err(&dc->err, kErrOverflow);
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+    k_scan_apply(const int32_t *__restrict__ x, int64_t m, const long long *__restrict__ partial,
+                 int32_t *__restrict__ out) {
+  __shared__ long long red[33];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+  int32_t v[kScanPer];
+  long long s = 0;
+#pragma unroll
+  for (int u = 0; u < kScanPer; ++u) {
+    v[u] = base + u < m ? x[base + u] : 0;
+    s += v[u];
+  }
+  long long tot;
+  long long run = partial[blockIdx.x] + block_excl_scan(s, red, &tot);
+#pragma unroll
+  for (int u = 0; u < kScanPer; ++u) {
+    if (base + u < m) out[base + u] = (int32_t)run;
+    run += v[u];
+    if (base + u == m - 1) out[m] = (int32_t)run;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+    k_num_classify(const int32_t *__restrict__ nnz_row, const uint8_t *__restrict__ rbin,
+                   const int64_t *__restrict__ flop, int64_t m, uint8_t *__restrict__ rbin2, DevCounters *dc) {
+  __shared__ unsigned int hist[kNumNumBins];
+  __shared__ unsigned long long hflop[kNumNumBins];
+  __shared__ unsigned long long s_maxg;
+  if (threadIdx.x < kNumNumBins) {
+    hist[threadIdx.x] = 0;
+    hflop[threadIdx.x] = 0;
+  }
+  if (threadIdx.x == 0) s_maxg = 0;
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) {
+    int b = 255;
+    if (rbin[i] != kSymBitmapBin) {
+      const int32_t z = nnz_row[i];
+      b = num_bin_of(z);
+      if (b == kNumGlobalBin) atomicMax(&s_maxg, (unsigned long long)z);
+    } else if (nnz_row[i] > 0) {
+      atomicAdd(&hflop[kNumBitmapBin], (unsigned long long)flop[i]);  // rows of the bitmap items
+    }
+    rbin2[i] = (uint8_t)b;
+    if (b != 255) {
+      atomicAdd(&hist[b], 1u);
+      atomicAdd(&hflop[b], (unsigned long long)flop[i]);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < kNumNumBins && hist[threadIdx.x]) atomicAdd(&dc->num_count[threadIdx.x], hist[threadIdx.x]);
+  if (threadIdx.x < kNumNumBins && hflop[threadIdx.x]) atomicAdd(&dc->num_flop[threadIdx.x], hflop[threadIdx.x]);
+  if (threadIdx.x == 0 && s_maxg) atomicMax(&dc->max_nnz_global, s_maxg);
+}
+
+__global__ void __launch_bounds__(256)
+    k_bm_items_count(const int32_t *__restrict__ rows, int64_t n, const int32_t *__restrict__ nnz_row, int cap,
+                     DevCounters *dc) {
+  __shared__ long long red[33];
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  long long w = 0;
+  if (t < n) w = (nnz_row[rows[t]] + (long long)cap - 1) / cap;
+  w = block_sum(w, red);
+  if (threadIdx.x == 0 && w) atomicAdd(&dc->bm_items, (unsigned long long)w);
+}
+
+__global__ void __launch_bounds__(256)
+    k_bm_items_fill(const int32_t *__restrict__ rows, int64_t n, const int32_t *__restrict__ nnz_row, int cap,
+                    DevCounters *dc, int2 *__restrict__ items) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int w = (int)((nnz_row[rows[t]] + (long long)cap - 1) / cap);
+  if (w == 0) return;
+  const unsigned long long base = atomicAdd(&dc->bm_cursor, (unsigned long long)w);
+  for (int q = 0; q < w; ++q) items[base + q] = make_int2((int)t, q);
+}
+
+// ---------------------------------------------------------------------------
+int max_smem_per_block() {
+  static int cached[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 48 * 1024;
+  if (cached[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || v <= 0)
+      v = 48 * 1024;
+    cached[dev] = v;
+  }
+  return cached[dev];
+}
+
+static int sm_count() {
+  static int cached[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 1;
+  if (cached[dev] == 0) {
+    int v = 1;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = v > 0 ? v : 1;
+  }
+  return cached[dev];
+}
+
+static size_t value_size(int dtype) { return dtype == SPGEMM_F32 ? 4 : 8; }
+
+// Values per numeric bitmap window: what shared memory holds after the
+// bitmap and its prefix counts (a little is kept for static shared data).
+int64_t bitmap_capacity(int dtype, int bm_words) {
+  const int64_t avail = (int64_t)max_smem_per_block() - 1024 - (int64_t)bm_words * 8;
+  int64_t cap = avail / (int64_t)value_size(dtype);
+  cap = (cap / 256) * 256;
+  return cap > 0 ? cap : 0;
+}
+
+}  // namespace sg
+
+using namespace sg;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail_cuda(cudaError_t e, const char *where) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return SPGEMM_ERR_OUT_OF_MEMORY;
+  return SPGEMM_ERR_DEVICE;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+std::mutex g_pool_mu;
+bool g_pool_done[64];
+
+// Keep freed workspace in the device's default memory pool instead of
+// returning it to the driver, so repeated plans do not pay for allocation.
+void keep_pool(int dev) {
+  std::lock_guard<std::mutex> g(g_pool_mu);
+  if (dev < 0 || dev >= 64 || g_pool_done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  g_pool_done[dev] = true;
+}
+
+int read_counters(spgemm_plan_s *p) {
+  cudaError_t e = cudaMemcpyAsync(p->hc, p->dc, sizeof(DevCounters), cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return fail_cuda(e, "reading plan counters");
+  const unsigned err = p->hc->err;
+  if (err & kErrCsr) {
+    g_last_error = "input CSR has an index out of range or a malformed row_ptr";
+    return SPGEMM_ERR_INVALID_CSR;
+  }
+  if (err & kErrOverflow) {
+    g_last_error = "nnz(C) exceeds int32 indexing";
+    return SPGEMM_ERR_INDEX_OVERFLOW;
+  }
+  if (err) {
+    g_last_error = "device-side check failed (hash probe or atomic retry bound)";
+    return SPGEMM_ERR_DEVICE;
+  }
+  return SPGEMM_OK;
+}
+
+int64_t pow2_above(int64_t x) {  // smallest power of two strictly greater than x
+  int64_t s = 1;
+  while (s <= x) s <<= 1;
+  return s;
+}
+
+int valid_csr_desc(const spgemm_csr *c) {
+  if (!c) return 0;
+  if (c->nrows < 0 || c->ncols < 0 || c->nnz < 0) return 0;
+  if (c->nrows > INT32_MAX || c->ncols > INT32_MAX || c->nnz > INT32_MAX) return 0;
+  if (!c->row_ptr) return 0;
+  if (c->nnz > 0 && (!c->col_idx || !c->vals)) return 0;
+  return 1;
+}
+
+void free_events(spgemm_plan_s *p) {
+  for (auto &t : p->timed) {
+    if (t.start) cudaEventDestroy(t.start);
+    if (t.stop) cudaEventDestroy(t.stop);
+  }
+  p->timed.clear();
+}
+
+void free_ws(spgemm_plan_s *p) {
+  free_events(p);
+  if (p->ws_fixed) cudaFreeAsync(p->ws_fixed, p->stream);
+  if (p->bitmaps) cudaFreeAsync(p->bitmaps, p->stream);
+  if (p->bm_items) cudaFreeAsync(p->bm_items, p->stream);
+  if (p->gtab) cudaFreeAsync(p->gtab, p->stream);
+  p->ws_fixed = nullptr;
+  p->bitmaps = nullptr;
+  p->bm_items = nullptr;
+  p->gtab = nullptr;
+}
+
+int alloc_gtab(spgemm_plan_s *p, int64_t slots, size_t entry_bytes, int64_t rows) {
+  // Blocks that work on heavy rows at once: two per SM, fewer when the
+  // tables would pass 4 GiB.
+  int64_t blocks = std::min<int64_t>(rows, 2 * (int64_t)sm_count());
+  const size_t per = (size_t)slots * entry_bytes;
+  const size_t budget = (size_t)4 << 30;
+  while (blocks > 1 && per * (size_t)blocks > budget) blocks >>= 1;
+  const size_t need = per * (size_t)blocks;
+  if (p->gtab && p->gtab_bytes >= need) {
+    p->gtab_slots = slots;
+    p->gtab_blocks = blocks;
+    return SPGEMM_OK;
+  }
+  if (p->gtab) cudaFreeAsync(p->gtab, p->stream);
+  p->gtab = nullptr;
+  cudaError_t e = cudaMallocAsync(&p->gtab, need, p->stream);
+  if (e != cudaSuccess) {
+    p->gtab = nullptr;
+    return fail_cuda(e, "allocating heavy-row hash tables");
+  }
+  p->gtab_bytes = need;
+  p->gtab_slots = slots;
+  p->gtab_blocks = blocks;
+  return SPGEMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *spgemm_status_string(int status) {
+  switch (status) {
+    case SPGEMM_OK: return "ok";
+    case SPGEMM_ERR_INVALID_ARGUMENT: return "invalid argument";
+    case SPGEMM_ERR_INVALID_CSR: return "invalid CSR input";
+    case SPGEMM_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case SPGEMM_ERR_INDEX_OVERFLOW: return "index overflow (nnz(C) > 2^31-1)";
+    case SPGEMM_ERR_BAD_STATE: return "call out of order";
+    case SPGEMM_ERR_DEVICE: return "device error";
+    case SPGEMM_ERR_TIMEOUT: return "timeout";
+    default: return "unknown status";
+  }
+}
+
+const char *spgemm_last_error(void) { return g_last_error.c_str(); }
+
+int spgemm_plan_create(spgemm_plan_t *out, const spgemm_csr *A, const spgemm_csr *B, int dtype, unsigned flags,
+                       void *stream) {
+  if (!out) return SPGEMM_ERR_INVALID_ARGUMENT;
+  *out = nullptr;
+  g_last_error.clear();
+  if (!valid_csr_desc(A) || !valid_csr_desc(B) || A->ncols != B->nrows) return SPGEMM_ERR_INVALID_ARGUMENT;
+  if (dtype != SPGEMM_I64 && dtype != SPGEMM_F32 && dtype != SPGEMM_F64) return SPGEMM_ERR_INVALID_ARGUMENT;
+  if (flags & ~(SPGEMM_SORTED | SPGEMM_VALIDATE | SPGEMM_TIMING)) return SPGEMM_ERR_INVALID_ARGUMENT;
+
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail_cuda(e, "cudaGetDevice");
+  keep_pool(dev);
+
+  spgemm_plan_s *p = new (std::nothrow) spgemm_plan_s();
+  if (!p) return SPGEMM_ERR_OUT_OF_MEMORY;
+  p->hc = new (std::nothrow) DevCounters();
+  if (!p->hc) {
+    delete p;
+    return SPGEMM_ERR_OUT_OF_MEMORY;
+  }
+  p->m = A->nrows;
+  p->n = A->ncols;
+  p->k = B->ncols;
+  p->nnz_a = A->nnz;
+  p->nnz_b = B->nnz;
+  p->arp = A->row_ptr;
+  p->aci = A->col_idx;
+  p->brp = B->row_ptr;
+  p->bci = B->col_idx;
+  p->av = A->vals;
+  p->bv = B->vals;
+  p->dtype = dtype;
+  p->flags = flags;
+  p->stream = (cudaStream_t)stream;
+  p->device = dev;
+  const double avg_b = p->n > 0 ? (double)p->nnz_b / (double)p->n : 0.0;
+  p->G = avg_b >= 24 ? 32 : avg_b >= 12 ? 16 : avg_b >= 6 ? 8 : 4;
+  p->bitmap_ok = p->k <= kBitmapMaxCols;
+  p->bm_words = (int)((p->k + 31) / 32);
+  p->bm_cap = bitmap_capacity(dtype, p->bm_words);
+  if (p->bitmap_ok && p->bm_cap < 256) p->bitmap_ok = false;
+
+  // fixed workspace: counters, then per-row arrays
+  const int64_t m = p->m;
+  const int64_t nblk = (m + kScanTile - 1) / kScanTile + 1;
+  size_t off = 0;
+  const size_t o_dc = off;
+  off = align_up(off + sizeof(DevCounters), 256);
+  const size_t o_flop = off;
+  off = align_up(off + (size_t)m * 8, 256);
+  const size_t o_rbin = off;
+  off = align_up(off + (size_t)m, 256);
+  const size_t o_perm = off;
+  off = align_up(off + (size_t)m * 4, 256);
+  const size_t o_nnz = off;
+  off = align_up(off + (size_t)m * 4, 256);
+  const size_t o_rbin2 = off;
+  off = align_up(off + (size_t)m, 256);
+  const size_t o_perm2 = off;
+  off = align_up(off + (size_t)m * 4, 256);
+  const size_t o_part = off;
+  off = align_up(off + (size_t)nblk * 8, 256);
+  e = cudaMallocAsync(&p->ws_fixed, off, p->stream);
+  if (e != cudaSuccess) {
+    p->ws_fixed = nullptr;
+    int rc = fail_cuda(e, "allocating plan workspace");
+    delete p->hc;
+    delete p;
+    return rc;
+  }
+  p->ws_fixed_bytes = off;
+  char *base = (char *)p->ws_fixed;
+  p->dc = (DevCounters *)(base + o_dc);
+  p->flop = (int64_t *)(base + o_flop);
+  p->rbin = (uint8_t *)(base + o_rbin);
+  p->perm = (int32_t *)(base + o_perm);
+  p->nnz_row = (int32_t *)(base + o_nnz);
+  p->rbin2 = (uint8_t *)(base + o_rbin2);
+  p->perm2 = (int32_t *)(base + o_perm2);
+  (void)o_part;
+
+  int rc = SPGEMM_OK;
+  e = cudaMemsetAsync(p->dc, 0, sizeof(DevCounters), p->stream);
+  if (e == cudaSuccess && m > 0) {
+    Args a{p->m, p->n, p->k, p->arp, p->aci, p->brp, p->bci, p->av, p->bv, p->G, &p->dc->err};
+    {
+      KernelScope ks(p, "row_flop");
+      k_row_flop<<<(unsigned)((m + 31) / 32), 256, 0, p->stream>>>(a, p->nnz_a, p->nnz_b, p->bitmap_ok ? 1 : 0,
+                                                                    p->flop, p->rbin, p->nnz_row, p->dc);
+    }
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) rc = fail_cuda(e, "row flop pass");
+  if (rc == SPGEMM_OK) rc = read_counters(p);
+  if (rc == SPGEMM_OK) {
+    p->total_flop = (int64_t)p->hc->total_flop;
+    p->max_flop = (int64_t)p->hc->max_flop;
+    p->sym_off[0] = 0;
+    for (int b = 0; b < kNumSymBins; ++b) {
+      p->sym_flop[b] = (int64_t)p->hc->sym_flop[b];
+      p->sym_count[b] = (int64_t)p->hc->sym_count[b];
+      p->sym_off[b + 1] = p->sym_off[b] + p->sym_count[b];
+    }
+    if (p->sym_count[kSymBitmapBin] > 0) {
+      p->bitmaps_bytes = (size_t)p->sym_count[kSymBitmapBin] * p->bm_words * 4;
+      e = cudaMallocAsync((void **)&p->bitmaps, p->bitmaps_bytes, p->stream);
+      if (e != cudaSuccess) {
+        p->bitmaps = nullptr;
+        rc = fail_cuda(e, "allocating row bitmaps");
+      }
+    }
+    if (rc == SPGEMM_OK && p->sym_count[kSymGlobalBin] > 0)
+      rc = alloc_gtab(p, pow2_above((int64_t)p->hc->max_bound_global), 4, p->sym_count[kSymGlobalBin]);
+    if (rc == SPGEMM_OK && m > 0) {
+      Offsets o{};
+      for (int b = 0; b < kNumSymBins; ++b) o.v[b] = p->sym_off[b];
+      {
+        KernelScope ks(p, "bin_rows_sym");
+        k_bin_scatter<<<(unsigned)((m + 255) / 256), 256, 0, p->stream>>>(p->rbin, m, o, p->dc->sym_cursor,
+                                                                          p->perm, kNumSymBins);
+      }
+      e = cudaGetLastError();
+      if (e != cudaSuccess) rc = fail_cuda(e, "row binning");
+    }
+  }
+  if (rc != SPGEMM_OK) {
+    free_ws(p);
+    delete p->hc;
+    delete p;
+    return rc;
+  }
+  p->state = 0;
+  *out = p;
+  return SPGEMM_OK;
+}
+
+int spgemm_symbolic(spgemm_plan_t p, int32_t *c_row_ptr, int64_t *nnz_c) {
+  if (!p || !c_row_ptr || !nnz_c) return SPGEMM_ERR_INVALID_ARGUMENT;
+  if (p->state != 0) return SPGEMM_ERR_BAD_STATE;
+  g_last_error.clear();
+  cudaError_t e = launch_symbolic(p);
+  if (e != cudaSuccess) return fail_cuda(e, "symbolic kernels");
+  const int64_t m = p->m;
+  if (m == 0) {
+    e = cudaMemsetAsync(c_row_ptr, 0, sizeof(int32_t), p->stream);
+    if (e != cudaSuccess) return fail_cuda(e, "row_ptr");
+  } else {
+    const int64_t nblk = (m + kScanTile - 1) / kScanTile;
+    // partial[] is the last segment of the fixed workspace, after perm2
+    long long *partial = (long long *)((char *)p->perm2 + align_up((size_t)m * 4, 256));
+    {
+      KernelScope ks(p, "scan_reduce");
+      k_scan_reduce<<<(unsigned)nblk, kScanThreads, 0, p->stream>>>(p->nnz_row, m, partial);
+    }
+    {
+      KernelScope ks(p, "scan_spine");
+      k_scan_spine<<<1, kScanThreads, 0, p->stream>>>(partial, nblk, p->dc);
+    }
+    {
+      KernelScope ks(p, "scan_apply");
+      k_scan_apply<<<(unsigned)nblk, kScanThreads, 0, p->stream>>>(p->nnz_row, m, partial, c_row_ptr);
+    }
+    {
+      KernelScope ks(p, "num_classify");
+      k_num_classify<<<(unsigned)((m + 255) / 256), 256, 0, p->stream>>>(p->nnz_row, p->rbin, p->flop, m, p->rbin2,
+                                                                         p->dc);
+    }
+    const int64_t nbm = p->sym_count[kSymBitmapBin];
+    if (nbm > 0) {
+      KernelScope ks(p, "bm_items_count");
+      k_bm_items_count<<<(unsigned)((nbm + 255) / 256), 256, 0, p->stream>>>(
+          p->perm + p->sym_off[kSymBitmapBin], nbm, p->nnz_row, (int)p->bm_cap, p->dc);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail_cuda(e, "row_ptr scan");
+  }
+  int rc = read_counters(p);
+  if (rc != SPGEMM_OK) return rc;
+  p->nnz_c = m > 0 ? (int64_t)p->hc->nnz_c : 0;
+  p->num_off[0] = 0;
+  for (int b = 0; b < kNumNumBins; ++b) {
+    p->num_flop[b] = (int64_t)p->hc->num_flop[b];
+    p->num_count[b] = (int64_t)p->hc->num_count[b];
+    p->num_off[b + 1] = p->num_off[b] + p->num_count[b];
+  }
+  // the bitmap bin holds work items (row, rank window), not rows of perm2
+  p->num_count[kNumBitmapBin] = (int64_t)p->hc->bm_items;
+  *nnz_c = p->nnz_c;
+  p->c_rp = c_row_ptr;
+  p->state = 1;
+  return SPGEMM_OK;
+}
+
+int spgemm_numeric(spgemm_plan_t p, const int32_t *c_row_ptr, int32_t *c_col_idx, void *c_vals) {
+  if (!p || !c_row_ptr) return SPGEMM_ERR_INVALID_ARGUMENT;
+  if (p->state != 1) return SPGEMM_ERR_BAD_STATE;
+  if (p->nnz_c > 0 && (!c_col_idx || !c_vals)) return SPGEMM_ERR_INVALID_ARGUMENT;
+  g_last_error.clear();
+  const int64_t m = p->m;
+  cudaError_t e = cudaSuccess;
+  int rc = SPGEMM_OK;
+  if (p->nnz_c > 0) {
+    const int64_t nitems = p->num_count[kNumBitmapBin];
+    if (nitems > 0) {
+      p->bm_items_bytes = (size_t)nitems * sizeof(int2);
+      e = cudaMallocAsync((void **)&p->bm_items, p->bm_items_bytes, p->stream);
+      if (e != cudaSuccess) {
+        p->bm_items = nullptr;
+        return fail_cuda(e, "allocating bitmap work items");
+      }
+      const int64_t nbm = p->sym_count[kSymBitmapBin];
+      KernelScope ks(p, "bm_items_fill");
+      k_bm_items_fill<<<(unsigned)((nbm + 255) / 256), 256, 0, p->stream>>>(
+          p->perm + p->sym_off[kSymBitmapBin], nbm, p->nnz_row, (int)p->bm_cap, p->dc, p->bm_items);
+    }
+    if (p->num_count[kNumGlobalBin] > 0) {
+      const int64_t slots = pow2_above((int64_t)p->hc->max_nnz_global * 4 / 3);
+      rc = alloc_gtab(p, slots, 4 + value_size(p->dtype), p->num_count[kNumGlobalBin]);
+      if (rc != SPGEMM_OK) return rc;
+    }
+    Offsets o{};
+    for (int b = 0; b < kNumNumBins; ++b) o.v[b] = p->num_off[b];
+    {
+      KernelScope ks(p, "bin_rows_num");
+      k_bin_scatter<<<(unsigned)((m + 255) / 256), 256, 0, p->stream>>>(p->rbin2, m, o, p->dc->num_cursor, p->perm2,
+                                                                        kNumNumBins);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail_cuda(e, "numeric binning");
+    switch (p->dtype) {
+      case SPGEMM_F64: e = launch_numeric_f64(p, c_row_ptr, c_col_idx, c_vals); break;
+      case SPGEMM_F32: e = launch_numeric_f32(p, c_row_ptr, c_col_idx, c_vals); break;
+      default: e = launch_numeric_i64(p, c_row_ptr, c_col_idx, c_vals); break;
+    }
+    if (e != cudaSuccess) return fail_cuda(e, "numeric kernels");
+  }
+  p->state = 2;
+  return SPGEMM_OK;
+}
+
+int spgemm_plan_destroy(spgemm_plan_t p) {
+  if (!p) return SPGEMM_OK;
+  free_ws(p);
+  delete p->hc;
+  delete p;
+  return SPGEMM_OK;
+}
+
+int spgemm_plan_kernel_times(spgemm_plan_t p, spgemm_kernel_time *out, int max_entries, int *n_out) {
+  if (!p || !n_out || (max_entries > 0 && !out)) return SPGEMM_ERR_INVALID_ARGUMENT;
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return fail_cuda(e, "timing sync");
+  std::vector<std::string> names;
+  std::vector<float> ms;
+  std::vector<int> cnt;
+  for (auto &t : p->timed) {
+    float x = 0.f;
+    if (cudaEventElapsedTime(&x, t.start, t.stop) != cudaSuccess) x = 0.f;
+    size_t j = 0;
+    while (j < names.size() && names[j] != t.name) ++j;
+    if (j == names.size()) {
+      names.push_back(t.name);
+      ms.push_back(0.f);
+      cnt.push_back(0);
+    }
+    ms[j] += x;
+    cnt[j] += 1;
+  }
+  *n_out = (int)names.size();
+  for (int j = 0; j < (int)names.size() && j < max_entries; ++j) {
+    std::memset(out[j].name, 0, sizeof(out[j].name));
+    std::strncpy(out[j].name, names[j].c_str(), sizeof(out[j].name) - 1);
+    out[j].ms = ms[j];
+    out[j].launches = cnt[j];
+  }
+  return SPGEMM_OK;
+}
+
+int spgemm_plan_workspace_bytes(spgemm_plan_t p, size_t *bytes) {
+  if (!p || !bytes) return SPGEMM_ERR_INVALID_ARGUMENT;
+  *bytes = p->ws_fixed_bytes + (p->bitmaps ? p->bitmaps_bytes : 0) + (p->bm_items ? p->bm_items_bytes : 0) +
+           (p->gtab ? p->gtab_bytes : 0);
+  return SPGEMM_OK;
+}
+
+int spgemm_plan_stats(spgemm_plan_t p, spgemm_stats *s) {
+  if (!p || !s) return SPGEMM_ERR_INVALID_ARGUMENT;
+  int rc = read_counters(p);
+  std::memset(s, 0, sizeof(*s));
+  s->m = p->m;
+  s->n = p->n;
+  s->k = p->k;
+  s->total_flop = p->total_flop;
+  s->max_row_flop = p->max_flop;
+  s->nnz_c = p->nnz_c;
+  s->n_sym_bins = kNumSymBins;
+  s->n_num_bins = kNumNumBins;
+  for (int b = 0; b < kNumSymBins; ++b) {
+    s->sym_bin_flop[b] = p->sym_flop[b];
+    s->sym_bin_rows[b] = p->sym_count[b];
+    s->sym_bin_table[b] = kSymBins[b].table;
+  }
+  for (int b = 0; b < kNumNumBins; ++b) {
+    s->num_bin_flop[b] = p->num_flop[b];
+    s->num_bin_rows[b] = p->num_count[b];
+    s->num_bin_table[b] = kNumBins[b].table;
+  }
+  size_t ws = 0;
+  spgemm_plan_workspace_bytes(p, &ws);
+  s->workspace_bytes = (int64_t)ws;
+  s->kernel_launches = p->launches;
+  s->state = p->state;
+  return rc;
+}
+
+int spgemm_plan_row_flop(spgemm_plan_t p, int64_t *flop_out) {
+  if (!p || (!flop_out && p->m > 0)) return SPGEMM_ERR_INVALID_ARGUMENT;
+  if (p->m == 0) return SPGEMM_OK;
+  cudaError_t e = cudaMemcpyAsync(flop_out, p->flop, (size_t)p->m * 8, cudaMemcpyDeviceToDevice, p->stream);
+  return e == cudaSuccess ? SPGEMM_OK : fail_cuda(e, "copy flop");
+}
+
+int spgemm_plan_sym_bins(spgemm_plan_t p, int32_t *perm_out, int64_t *offsets) {
+  if (!p || !offsets || (!perm_out && p->m > 0)) return SPGEMM_ERR_INVALID_ARGUMENT;
+  for (int b = 0; b <= kNumSymBins; ++b) offsets[b] = p->sym_off[b];
+  const int64_t n = p->sym_off[kNumSymBins];
+  if (n == 0) return SPGEMM_OK;
+  cudaError_t e = cudaMemcpyAsync(perm_out, p->perm, (size_t)n * 4, cudaMemcpyDeviceToDevice, p->stream);
+  return e == cudaSuccess ? SPGEMM_OK : fail_cuda(e, "copy perm");
+}
+
+int spgemm_plan_row_nnz(spgemm_plan_t p, int32_t *nnz_out) {
+  if (!p || (!nnz_out && p->m > 0)) return SPGEMM_ERR_INVALID_ARGUMENT;
+  if (p->state < 1) return SPGEMM_ERR_BAD_STATE;
+  if (p->m == 0) return SPGEMM_OK;
+  cudaError_t e = cudaMemcpyAsync(nnz_out, p->nnz_row, (size_t)p->m * 4, cudaMemcpyDeviceToDevice, p->stream);
+  return e == cudaSuccess ? SPGEMM_OK : fail_cuda(e, "copy nnz_row");
+}
+
+int spgemm(const spgemm_csr *A, const spgemm_csr *B, int dtype, unsigned flags, void *stream, spgemm_alloc_fn alloc,
+           void *alloc_ctx, int32_t **c_row_ptr, int32_t **c_col_idx, void **c_vals, int64_t *nnz_c) {
+  if (!alloc || !c_row_ptr || !c_col_idx || !c_vals || !nnz_c || !A) return SPGEMM_ERR_INVALID_ARGUMENT;
+  *c_row_ptr = nullptr;
+  *c_col_idx = nullptr;
+  *c_vals = nullptr;
+  *nnz_c = 0;
+  spgemm_plan_t p = nullptr;
+  int rc = spgemm_plan_create(&p, A, B, dtype, flags, stream);
+  if (rc != SPGEMM_OK) return rc;
+  int32_t *rp = (int32_t *)alloc((size_t)(A->nrows + 1) * 4, alloc_ctx);
+  if (!rp) {
+    spgemm_plan_destroy(p);
+    return SPGEMM_ERR_OUT_OF_MEMORY;
+  }
+  rc = spgemm_symbolic(p, rp, nnz_c);
+  if (rc == SPGEMM_OK) {
+    const size_t nz = (size_t)*nnz_c;
+    const size_t vs = dtype == SPGEMM_F32 ? 4 : 8;
+    int32_t *ci = (int32_t *)alloc(nz > 0 ? nz * 4 : 16, alloc_ctx);
+    void *cv = alloc(nz > 0 ? nz * vs : 16, alloc_ctx);
+    if (!ci || !cv) rc = SPGEMM_ERR_OUT_OF_MEMORY;
+    if (rc == SPGEMM_OK) rc = spgemm_numeric(p, rp, ci, cv);
+    *c_col_idx = ci;
+    *c_vals = cv;
+  }
+  *c_row_ptr = rp;
+  spgemm_plan_destroy(p);
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,204 @@
+// Symbolic phase (paper Sec. 4.2.1: "it is enough to insert keys to the
+// hash table"): nnz(c_i*) = number of distinct keys inserted for row i.
+//
+//   k_sym_warp<S>    one warp per row, S-slot table in shared memory
+//   k_sym_block<S>   one block per row, S-slot table in shared memory
+//   k_sym_bitmap     heavy rows, one block per row, a bit per column of B in
+//                    shared memory; the bitmap is saved for the numeric phase
+//   k_sym_global     heavy rows when B has too many columns for a bitmap:
+//                    the hash table lives in global memory (L2)
+//
+// Keys are inserted with atomicCAS on the int32 key (empty = -1) and
+// linear probing (Sec. 4.2.1); an insert that finds -1 claims the slot and
+// counts one new column.
+#include <algorithm>
+#include <string>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace sg {
+
+constexpr int kU = 4;  // B entries loaded ahead per lane
+
+// Inserts key c into an S-slot table; returns 1 when c was new.
+template <bool GLOBAL_MEM>
+__device__ __forceinline__ int insert_key(int32_t *tab, uint32_t mask, int32_t c, uint32_t *err) {
+  uint32_t h = hash_slot(c, mask);
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    const int32_t old = atomicCAS(tab + h, kEmpty, c);
+    if (old == kEmpty) return 1;
+    if (old == c) return 0;
+    h = (h + 1) & mask;
+  }
+  raise_err(err, kErrProbe);
+  return 0;
+}
+
+template <int S>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    k_sym_warp(Args a, const int32_t *__restrict__ rows, int64_t nrows, int32_t *__restrict__ nnz_row) {
+  extern __shared__ int32_t sm_sym_warp[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+  if (w >= nrows) return;  // whole warp leaves; no block barrier below
+  int32_t *tab = sm_sym_warp + warp * S;
+  for (int s = lane; s < S; s += 32) tab[s] = kEmpty;
+  __syncwarp();
+  const int32_t i = rows[w];
+  const int G = a.G;
+  int cnt = 0;
+  for_row_products<kU, false, int32_t>(a.arp[i], a.arp[i + 1], lane / G, 32 / G, lane & (G - 1), G, a.aci,
+                                       (const int32_t *)nullptr, a.brp, a.bci, (const int32_t *)nullptr,
+                                       (int32_t)a.k, a.err,
+                                       [&](int32_t c, int32_t, int32_t) { cnt += insert_key<false>(tab, S - 1, c, a.err); });
+  cnt = warp_sum(cnt);
+  if (lane == 0) nnz_row[i] = cnt;
+}
+
+template <int S>
+__global__ void __launch_bounds__(1024, 1)
+    k_sym_block(Args a, const int32_t *__restrict__ rows, int32_t *__restrict__ nnz_row) {
+  extern __shared__ int32_t sm_sym_block[];
+  __shared__ int red[33];
+  int32_t *tab = sm_sym_block;
+  for (int s = threadIdx.x; s < S; s += blockDim.x) tab[s] = kEmpty;
+  __syncthreads();
+  const int32_t i = rows[blockIdx.x];
+  const int G = a.G;
+  int cnt = 0;
+  for_row_products<kU, false, int32_t>(a.arp[i], a.arp[i + 1], threadIdx.x / G, blockDim.x / G,
+                                       threadIdx.x & (G - 1), G, a.aci, (const int32_t *)nullptr, a.brp, a.bci,
+                                       (const int32_t *)nullptr, (int32_t)a.k, a.err,
+                                       [&](int32_t c, int32_t, int32_t) { cnt += insert_key<false>(tab, S - 1, c, a.err); });
+  cnt = block_sum(cnt, red);
+  if (threadIdx.x == 0) nnz_row[i] = cnt;
+}
+
+// Heavy rows with a bitmap over the columns of B.  words = ceil(k / 32).
+__global__ void __launch_bounds__(1024, 1)
+    k_sym_bitmap(Args a, const int32_t *__restrict__ rows, int32_t *__restrict__ nnz_row,
+                 uint32_t *__restrict__ bitmaps, int words) {
+  extern __shared__ uint32_t sm_bm[];
+  __shared__ int red[33];
+  for (int w = threadIdx.x; w < words; w += blockDim.x) sm_bm[w] = 0u;
+  __syncthreads();
+  const int32_t i = rows[blockIdx.x];
+  const int G = a.G;
+  for_row_products<kU, false, int32_t>(a.arp[i], a.arp[i + 1], threadIdx.x / G, blockDim.x / G,
+                                       threadIdx.x & (G - 1), G, a.aci, (const int32_t *)nullptr, a.brp, a.bci,
+                                       (const int32_t *)nullptr, (int32_t)a.k, a.err,
+                                       [&](int32_t c, int32_t, int32_t) { atomicOr(sm_bm + (c >> 5), 1u << (c & 31)); });
+  __syncthreads();
+  int cnt = 0;
+  uint32_t *out = bitmaps + (size_t)blockIdx.x * words;
+  for (int w = threadIdx.x; w < words; w += blockDim.x) {
+    const uint32_t b = sm_bm[w];
+    out[w] = b;
+    cnt += __popc(b);
+  }
+  cnt = block_sum(cnt, red);
+  if (threadIdx.x == 0) nnz_row[i] = cnt;
+}
+
+// Heavy rows, hash table in global memory: block b owns tables[b*S .. b*S+S)
+// and walks rows b, b+gridDim.x, ...
+__global__ void __launch_bounds__(1024, 1)
+    k_sym_global(Args a, const int32_t *__restrict__ rows, int64_t nrows, int32_t *__restrict__ nnz_row,
+                 int32_t *__restrict__ tables, int64_t S) {
+  __shared__ int red[33];
+  int32_t *tab = tables + (size_t)blockIdx.x * S;
+  const uint32_t mask = (uint32_t)(S - 1);
+  const int G = a.G;
+  for (int64_t r = blockIdx.x; r < nrows; r += gridDim.x) {
+    for (int64_t s = threadIdx.x; s < S; s += blockDim.x) tab[s] = kEmpty;
+    __syncthreads();
+    const int32_t i = rows[r];
+    int cnt = 0;
+    for_row_products<kU, false, int32_t>(a.arp[i], a.arp[i + 1], threadIdx.x / G, blockDim.x / G,
+                                         threadIdx.x & (G - 1), G, a.aci, (const int32_t *)nullptr, a.brp, a.bci,
+                                         (const int32_t *)nullptr, (int32_t)a.k, a.err,
+                                         [&](int32_t c, int32_t, int32_t) { cnt += insert_key<true>(tab, mask, c, a.err); });
+    cnt = block_sum(cnt, red);
+    if (threadIdx.x == 0) nnz_row[i] = cnt;
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <typename K>
+static cudaError_t prep(K kernel, size_t smem) {
+  if (smem > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaSuccess;
+}
+
+template <int S>
+static cudaError_t sym_warp(spgemm_plan_s *p, const Args &a, const int32_t *rows, int64_t n) {
+  const size_t smem = (size_t)kWarpsPerBlock * S * sizeof(int32_t);
+  cudaError_t e = prep(k_sym_warp<S>, smem);
+  if (e != cudaSuccess) return e;
+  const int64_t blocks = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  {
+    KernelScope ks(p, "sym_warp_" + std::to_string(S));
+    k_sym_warp<S><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, p->stream>>>(a, rows, n, p->nnz_row);
+  }
+  return cudaGetLastError();
+}
+
+template <int S>
+static cudaError_t sym_block(spgemm_plan_s *p, const Args &a, const int32_t *rows, int64_t n, int threads) {
+  const size_t smem = (size_t)S * sizeof(int32_t);
+  cudaError_t e = prep(k_sym_block<S>, smem);
+  if (e != cudaSuccess) return e;
+  {
+    KernelScope ks(p, "sym_block_" + std::to_string(S));
+    k_sym_block<S><<<(unsigned)n, threads, smem, p->stream>>>(a, rows, p->nnz_row);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_symbolic(spgemm_plan_s *p) {
+  Args a{p->m, p->n, p->k, p->arp, p->aci, p->brp, p->bci, p->av, p->bv, p->G, &p->dc->err};
+  cudaError_t e = cudaSuccess;
+  for (int b = 0; b < kNumSymBins && e == cudaSuccess; ++b) {
+    const int64_t n = p->sym_count[b];
+    if (n == 0) continue;
+    const int32_t *rows = p->perm + p->sym_off[b];
+    const BinCfg &c = kSymBins[b];
+    switch (b) {
+      case 0: e = sym_warp<64>(p, a, rows, n); break;
+      case 1: e = sym_warp<128>(p, a, rows, n); break;
+      case 2: e = sym_warp<256>(p, a, rows, n); break;
+      case 3: e = sym_warp<512>(p, a, rows, n); break;
+      case 4: e = sym_warp<1024>(p, a, rows, n); break;
+      case 5: e = sym_block<2048>(p, a, rows, n, c.threads); break;
+      case 6: e = sym_block<4096>(p, a, rows, n, c.threads); break;
+      case 7: e = sym_block<8192>(p, a, rows, n, c.threads); break;
+      case 8: e = sym_block<16384>(p, a, rows, n, c.threads); break;
+      case 9: e = sym_block<32768>(p, a, rows, n, c.threads); break;
+      case kSymBitmapBin: {
+        const size_t smem = (size_t)p->bm_words * sizeof(uint32_t);
+        e = prep(k_sym_bitmap, smem);
+        if (e != cudaSuccess) break;
+        {
+          KernelScope ks(p, "sym_bitmap");
+          k_sym_bitmap<<<(unsigned)n, c.threads, smem, p->stream>>>(a, rows, p->nnz_row, p->bitmaps, p->bm_words);
+        }
+        e = cudaGetLastError();
+        break;
+      }
+      case kSymGlobalBin: {
+        {
+          KernelScope ks(p, "sym_global");
+          k_sym_global<<<(unsigned)p->gtab_blocks, c.threads, 0, p->stream>>>(a, rows, n, p->nnz_row,
+                                                                              (int32_t *)p->gtab, p->gtab_slots);
+        }
+        e = cudaGetLastError();
+        break;
+      }
+      default: break;
+    }
+  }
+  return e;
+}
+
+}  // namespace sg

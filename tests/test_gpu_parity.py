@@ -1,0 +1,303 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Covers every step of the path: the row flop pass (bit-exact), the row bins
+(a permutation obeying the bin rule), the symbolic counts and row_ptr
+(bit-exact), the numeric values (int64 bit-exact, FP within tolerance) in
+sorted and unsorted mode, on the named workloads at full size and on edge
+cases: empty shapes, empty rows, heavy rows split into several windows,
+heavy rows on global-memory tables, unsorted inputs, structural zeros,
+int64 wrap-around and invalid input.
+"""
+import json
+import hashlib
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1804_01698_gb300 import inputs
+from paper_1804_01698_gb300.inputs import CSR
+from gpu_helpers import assert_matches_oracle, gpu_product, sort_rows_on_device
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLDEN = json.load(open(os.path.join(HERE, "golden", "workloads.json")))
+HASH_CAPS = [32, 64, 128, 256, 512, 1536, 3072, 6144, 12288]
+DT = {"i64": torch.int64, "f32": torch.float32, "f64": torch.float64}
+
+
+def int_valued(m: CSR, seed: int, lo=-3, hi=3) -> CSR:
+    v = (inputs.draw_bits(seed, 9, np.arange(m.nnz, dtype=np.uint64)) % np.uint64(hi - lo + 1)).astype(np.int64) + lo
+    return m.with_vals(v)
+
+
+def host_vals(m: CSR, dtype) -> CSR:
+    return m.astype({torch.int64: np.int64, torch.float32: np.float32, torch.float64: np.float64}[dtype])
+
+
+# ------------------------------------------------------------ a1, a2, a3, a4
+
+@pytest.mark.parametrize("name", ["er", "rmat", "tall"])
+def test_flop_bins_counts_rowptr(name):
+    from paper_1804_01698_gb300 import binding as sg
+    if name == "er":
+        A = B = inputs.er_exact(4096, 8, seed=1)
+    elif name == "rmat":
+        A = B = inputs.rmat(13, 16, seed=2)
+    else:
+        A = inputs.rmat(14, 16, seed=3, kind="ones")
+        B = inputs.frontier(A.ncols, 1024, seed=3, kind="ones", dtype=np.float64)
+    dA, dB = sg.to_device(A), sg.to_device(B)
+    with sg.Plan(dA, dB, True) as plan:
+        flop = plan.row_flop().cpu().numpy()
+        ref_flop = oracle.row_flop(A, B)
+        assert np.array_equal(flop, ref_flop)                                  # a1 bit-exact
+        perm, offs = plan.sym_bins()
+        perm = perm.cpu().numpy()
+        bound = np.minimum(ref_flop, B.ncols)
+        assert sorted(perm.tolist()) == np.nonzero(bound > 0)[0].tolist()     # a2: a permutation
+        lo = 0
+        for b, cap in enumerate(HASH_CAPS):                                   # a2: the bin rule
+            rows = perm[offs[b]:offs[b + 1]]
+            assert np.all((bound[rows] > lo) & (bound[rows] <= cap)), b
+            lo = cap
+        heavy = perm[offs[len(HASH_CAPS)]:]
+        assert np.all(bound[heavy] > HASH_CAPS[-1])
+        nnz_c = plan.symbolic()
+        ref_nnz = oracle.symbolic(A, B)
+        assert np.array_equal(plan.row_nnz().cpu().numpy(), ref_nnz)          # a3 bit-exact
+        rp = plan.c_row_ptr.cpu().numpy()
+        assert rp[0] == 0 and np.array_equal(np.diff(rp), ref_nnz)            # a4 bit-exact
+        assert nnz_c == ref_nnz.sum()
+        st = plan.stats()
+        assert st["total_flop"] == ref_flop.sum() and st["max_row_flop"] == ref_flop.max()
+        assert st["status"] == 0
+
+
+# ------------------------------------------------------------ a5, a6: named workloads at full size
+
+def _golden_check(C, name):
+    g = GOLDEN[name]
+    rp = C.row_ptr.cpu().numpy()
+    ci, _ = sort_rows_on_device(C)
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(rp, dtype=np.int32).tobytes())
+    h.update(np.ascontiguousarray(ci.cpu().numpy(), dtype=np.int32).tobytes())
+    assert int(rp[-1]) == g["nnz_c"]
+    assert h.hexdigest() == g["c_structure_sha256"]
+
+
+def test_er4096_sorted_f64():
+    A, B, _ = inputs.workload("er4096_k8_f64")
+    C, stats = gpu_product(A, B, torch.float64, True)
+    assert stats["total_flop"] == 4096 * 64
+    assert_matches_oracle(C, A, B, True)
+    _golden_check(C, "er4096_k8_f64")
+
+
+@pytest.fixture(scope="module")
+def rmat16():
+    A, B, _ = inputs.workload("rmat16_ef16_f64")
+    return A, B, oracle.spgemm(A, B, nthreads=os.cpu_count() or 8)
+
+
+@pytest.mark.parametrize("sorted_output", [True, False])
+def test_rmat16_f64(rmat16, sorted_output):
+    A, B, expect = rmat16
+    C, stats = gpu_product(A, B, torch.float64, sorted_output)
+    assert stats["total_flop"] == GOLDEN["rmat16_ef16_f64"]["total_flop"]
+    assert_matches_oracle(C, A, B, sorted_output, expect=expect)
+    _golden_check(C, "rmat16_ef16_f64")
+
+
+def test_rmat18_frontier_f32_and_int64():
+    A, B, _ = inputs.workload("rmat18_frontier1024_f32")
+    expect = oracle.spgemm(A, B, nthreads=os.cpu_count() or 8)
+    C, _ = gpu_product(A, B, torch.float32, False)
+    assert_matches_oracle(C, A, B, False, expect=expect)
+    _golden_check(C, "rmat18_frontier1024_f32")
+    Ai, Bi = A.astype(np.int64), B.astype(np.int64)
+    Ci, _ = gpu_product(Ai, Bi, torch.int64, False)
+    assert_matches_oracle(Ci, Ai, Bi, False)
+
+
+# ------------------------------------------------------------ value types x modes on mid-size inputs
+
+@pytest.mark.parametrize("dt", ["i64", "f32", "f64"])
+@pytest.mark.parametrize("sorted_output", [True, False])
+@pytest.mark.parametrize("shape", ["rmat12", "er", "rect"])
+def test_dtypes_modes(dt, sorted_output, shape):
+    dtype = DT[dt]
+    if shape == "rmat12":
+        A = inputs.rmat(12, 16, seed=21)
+        B = A
+    elif shape == "er":
+        A = inputs.er_exact(3000, 11, seed=22, ncols=5000)
+        B = inputs.er_exact(5000, 7, seed=23, ncols=777)
+    else:  # ragged rectangular product, rows of very different lengths
+        A = inputs.rmat(11, 24, seed=24, abcd=(0.45, 0.25, 0.15, 0.15))
+        A = CSR(A.nrows, A.ncols, A.row_ptr, A.col_idx, A.vals)
+        B = inputs.er_exact(A.ncols, 5, seed=25, ncols=3001)
+    if dt != "f64":  # small integers: exact in float32 and int64
+        A, B = int_valued(A, 31), int_valued(B, 32)
+    A, B = host_vals(A, dtype), host_vals(B, dtype)
+    C, _ = gpu_product(A, B, dtype, sorted_output)
+    assert_matches_oracle(C, A, B, sorted_output)
+
+
+def test_float32_uniform_values_within_tolerance():
+    A = inputs.er_exact(2048, 8, seed=41, dtype=np.float32)
+    C, _ = gpu_product(A, A, torch.float32, True)
+    assert_matches_oracle(C, A, A, True)
+
+
+def test_every_bin_is_exercised():
+    """The inputs above reach every symbolic and numeric bin; checked here on one
+    mixed input so that a bin that never runs does not go unnoticed."""
+    A = inputs.rmat(15, 16, seed=51)
+    C, st = gpu_product(A, A, torch.float64, True)
+    assert all(st["sym_bin_rows"][b] > 0 for b in range(9))
+    assert st["sym_bin_rows"][10] > 0            # bitmap heavy rows
+    assert all(st["num_bin_rows"][b] > 0 for b in range(9))
+    assert st["num_bin_rows"][9] > 0             # bitmap work items
+    assert_matches_oracle(C, A, A, True)
+
+
+# ------------------------------------------------------------ heavy rows
+
+def _heavy_rows(nrows_a, entries, ncols_b, b_row_len, seed):
+    """A: nrows_a rows of `entries` distinct columns; B: rows of b_row_len random columns."""
+    A = inputs.er_exact(nrows_a, entries, seed=seed, ncols=entries * 4)
+    B = inputs.er_exact(entries * 4, b_row_len, seed=seed + 1, ncols=ncols_b)
+    return A, B
+
+
+@pytest.mark.parametrize("dt", ["f64", "i64"])
+def test_bitmap_rows_split_into_several_windows(dt):
+    dtype = DT[dt]
+    A, B = _heavy_rows(6, 64, 65536, 1000, seed=61)     # ~40k entries per row: 2 windows
+    if dt == "i64":
+        A, B = int_valued(A, 62), int_valued(B, 63)
+    A, B = host_vals(A, dtype), host_vals(B, dtype)
+    C, st = gpu_product(A, B, dtype, True)
+    assert st["sym_bin_rows"][10] == 6 and st["num_bin_rows"][9] > 6
+    assert_matches_oracle(C, A, B, True)
+
+
+@pytest.mark.parametrize("sorted_output", [True, False])
+@pytest.mark.parametrize("dt", ["f64", "i64", "f32"])
+def test_global_table_rows(sorted_output, dt):
+    dtype = DT[dt]
+    # 2^20 columns: too many for bitmaps; flop 40k per row -> global tables;
+    # plus rows of flop ~20k -> the 32768-slot block bin.
+    A1, B1 = _heavy_rows(5, 40, 1 << 20, 1000, seed=71)
+    A2 = inputs.er_exact(7, 20, seed=73, ncols=160)
+    A = CSR(12, 160, np.concatenate([A1.row_ptr, A2.row_ptr[1:] + A1.nnz]).astype(np.int32),
+            np.concatenate([A1.col_idx, A2.col_idx]), np.concatenate([A1.vals, A2.vals]))
+    B = B1
+    if dt != "f64":
+        A, B = int_valued(A, 74), int_valued(B, 75)
+    A, B = host_vals(A, dtype), host_vals(B, dtype)
+    C, st = gpu_product(A, B, dtype, sorted_output)
+    assert st["sym_bin_rows"][11] == 5 and st["sym_bin_rows"][9] == 7
+    assert st["num_bin_rows"][10] >= 5
+    assert_matches_oracle(C, A, B, sorted_output)
+
+
+# ------------------------------------------------------------ edge cases
+
+def _csr(m, n, rows):
+    rp = np.zeros(m + 1, np.int32)
+    cols, vals = [], []
+    for i, r in enumerate(rows):
+        rp[i + 1] = rp[i] + len(r)
+        cols += [c for c, _ in r]
+        vals += [v for _, v in r]
+    return CSR(m, n, rp, np.array(cols, np.int32), np.array(vals, np.float64))
+
+
+@pytest.mark.parametrize("shape", [(0, 5, 3), (4, 0, 3), (4, 5, 0), (3, 3, 3)])
+def test_empty_shapes(shape):
+    m, n, k = shape
+    A = CSR(m, n, np.zeros(m + 1, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    B = CSR(n, k, np.zeros(n + 1, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    for one_shot in (False, True):
+        C, _ = gpu_product(A, B, torch.float64, True, one_shot=one_shot)
+        assert C.nrows == m and C.nnz == 0
+        assert np.array_equal(C.row_ptr.cpu().numpy(), np.zeros(m + 1, np.int32))
+
+
+def test_empty_rows_and_structural_zero():
+    A = _csr(4, 3, [[], [(0, 1.0), (1, 1.0)], [], [(2, 2.0)]])
+    B = _csr(3, 2, [[(0, 1.0)], [(0, -1.0)], [(1, 3.0)]])
+    C, _ = gpu_product(A, B, torch.float64, True)
+    assert C.row_ptr.cpu().tolist() == [0, 0, 1, 1, 2]
+    assert C.col_idx.cpu().tolist() == [0, 1]
+    assert C.vals.cpu().tolist() == [0.0, 6.0]          # 1*1 + 1*(-1) kept as a stored zero
+
+
+def test_int64_wraps_like_the_oracle():
+    A = CSR(1, 2, np.array([0, 2], np.int32), np.array([0, 1], np.int32), np.array([2 ** 62, 3], np.int64))
+    B = CSR(2, 1, np.array([0, 1, 2], np.int32), np.array([0, 0], np.int32), np.array([4, -5], np.int64))
+    C, _ = gpu_product(A, B, torch.int64, True)
+    assert C.vals.cpu().tolist() == [-15]
+
+
+def test_unsorted_inputs_give_the_same_product():
+    A = inputs.rmat(12, 16, seed=81)
+    S = inputs.shuffle_rows(A, seed=82)
+    expect = oracle.spgemm(A, A, nthreads=8)
+    for sorted_output in (True, False):
+        C, _ = gpu_product(S, S, torch.float64, sorted_output)
+        assert_matches_oracle(C, S, S, sorted_output, expect=expect)
+
+
+def test_one_shot_entry_point():
+    A = inputs.rmat(11, 16, seed=91)
+    C, _ = gpu_product(A, A, torch.float64, True, one_shot=True)
+    assert_matches_oracle(C, A, A, True)
+
+
+def test_tiny_random_products_against_oracle():
+    rng = np.random.default_rng(5)
+    for t in range(25):
+        m, n, k = (int(x) for x in rng.integers(1, 70, size=3))
+        A = CSR(m, n, *_rand_csr(rng, m, n))
+        B = CSR(n, k, *_rand_csr(rng, n, k))
+        for dt in (torch.int64, torch.float64):
+            Ah = A if dt == torch.float64 else int_valued(A, t)
+            Bh = B if dt == torch.float64 else int_valued(B, t + 100)
+            C, _ = gpu_product(host_vals(Ah, dt), host_vals(Bh, dt), dt, bool(t % 2))
+            assert_matches_oracle(C, host_vals(Ah, dt), host_vals(Bh, dt), bool(t % 2))
+
+
+def _rand_csr(rng, m, n):
+    dens = rng.uniform(0.0, 0.5)
+    mask = rng.random((m, n)) < dens
+    rp = np.zeros(m + 1, np.int32)
+    rp[1:] = np.cumsum(mask.sum(1))
+    r, c = np.nonzero(mask)
+    return rp, c.astype(np.int32), rng.uniform(-1, 1, size=len(c))
+
+
+@pytest.mark.parametrize("where", ["A", "B"])
+def test_out_of_range_column_is_an_error_not_a_fault(where):
+    from paper_1804_01698_gb300 import binding as sg
+    A = inputs.er_exact(64, 4, seed=101)
+    B = inputs.er_exact(64, 4, seed=102)
+    bad = (A if where == "A" else B)
+    ci = bad.col_idx.copy()
+    ci[7] = 64 + 5                                   # one column past the end
+    bad = CSR(bad.nrows, bad.ncols, bad.row_ptr, ci, bad.vals)
+    A, B = (bad, B) if where == "A" else (A, bad)
+    dA, dB = sg.to_device(A), sg.to_device(B)
+    with pytest.raises(sg.SpgemmError) as ei:
+        with sg.Plan(dA, dB, True) as plan:
+            plan.symbolic()
+    assert ei.value.status == -2                     # SPGEMM_ERR_INVALID_CSR
+    # the context is still usable
+    C, _ = gpu_product(inputs.er_exact(64, 4, seed=103), inputs.er_exact(64, 4, seed=104), torch.float64, True)
+    assert C.nnz > 0
