@@ -85,6 +85,8 @@ typedef enum { SPGEMM_I64 = 0, SPGEMM_F32 = 1, SPGEMM_F64 = 2 } spgemm_dtype;
 #define SPGEMM_SORTED 1u   /* output columns ascending within each row */
 #define SPGEMM_VALIDATE 2u /* accepted; the device checks listed under Errors always run */
 #define SPGEMM_TIMING 4u   /* record CUDA events around every kernel (spgemm_plan_kernel_times) */
+#define SPGEMM_SERIAL 8u   /* run the bins of a phase one after another on the plan's stream
+                              (default: concurrently on side streams joined back to it) */
 
 /* A CSR operand (device pointers). */
 typedef struct {

@@ -25,7 +25,7 @@ from . import build as _build
 _LIB = None
 
 SPGEMM_I64, SPGEMM_F32, SPGEMM_F64 = 0, 1, 2
-SPGEMM_UNSORTED, SPGEMM_SORTED, SPGEMM_VALIDATE, SPGEMM_TIMING = 0, 1, 2, 4
+SPGEMM_UNSORTED, SPGEMM_SORTED, SPGEMM_VALIDATE, SPGEMM_TIMING, SPGEMM_SERIAL = 0, 1, 2, 4, 8
 MAX_BINS = 24
 
 _DTYPES = {torch.int64: SPGEMM_I64, torch.float32: SPGEMM_F32, torch.float64: SPGEMM_F64}
@@ -154,7 +154,8 @@ def _stream_ptr(stream) -> int | None:
 class Plan:
     """A plan for C = A*B; methods mirror spgemm_symbolic / spgemm_numeric."""
 
-    def __init__(self, A: DeviceCSR, B: DeviceCSR, sorted_output: bool = True, stream=None, timing: bool = False):
+    def __init__(self, A: DeviceCSR, B: DeviceCSR, sorted_output: bool = True, stream=None, timing: bool = False,
+                 serial: bool = False):
         self.lib = library()
         if A.vals.dtype != B.vals.dtype or A.vals.dtype not in _DTYPES:
             raise TypeError("A and B must share a value dtype among int64, float32, float64")
@@ -162,7 +163,8 @@ class Plan:
         self.dtype = A.vals.dtype
         self.device = A.row_ptr.device
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        flags = (SPGEMM_SORTED if sorted_output else SPGEMM_UNSORTED) | (SPGEMM_TIMING if timing else 0)
+        flags = (SPGEMM_SORTED if sorted_output else SPGEMM_UNSORTED) | (SPGEMM_TIMING if timing else 0) | \
+            (SPGEMM_SERIAL if serial else 0)
         self._a, self._b = A.desc(), B.desc()
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
@@ -254,8 +256,8 @@ class Plan:
 
 
 def spgemm_plan_create(A: DeviceCSR, B: DeviceCSR, sorted_output: bool = True, stream=None,
-                       timing: bool = False) -> Plan:
-    return Plan(A, B, sorted_output, stream, timing)
+                       timing: bool = False, serial: bool = False) -> Plan:
+    return Plan(A, B, sorted_output, stream, timing, serial)
 
 
 def spgemm_plan_kernel_times(plan: Plan) -> dict:

@@ -177,4 +177,146 @@ __device__ __forceinline__ void for_row_products(int64_t a0, int64_t a1, int gro
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Staged, segmented row loop.  The stored a_ik of a row are processed in
+// rounds of up to kStageN entries.  Per round, the metadata of each entry
+// (start and length of row k of B, a_ik) is loaded cooperatively into shared
+// memory, so the dependent loads col_idx(A) -> row_ptr(B) are issued in
+// bulk.  Every B row is cut into segments of SEG = G * U * kSegIters entries
+// and the segments of the round are numbered by a prefix sum; groups of G
+// lanes claim segment numbers from a shared counter, find the owning entry
+// by binary search over the prefix, and stride over the segment with U loads
+// in flight per lane.  A long row of B is thereby shared by many groups and
+// no group waits for another at the end of the round.
+constexpr int kStageN = 256;  // entries staged per round (block form)
+constexpr int kSegIters = 2;  // strided iterations per claimed segment
+
+template <typename T> struct Stage {
+  int2 *meta;  // (start, length) of the B row of each staged entry
+  T *a;        // a_ik of each staged entry
+  int *segoff; // exclusive prefix of segment counts, one slot per entry + total
+  int *next;   // next unclaimed segment
+};
+
+template <int U, bool NEED_VAL, typename T, typename F>
+__device__ __forceinline__ void process_segment(const Stage<T> &st, int n, int seg, int SEG, int G, int lig,
+                                                const int32_t *__restrict__ bci, const T *__restrict__ bv,
+                                                int32_t ncols, uint32_t *err, F &&f) {
+  int lo = 0, hi = n - 1;  // largest e with segoff[e] <= seg
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (st.segoff[mid] <= seg) lo = mid;
+    else hi = mid - 1;
+  }
+  const int2 m = st.meta[lo];
+  const T a = NEED_VAL ? st.a[lo] : T(0);
+  const int32_t q0 = m.x + (seg - st.segoff[lo]) * SEG;
+  const int32_t qe = min(m.x + m.y, q0 + SEG);
+  for (int32_t q = q0 + lig; q < qe; q += G * U) {
+    int32_t c[U];
+    T v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int32_t qq = q + u * G;
+      c[u] = qq < qe ? __ldg(bci + qq) : -1;
+      if (NEED_VAL) v[u] = qq < qe ? __ldg(bv + qq) : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (q + u * G < qe) {
+        if ((uint32_t)c[u] < (uint32_t)ncols) f(c[u], a, NEED_VAL ? v[u] : T(0));
+        else raise_err(err, kErrCsr);
+      }
+    }
+  }
+}
+
+// Block-wide form: every thread of the block calls it (blockDim.x >= kStageN).
+// st.meta/st.a hold kStageN entries, st.segoff kStageN + 1, plus 8 ints of
+// scratch after them (st.segoff[kStageN + 1 ...]).
+template <int U, bool NEED_VAL, typename T, typename F>
+__device__ __forceinline__ void block_row_products(int64_t a0, int64_t a1, int G, const int32_t *__restrict__ aci,
+                                                   const T *__restrict__ av, const int32_t *__restrict__ brp,
+                                                   const int32_t *__restrict__ bci, const T *__restrict__ bv,
+                                                   int32_t ncols, uint32_t *err, Stage<T> st, F &&f) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, lig = tid & (G - 1);
+  const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+  const int leader = lane & ~(G - 1);
+  const int SEG = G * U * kSegIters;
+  int *wsum = st.segoff + kStageN + 1;  // 8 warp totals
+  for (int64_t j0 = a0; j0 < a1; j0 += kStageN) {
+    const int n = (int)((a1 - j0) < kStageN ? (a1 - j0) : kStageN);
+    int nseg = 0;
+    if (tid < n) {
+      const int32_t kk = __ldg(aci + j0 + tid);
+      const int32_t bs = __ldg(brp + kk), be = __ldg(brp + kk + 1);
+      st.meta[tid] = make_int2(bs, be - bs);
+      if (NEED_VAL) st.a[tid] = __ldg(av + j0 + tid);
+      nseg = (be - bs + SEG - 1) / SEG;
+    }
+    // exclusive scan of nseg over the first kStageN threads (8 warps)
+    int inc = nseg;
+    if (wid < kStageN / 32) {
+      inc = warp_incl_scan(nseg);
+      if (lane == 31) wsum[wid] = inc;
+    }
+    if (tid == 0) *st.next = 0;
+    __syncthreads();
+    if (wid < kStageN / 32) {
+      int base = 0;
+      for (int w = 0; w < wid; ++w) base += wsum[w];
+      if (tid < n) st.segoff[tid] = base + inc - nseg;
+      if (tid == kStageN - 1) st.segoff[kStageN] = base + inc;
+    }
+    __syncthreads();
+    const int total = st.segoff[kStageN];
+    for (;;) {
+      int seg = 0;
+      if (lig == 0) seg = atomicAdd(st.next, 1);
+      seg = __shfl_sync(gmask, seg, leader);
+      if (seg >= total) break;
+      process_segment<U, NEED_VAL>(st, n, seg, SEG, G, lig, bci, bv, ncols, err, f);
+    }
+    __syncthreads();
+  }
+}
+
+// Warp form: the 32 lanes of one warp work on one row; `st` points to this
+// warp's own staging area (32 entries, segoff 33 ints).
+template <int U, bool NEED_VAL, typename T, typename F>
+__device__ __forceinline__ void warp_row_products(int64_t a0, int64_t a1, int G, const int32_t *__restrict__ aci,
+                                                  const T *__restrict__ av, const int32_t *__restrict__ brp,
+                                                  const int32_t *__restrict__ bci, const T *__restrict__ bv,
+                                                  int32_t ncols, uint32_t *err, Stage<T> st, F &&f) {
+  const int lane = threadIdx.x & 31, lig = lane & (G - 1);
+  const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+  const int leader = lane & ~(G - 1);
+  const int SEG = G * U * kSegIters;
+  for (int64_t j0 = a0; j0 < a1; j0 += 32) {
+    const int n = (int)((a1 - j0) < 32 ? (a1 - j0) : 32);
+    int nseg = 0;
+    if (lane < n) {
+      const int32_t kk = __ldg(aci + j0 + lane);
+      const int32_t bs = __ldg(brp + kk), be = __ldg(brp + kk + 1);
+      st.meta[lane] = make_int2(bs, be - bs);
+      if (NEED_VAL) st.a[lane] = __ldg(av + j0 + lane);
+      nseg = (be - bs + SEG - 1) / SEG;
+    }
+    const int inc = warp_incl_scan(nseg);
+    st.segoff[lane] = inc - nseg;
+    const int total = __shfl_sync(0xffffffffu, inc, 31);
+    if (lane == 0) *st.next = 0;
+    __syncwarp();
+    for (;;) {
+      int seg = 0;
+      if (lig == 0) seg = atomicAdd(st.next, 1);
+      seg = __shfl_sync(gmask, seg, leader);
+      if (seg >= total) break;
+      process_segment<U, NEED_VAL>(st, n, seg, SEG, G, lig, bci, bv, ncols, err, f);
+    }
+    __syncwarp();
+  }
+}
+
 }  // namespace sg

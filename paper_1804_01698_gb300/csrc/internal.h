@@ -41,6 +41,9 @@ constexpr int kNumBitmapBin = 9;   // numeric bins 0..8 are hash bins
 constexpr int kNumGlobalBin = 10;
 constexpr int kNumNumBins = 11;
 constexpr int kWarpsPerBlock = 4;  // warp bins: rows per block
+// shared memory kept free beside a bitmap kernel's dynamic allocation for
+// its static arrays (staging of 256 entries, reductions)
+constexpr int kStaticSmemReserve = 256 * 20 + 1024;
 
 // Symbolic bins 0..9: tables 64 .. 32768 slots, load factor 1/2 for warp
 // tables and 3/4 for block tables (the bound overestimates the key count
@@ -128,6 +131,11 @@ struct spgemm_plan_s {
   int32_t launches;
   const int32_t *c_rp;
 
+  // side streams for bins that run concurrently (fork/join on `stream`)
+  cudaStream_t side[4];
+  cudaEvent_t fork_ev, join_ev[4];
+  bool side_ready;
+
   // per-kernel CUDA events (SPGEMM_TIMING)
   struct Timed {
     std::string name;
@@ -141,24 +149,37 @@ namespace sg {
 // and counts the launch.
 struct KernelScope {
   spgemm_plan_s *p;
+  cudaStream_t s;
   int idx = -1;
-  KernelScope(spgemm_plan_s *plan, const std::string &name) : p(plan) {
+  KernelScope(spgemm_plan_s *plan, const std::string &name) : KernelScope(plan, name, plan->stream) {}
+  KernelScope(spgemm_plan_s *plan, const std::string &name, cudaStream_t stream) : p(plan), s(stream) {
     p->launches++;
     if (!(p->flags & SPGEMM_TIMING)) return;
     spgemm_plan_s::Timed t{name, nullptr, nullptr};
     if (cudaEventCreate(&t.start) != cudaSuccess || cudaEventCreate(&t.stop) != cudaSuccess) return;
-    cudaEventRecord(t.start, p->stream);
+    cudaEventRecord(t.start, s);
     p->timed.push_back(t);
     idx = (int)p->timed.size() - 1;
   }
   ~KernelScope() {
-    if (idx >= 0) cudaEventRecord(p->timed[idx].stop, p->stream);
+    if (idx >= 0) cudaEventRecord(p->timed[idx].stop, s);
   }
 };
+
+// Concurrent bins: fork() makes the side streams wait for the plan's stream,
+// bin_stream(i) picks the stream of the i-th launched bin, join() makes the
+// plan's stream wait for every side stream.  Without side streams all bins
+// run on the plan's stream.
+cudaError_t fork(spgemm_plan_s *p);
+cudaStream_t bin_stream(spgemm_plan_s *p, int i);
+cudaError_t join(spgemm_plan_s *p);
 
 // Launchers (return a cudaError_t from the launch).
 cudaError_t launch_symbolic(spgemm_plan_s *p);
 cudaError_t launch_numeric(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_ci, void *c_v);
 int64_t bitmap_capacity(int dtype, int bm_words);
+// Raises a kernel's dynamic shared memory limit to at least `bytes` (once per
+// kernel, device and size; the static arrays count against the default 48 KB).
+cudaError_t set_dynamic_smem(const void *kernel, size_t bytes);
 int max_smem_per_block();
 }  // namespace sg

@@ -23,7 +23,7 @@
 
 namespace sg {
 
-constexpr int kUN = 2;  // B entries (column + value) loaded ahead per lane
+constexpr int kUN = 4;  // B entries (column + value) loaded ahead per lane
 
 // Finds or claims the slot of key c and accumulates a*b there.
 template <typename T, bool GLOBAL_MEM>
@@ -76,10 +76,14 @@ __device__ __forceinline__ void bitonic_sort(uint32_t *keys, T *vals, int n, int
 
 // ---------------------------------------------------------------------------
 template <typename T, int S>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 8)
     k_num_warp(Args a, const int32_t *__restrict__ rows, int64_t nrows, const int32_t *__restrict__ c_rp,
                int32_t *__restrict__ c_ci, T *__restrict__ c_v, int sorted) {
   extern __shared__ __align__(16) unsigned char sm_num_warp[];
+  __shared__ int2 s_meta[kWarpsPerBlock][32];
+  __shared__ int s_segoff[kWarpsPerBlock][33];
+  __shared__ T s_a[kWarpsPerBlock][32];
+  __shared__ int s_next[kWarpsPerBlock];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
   if (w >= nrows) return;
@@ -92,8 +96,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   __syncwarp();
   const int32_t i = rows[w];
   const int G = a.G;
-  for_row_products<kUN, true, T>(a.arp[i], a.arp[i + 1], lane / G, 32 / G, lane & (G - 1), G, a.aci,
-                                 (const T *)a.av, a.brp, a.bci, (const T *)a.bv, (int32_t)a.k, a.err,
+  warp_row_products<kUN, true, T>(a.arp[i], a.arp[i + 1], G, a.aci, (const T *)a.av, a.brp, a.bci, (const T *)a.bv,
+                                  (int32_t)a.k, a.err, Stage<T>{s_meta[warp], s_a[warp], s_segoff[warp], &s_next[warp]},
                                  [&](int32_t c, T av, T bv) { insert_acc<T, false>(keys, vals, S - 1, c, av, bv, a.err); });
   __syncwarp();
   const int32_t rp = c_rp[i];
@@ -130,6 +134,10 @@ __global__ void __launch_bounds__(1024, 1)
                 int32_t *__restrict__ c_ci, T *__restrict__ c_v, int sort_mode, int words) {
   extern __shared__ __align__(16) unsigned char sm_num_block[];
   __shared__ int red[33];
+  __shared__ int2 s_meta[kStageN];
+  __shared__ int s_segoff[kStageN + 1 + 8];
+  __shared__ T s_a[kStageN];
+  __shared__ int s_next;
   __shared__ int cursor;
   int32_t *keys = reinterpret_cast<int32_t *>(sm_num_block);
   T *vals = reinterpret_cast<T *>(sm_num_block + (size_t)S * sizeof(int32_t));
@@ -141,8 +149,8 @@ __global__ void __launch_bounds__(1024, 1)
   __syncthreads();
   const int32_t i = rows[blockIdx.x];
   const int G = a.G;
-  for_row_products<kUN, true, T>(a.arp[i], a.arp[i + 1], threadIdx.x / G, blockDim.x / G, threadIdx.x & (G - 1), G,
-                                 a.aci, (const T *)a.av, a.brp, a.bci, (const T *)a.bv, (int32_t)a.k, a.err,
+  block_row_products<kUN, true, T>(a.arp[i], a.arp[i + 1], G, a.aci, (const T *)a.av, a.brp, a.bci,
+                                   (const T *)a.bv, (int32_t)a.k, a.err, Stage<T>{s_meta, s_a, s_segoff, &s_next},
                                  [&](int32_t c, T av, T bv) { insert_acc<T, false>(keys, vals, S - 1, c, av, bv, a.err); });
   __syncthreads();
   const int32_t rp = c_rp[i];
@@ -216,6 +224,10 @@ __global__ void __launch_bounds__(1024, 1)
                  int32_t *__restrict__ c_ci, T *__restrict__ c_v) {
   extern __shared__ __align__(16) unsigned char sm_num_bm[];
   __shared__ int red[33];
+  __shared__ int2 s_meta[kStageN];
+  __shared__ int s_segoff[kStageN + 1 + 8];
+  __shared__ T s_a[kStageN];
+  __shared__ int s_next;
   T *vals = reinterpret_cast<T *>(sm_num_bm);
   uint32_t *bm = reinterpret_cast<uint32_t *>(sm_num_bm + (size_t)cap * sizeof(T));
   int32_t *pre = reinterpret_cast<int32_t *>(bm + words);
@@ -243,8 +255,8 @@ __global__ void __launch_bounds__(1024, 1)
   for (int r = threadIdx.x; r < hi - lo; r += blockDim.x) vals[r] = T(0);
   __syncthreads();
   const int G = a.G;
-  for_row_products<kUN, true, T>(a.arp[i], a.arp[i + 1], threadIdx.x / G, blockDim.x / G, threadIdx.x & (G - 1), G,
-                                 a.aci, (const T *)a.av, a.brp, a.bci, (const T *)a.bv, (int32_t)a.k, a.err,
+  block_row_products<kUN, true, T>(a.arp[i], a.arp[i + 1], G, a.aci, (const T *)a.av, a.brp, a.bci,
+                                   (const T *)a.bv, (int32_t)a.k, a.err, Stage<T>{s_meta, s_a, s_segoff, &s_next},
                                  [&](int32_t c, T av, T bv) {
                                    const uint32_t word = bm[c >> 5];
                                    const int r = pre[c >> 5] + __popc(word & ((1u << (c & 31)) - 1u));
@@ -282,6 +294,10 @@ __global__ void __launch_bounds__(1024, 1)
                  T *__restrict__ c_v, int sorted, int win_words) {
   extern __shared__ __align__(16) unsigned char sm_num_gl[];
   __shared__ int red[33];
+  __shared__ int2 s_meta[kStageN];
+  __shared__ int s_segoff[kStageN + 1 + 8];
+  __shared__ T s_a[kStageN];
+  __shared__ int s_next;
   __shared__ int cursor;
   int32_t *keys = keys_all + (size_t)blockIdx.x * S;
   T *vals = vals_all + (size_t)blockIdx.x * S;
@@ -296,8 +312,8 @@ __global__ void __launch_bounds__(1024, 1)
     if (threadIdx.x == 0) cursor = 0;
     __syncthreads();
     const int32_t i = rows[r];
-    for_row_products<kUN, true, T>(a.arp[i], a.arp[i + 1], threadIdx.x / G, blockDim.x / G, threadIdx.x & (G - 1),
-                                   G, a.aci, (const T *)a.av, a.brp, a.bci, (const T *)a.bv, (int32_t)a.k, a.err,
+    block_row_products<kUN, true, T>(a.arp[i], a.arp[i + 1], G, a.aci, (const T *)a.av, a.brp, a.bci,
+                                   (const T *)a.bv, (int32_t)a.k, a.err, Stage<T>{s_meta, s_a, s_segoff, &s_next},
                                    [&](int32_t c, T av, T bv) { insert_acc<T, true>(keys, vals, mask, c, av, bv, a.err); });
     __syncthreads();
     const int32_t rp = c_rp[i];
@@ -367,30 +383,31 @@ __global__ void __launch_bounds__(1024, 1)
 }
 
 // ---------------------------------------------------------------------------
+// Raises the kernel's dynamic shared memory limit once per size (the
+// static arrays count against the default 48 KB as well).
 template <typename K>
 static cudaError_t prep_num(K kernel, size_t smem) {
-  if (smem > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  return cudaSuccess;
+  return set_dynamic_smem(reinterpret_cast<const void *>(kernel), smem);
 }
 
 template <typename T, int S>
-static cudaError_t num_warp(spgemm_plan_s *p, const Args &a, const int32_t *rows, int64_t n, const int32_t *c_rp,
-                            int32_t *c_ci, T *c_v) {
+static cudaError_t num_warp(spgemm_plan_s *p, cudaStream_t st, const Args &a, const int32_t *rows, int64_t n,
+                            const int32_t *c_rp, int32_t *c_ci, T *c_v) {
   const size_t smem = (size_t)kWarpsPerBlock * S * (sizeof(int32_t) + sizeof(T));
   cudaError_t e = prep_num(k_num_warp<T, S>, smem);
   if (e != cudaSuccess) return e;
   const int64_t blocks = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
   {
-    KernelScope ks(p, "num_warp_" + std::to_string(S));
-    k_num_warp<T, S><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, p->stream>>>(
+    KernelScope ks(p, "num_warp_" + std::to_string(S), st);
+    k_num_warp<T, S><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, st>>>(
         a, rows, n, c_rp, c_ci, c_v, (p->flags & SPGEMM_SORTED) ? 1 : 0);
   }
   return cudaGetLastError();
 }
 
 template <typename T, int S>
-static cudaError_t num_block(spgemm_plan_s *p, const Args &a, const int32_t *rows, int64_t n, int threads,
-                             const int32_t *c_rp, int32_t *c_ci, T *c_v) {
+static cudaError_t num_block(spgemm_plan_s *p, cudaStream_t st, const Args &a, const int32_t *rows, int64_t n,
+                             int threads, const int32_t *c_rp, int32_t *c_ci, T *c_v) {
   size_t smem = (size_t)S * (sizeof(int32_t) + sizeof(T));
   int mode = 0;
   if (p->flags & SPGEMM_SORTED) {
@@ -405,8 +422,8 @@ static cudaError_t num_block(spgemm_plan_s *p, const Args &a, const int32_t *row
   cudaError_t e = prep_num(k_num_block<T, S>, smem);
   if (e != cudaSuccess) return e;
   {
-    KernelScope ks(p, "num_block_" + std::to_string(S));
-    k_num_block<T, S><<<(unsigned)n, threads, smem, p->stream>>>(a, rows, c_rp, c_ci, c_v, mode, p->bm_words);
+    KernelScope ks(p, "num_block_" + std::to_string(S), st);
+    k_num_block<T, S><<<(unsigned)n, threads, smem, st>>>(a, rows, c_rp, c_ci, c_v, mode, p->bm_words);
   }
   return cudaGetLastError();
 }
@@ -414,29 +431,35 @@ static cudaError_t num_block(spgemm_plan_s *p, const Args &a, const int32_t *row
 template <typename T>
 cudaError_t launch_numeric_t(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_ci, T *c_v) {
   Args a{p->m, p->n, p->k, p->arp, p->aci, p->brp, p->bci, p->av, p->bv, p->G, &p->dc->err};
-  cudaError_t e = cudaSuccess;
-  for (int b = 0; b < kNumNumBins && e == cudaSuccess; ++b) {
+  // heavy bins first, each bin on the next side stream
+  static const int order[kNumNumBins] = {kNumBitmapBin, kNumGlobalBin, 8, 7, 6, 5, 4, 3, 2, 1, 0};
+  const bool concurrent = !(p->flags & SPGEMM_SERIAL);
+  cudaError_t e = concurrent ? fork(p) : cudaSuccess;
+  int launched = 0;
+  for (int o = 0; o < kNumNumBins && e == cudaSuccess; ++o) {
+    const int b = order[o];
     const int64_t n = p->num_count[b];
     if (n == 0) continue;
     const int32_t *rows = p->perm2 + p->num_off[b];
     const BinCfg &c = kNumBins[b];
+    cudaStream_t st = concurrent ? bin_stream(p, launched++) : p->stream;
     switch (b) {
-      case 0: e = num_warp<T, 64>(p, a, rows, n, c_rp, c_ci, c_v); break;
-      case 1: e = num_warp<T, 128>(p, a, rows, n, c_rp, c_ci, c_v); break;
-      case 2: e = num_warp<T, 256>(p, a, rows, n, c_rp, c_ci, c_v); break;
-      case 3: e = num_warp<T, 512>(p, a, rows, n, c_rp, c_ci, c_v); break;
-      case 4: e = num_warp<T, 1024>(p, a, rows, n, c_rp, c_ci, c_v); break;
-      case 5: e = num_block<T, 2048>(p, a, rows, n, c.threads, c_rp, c_ci, c_v); break;
-      case 6: e = num_block<T, 4096>(p, a, rows, n, c.threads, c_rp, c_ci, c_v); break;
-      case 7: e = num_block<T, 8192>(p, a, rows, n, c.threads, c_rp, c_ci, c_v); break;
-      case 8: e = num_block<T, 16384>(p, a, rows, n, c.threads, c_rp, c_ci, c_v); break;
+      case 0: e = num_warp<T, 64>(p, st, a, rows, n, c_rp, c_ci, c_v); break;
+      case 1: e = num_warp<T, 128>(p, st, a, rows, n, c_rp, c_ci, c_v); break;
+      case 2: e = num_warp<T, 256>(p, st, a, rows, n, c_rp, c_ci, c_v); break;
+      case 3: e = num_warp<T, 512>(p, st, a, rows, n, c_rp, c_ci, c_v); break;
+      case 4: e = num_warp<T, 1024>(p, st, a, rows, n, c_rp, c_ci, c_v); break;
+      case 5: e = num_block<T, 2048>(p, st, a, rows, n, c.threads, c_rp, c_ci, c_v); break;
+      case 6: e = num_block<T, 4096>(p, st, a, rows, n, c.threads, c_rp, c_ci, c_v); break;
+      case 7: e = num_block<T, 8192>(p, st, a, rows, n, c.threads, c_rp, c_ci, c_v); break;
+      case 8: e = num_block<T, 16384>(p, st, a, rows, n, c.threads, c_rp, c_ci, c_v); break;
       case kNumBitmapBin: {
         const size_t smem = (size_t)p->bm_cap * sizeof(T) + (size_t)p->bm_words * 8;
         e = prep_num(k_num_bitmap<T>, smem);
         if (e != cudaSuccess) break;
         {
-          KernelScope ks(p, "num_bitmap");
-          k_num_bitmap<T><<<(unsigned)n, c.threads, smem, p->stream>>>(a, p->perm + p->sym_off[kSymBitmapBin],
+          KernelScope ks(p, "num_bitmap", st);
+          k_num_bitmap<T><<<(unsigned)n, c.threads, smem, st>>>(a, p->perm + p->sym_off[kSymBitmapBin],
                                                                        p->bm_items, p->bitmaps, p->bm_words,
                                                                        (int)p->bm_cap, c_rp, c_ci, c_v);
         }
@@ -451,8 +474,8 @@ cudaError_t launch_numeric_t(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_c
         int32_t *keys = (int32_t *)p->gtab;
         T *vals = reinterpret_cast<T *>((char *)p->gtab + (size_t)p->gtab_blocks * p->gtab_slots * sizeof(int32_t));
         {
-          KernelScope ks(p, "num_global");
-          k_num_global<T><<<(unsigned)p->gtab_blocks, c.threads, smem, p->stream>>>(
+          KernelScope ks(p, "num_global", st);
+          k_num_global<T><<<(unsigned)p->gtab_blocks, c.threads, smem, st>>>(
               a, rows, n, keys, vals, p->gtab_slots, c_rp, c_ci, c_v, (p->flags & SPGEMM_SORTED) ? 1 : 0, win_words);
         }
         e = cudaGetLastError();
@@ -461,6 +484,7 @@ cudaError_t launch_numeric_t(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_c
       default: break;
     }
   }
+  if (concurrent && e == cudaSuccess) e = join(p);
   return e;
 }
 

@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -283,6 +284,19 @@ int max_smem_per_block() {
   return cached[dev];
 }
 
+cudaError_t set_dynamic_smem(const void *kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void *, int>, size_t> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> g(mu);
+  size_t &have = done[{kernel, dev}];
+  if (bytes <= have) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) have = bytes;
+  return e;
+}
+
 static int sm_count() {
   static int cached[64];
   int dev = 0;
@@ -296,12 +310,38 @@ static int sm_count() {
   return cached[dev];
 }
 
+cudaError_t fork(spgemm_plan_s *p) {
+  if (!p->side_ready) {
+    bool ok = true;
+    for (int i = 0; i < 4 && ok; ++i) ok = cudaStreamCreateWithFlags(&p->side[i], cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; i < 4 && ok; ++i) ok = cudaEventCreateWithFlags(&p->join_ev[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) return cudaGetLastError() == cudaSuccess ? cudaErrorUnknown : cudaGetLastError();
+    p->side_ready = true;
+  }
+  cudaError_t e = cudaEventRecord(p->fork_ev, p->stream);
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(p->side[i], p->fork_ev, 0);
+  return e;
+}
+
+cudaStream_t bin_stream(spgemm_plan_s *p, int i) { return p->side_ready ? p->side[i & 3] : p->stream; }
+
+cudaError_t join(spgemm_plan_s *p) {
+  if (!p->side_ready) return cudaSuccess;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
+    e = cudaEventRecord(p->join_ev[i], p->side[i]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->stream, p->join_ev[i], 0);
+  }
+  return e;
+}
+
 static size_t value_size(int dtype) { return dtype == SPGEMM_F32 ? 4 : 8; }
 
 // Values per numeric bitmap window: what shared memory holds after the
 // bitmap and its prefix counts (a little is kept for static shared data).
 int64_t bitmap_capacity(int dtype, int bm_words) {
-  const int64_t avail = (int64_t)max_smem_per_block() - 1024 - (int64_t)bm_words * 8;
+  const int64_t avail = (int64_t)max_smem_per_block() - kStaticSmemReserve - (int64_t)bm_words * 8;
   int64_t cap = avail / (int64_t)value_size(dtype);
   cap = (cap / 256) * 256;
   return cap > 0 ? cap : 0;
@@ -384,6 +424,14 @@ void free_events(spgemm_plan_s *p) {
 
 void free_ws(spgemm_plan_s *p) {
   free_events(p);
+  if (p->side_ready) {
+    for (int i = 0; i < 4; ++i) {
+      cudaStreamDestroy(p->side[i]);
+      cudaEventDestroy(p->join_ev[i]);
+    }
+    cudaEventDestroy(p->fork_ev);
+    p->side_ready = false;
+  }
   if (p->ws_fixed) cudaFreeAsync(p->ws_fixed, p->stream);
   if (p->bitmaps) cudaFreeAsync(p->bitmaps, p->stream);
   if (p->bm_items) cudaFreeAsync(p->bm_items, p->stream);
@@ -447,7 +495,7 @@ int spgemm_plan_create(spgemm_plan_t *out, const spgemm_csr *A, const spgemm_csr
   g_last_error.clear();
   if (!valid_csr_desc(A) || !valid_csr_desc(B) || A->ncols != B->nrows) return SPGEMM_ERR_INVALID_ARGUMENT;
   if (dtype != SPGEMM_I64 && dtype != SPGEMM_F32 && dtype != SPGEMM_F64) return SPGEMM_ERR_INVALID_ARGUMENT;
-  if (flags & ~(SPGEMM_SORTED | SPGEMM_VALIDATE | SPGEMM_TIMING)) return SPGEMM_ERR_INVALID_ARGUMENT;
+  if (flags & ~(SPGEMM_SORTED | SPGEMM_VALIDATE | SPGEMM_TIMING | SPGEMM_SERIAL)) return SPGEMM_ERR_INVALID_ARGUMENT;
 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

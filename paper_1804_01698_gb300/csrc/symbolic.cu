@@ -36,9 +36,12 @@ __device__ __forceinline__ int insert_key(int32_t *tab, uint32_t mask, int32_t c
 }
 
 template <int S>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 8)
     k_sym_warp(Args a, const int32_t *__restrict__ rows, int64_t nrows, int32_t *__restrict__ nnz_row) {
   extern __shared__ int32_t sm_sym_warp[];
+  __shared__ int2 s_meta[kWarpsPerBlock][32];
+  __shared__ int s_segoff[kWarpsPerBlock][33];
+  __shared__ int s_next[kWarpsPerBlock];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
   if (w >= nrows) return;  // whole warp leaves; no block barrier below
@@ -48,10 +51,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   const int32_t i = rows[w];
   const int G = a.G;
   int cnt = 0;
-  for_row_products<kU, false, int32_t>(a.arp[i], a.arp[i + 1], lane / G, 32 / G, lane & (G - 1), G, a.aci,
-                                       (const int32_t *)nullptr, a.brp, a.bci, (const int32_t *)nullptr,
-                                       (int32_t)a.k, a.err,
-                                       [&](int32_t c, int32_t, int32_t) { cnt += insert_key<false>(tab, S - 1, c, a.err); });
+  Stage<int32_t> st{s_meta[warp], nullptr, s_segoff[warp], &s_next[warp]};
+  warp_row_products<kU, false, int32_t>(a.arp[i], a.arp[i + 1], G, a.aci, (const int32_t *)nullptr, a.brp, a.bci,
+                                        (const int32_t *)nullptr, (int32_t)a.k, a.err, st,
+                                        [&](int32_t c, int32_t, int32_t) { cnt += insert_key<false>(tab, S - 1, c, a.err); });
   cnt = warp_sum(cnt);
   if (lane == 0) nnz_row[i] = cnt;
 }
@@ -61,15 +64,18 @@ __global__ void __launch_bounds__(1024, 1)
     k_sym_block(Args a, const int32_t *__restrict__ rows, int32_t *__restrict__ nnz_row) {
   extern __shared__ int32_t sm_sym_block[];
   __shared__ int red[33];
+  __shared__ int2 s_meta[kStageN];
+  __shared__ int s_segoff[kStageN + 1 + 8];
+  __shared__ int s_next;
   int32_t *tab = sm_sym_block;
   for (int s = threadIdx.x; s < S; s += blockDim.x) tab[s] = kEmpty;
   __syncthreads();
   const int32_t i = rows[blockIdx.x];
   const int G = a.G;
   int cnt = 0;
-  for_row_products<kU, false, int32_t>(a.arp[i], a.arp[i + 1], threadIdx.x / G, blockDim.x / G,
-                                       threadIdx.x & (G - 1), G, a.aci, (const int32_t *)nullptr, a.brp, a.bci,
-                                       (const int32_t *)nullptr, (int32_t)a.k, a.err,
+  block_row_products<kU, false, int32_t>(a.arp[i], a.arp[i + 1], G, a.aci, (const int32_t *)nullptr,
+                                         a.brp, a.bci, (const int32_t *)nullptr, (int32_t)a.k, a.err,
+                                         Stage<int32_t>{s_meta, nullptr, s_segoff, &s_next},
                                        [&](int32_t c, int32_t, int32_t) { cnt += insert_key<false>(tab, S - 1, c, a.err); });
   cnt = block_sum(cnt, red);
   if (threadIdx.x == 0) nnz_row[i] = cnt;
@@ -81,13 +87,16 @@ __global__ void __launch_bounds__(1024, 1)
                  uint32_t *__restrict__ bitmaps, int words) {
   extern __shared__ uint32_t sm_bm[];
   __shared__ int red[33];
+  __shared__ int2 s_meta[kStageN];
+  __shared__ int s_segoff[kStageN + 1 + 8];
+  __shared__ int s_next;
   for (int w = threadIdx.x; w < words; w += blockDim.x) sm_bm[w] = 0u;
   __syncthreads();
   const int32_t i = rows[blockIdx.x];
   const int G = a.G;
-  for_row_products<kU, false, int32_t>(a.arp[i], a.arp[i + 1], threadIdx.x / G, blockDim.x / G,
-                                       threadIdx.x & (G - 1), G, a.aci, (const int32_t *)nullptr, a.brp, a.bci,
-                                       (const int32_t *)nullptr, (int32_t)a.k, a.err,
+  block_row_products<kU, false, int32_t>(a.arp[i], a.arp[i + 1], G, a.aci, (const int32_t *)nullptr,
+                                         a.brp, a.bci, (const int32_t *)nullptr, (int32_t)a.k, a.err,
+                                         Stage<int32_t>{s_meta, nullptr, s_segoff, &s_next},
                                        [&](int32_t c, int32_t, int32_t) { atomicOr(sm_bm + (c >> 5), 1u << (c & 31)); });
   __syncthreads();
   int cnt = 0;
@@ -107,6 +116,9 @@ __global__ void __launch_bounds__(1024, 1)
     k_sym_global(Args a, const int32_t *__restrict__ rows, int64_t nrows, int32_t *__restrict__ nnz_row,
                  int32_t *__restrict__ tables, int64_t S) {
   __shared__ int red[33];
+  __shared__ int2 s_meta[kStageN];
+  __shared__ int s_segoff[kStageN + 1 + 8];
+  __shared__ int s_next;
   int32_t *tab = tables + (size_t)blockIdx.x * S;
   const uint32_t mask = (uint32_t)(S - 1);
   const int G = a.G;
@@ -115,9 +127,9 @@ __global__ void __launch_bounds__(1024, 1)
     __syncthreads();
     const int32_t i = rows[r];
     int cnt = 0;
-    for_row_products<kU, false, int32_t>(a.arp[i], a.arp[i + 1], threadIdx.x / G, blockDim.x / G,
-                                         threadIdx.x & (G - 1), G, a.aci, (const int32_t *)nullptr, a.brp, a.bci,
-                                         (const int32_t *)nullptr, (int32_t)a.k, a.err,
+    block_row_products<kU, false, int32_t>(a.arp[i], a.arp[i + 1], G, a.aci, (const int32_t *)nullptr,
+                                         a.brp, a.bci, (const int32_t *)nullptr, (int32_t)a.k, a.err,
+                                         Stage<int32_t>{s_meta, nullptr, s_segoff, &s_next},
                                          [&](int32_t c, int32_t, int32_t) { cnt += insert_key<true>(tab, mask, c, a.err); });
     cnt = block_sum(cnt, red);
     if (threadIdx.x == 0) nnz_row[i] = cnt;
@@ -125,71 +137,79 @@ __global__ void __launch_bounds__(1024, 1)
 }
 
 // ---------------------------------------------------------------------------
+// Raises the kernel's dynamic shared memory limit once per size (the
+// static arrays count against the default 48 KB as well).
 template <typename K>
 static cudaError_t prep(K kernel, size_t smem) {
-  if (smem > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  return cudaSuccess;
+  return set_dynamic_smem(reinterpret_cast<const void *>(kernel), smem);
 }
 
 template <int S>
-static cudaError_t sym_warp(spgemm_plan_s *p, const Args &a, const int32_t *rows, int64_t n) {
+static cudaError_t sym_warp(spgemm_plan_s *p, cudaStream_t st, const Args &a, const int32_t *rows, int64_t n) {
   const size_t smem = (size_t)kWarpsPerBlock * S * sizeof(int32_t);
   cudaError_t e = prep(k_sym_warp<S>, smem);
   if (e != cudaSuccess) return e;
   const int64_t blocks = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
   {
-    KernelScope ks(p, "sym_warp_" + std::to_string(S));
-    k_sym_warp<S><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, p->stream>>>(a, rows, n, p->nnz_row);
+    KernelScope ks(p, "sym_warp_" + std::to_string(S), st);
+    k_sym_warp<S><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, st>>>(a, rows, n, p->nnz_row);
   }
   return cudaGetLastError();
 }
 
 template <int S>
-static cudaError_t sym_block(spgemm_plan_s *p, const Args &a, const int32_t *rows, int64_t n, int threads) {
+static cudaError_t sym_block(spgemm_plan_s *p, cudaStream_t st, const Args &a, const int32_t *rows, int64_t n,
+                             int threads) {
   const size_t smem = (size_t)S * sizeof(int32_t);
   cudaError_t e = prep(k_sym_block<S>, smem);
   if (e != cudaSuccess) return e;
   {
-    KernelScope ks(p, "sym_block_" + std::to_string(S));
-    k_sym_block<S><<<(unsigned)n, threads, smem, p->stream>>>(a, rows, p->nnz_row);
+    KernelScope ks(p, "sym_block_" + std::to_string(S), st);
+    k_sym_block<S><<<(unsigned)n, threads, smem, st>>>(a, rows, p->nnz_row);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_symbolic(spgemm_plan_s *p) {
   Args a{p->m, p->n, p->k, p->arp, p->aci, p->brp, p->bci, p->av, p->bv, p->G, &p->dc->err};
-  cudaError_t e = cudaSuccess;
-  for (int b = 0; b < kNumSymBins && e == cudaSuccess; ++b) {
+  // heavy bins first, each bin on the next side stream
+  static const int order[kNumSymBins] = {kSymBitmapBin, kSymGlobalBin, 9, 8, 7, 6, 5, 4, 3, 2, 1, 0};
+  const bool concurrent = !(p->flags & SPGEMM_SERIAL);
+  cudaError_t e = concurrent ? fork(p) : cudaSuccess;
+  int launched = 0;
+  for (int o = 0; o < kNumSymBins && e == cudaSuccess; ++o) {
+    const int b = order[o];
     const int64_t n = p->sym_count[b];
     if (n == 0) continue;
     const int32_t *rows = p->perm + p->sym_off[b];
     const BinCfg &c = kSymBins[b];
+    cudaStream_t st = concurrent ? bin_stream(p, launched++) : p->stream;
     switch (b) {
-      case 0: e = sym_warp<64>(p, a, rows, n); break;
-      case 1: e = sym_warp<128>(p, a, rows, n); break;
-      case 2: e = sym_warp<256>(p, a, rows, n); break;
-      case 3: e = sym_warp<512>(p, a, rows, n); break;
-      case 4: e = sym_warp<1024>(p, a, rows, n); break;
-      case 5: e = sym_block<2048>(p, a, rows, n, c.threads); break;
-      case 6: e = sym_block<4096>(p, a, rows, n, c.threads); break;
-      case 7: e = sym_block<8192>(p, a, rows, n, c.threads); break;
-      case 8: e = sym_block<16384>(p, a, rows, n, c.threads); break;
-      case 9: e = sym_block<32768>(p, a, rows, n, c.threads); break;
+      case 0: e = sym_warp<64>(p, st, a, rows, n); break;
+      case 1: e = sym_warp<128>(p, st, a, rows, n); break;
+      case 2: e = sym_warp<256>(p, st, a, rows, n); break;
+      case 3: e = sym_warp<512>(p, st, a, rows, n); break;
+      case 4: e = sym_warp<1024>(p, st, a, rows, n); break;
+      case 5: e = sym_block<2048>(p, st, a, rows, n, c.threads); break;
+      case 6: e = sym_block<4096>(p, st, a, rows, n, c.threads); break;
+      case 7: e = sym_block<8192>(p, st, a, rows, n, c.threads); break;
+      case 8: e = sym_block<16384>(p, st, a, rows, n, c.threads); break;
+      case 9: e = sym_block<32768>(p, st, a, rows, n, c.threads); break;
       case kSymBitmapBin: {
         const size_t smem = (size_t)p->bm_words * sizeof(uint32_t);
         e = prep(k_sym_bitmap, smem);
         if (e != cudaSuccess) break;
         {
-          KernelScope ks(p, "sym_bitmap");
-          k_sym_bitmap<<<(unsigned)n, c.threads, smem, p->stream>>>(a, rows, p->nnz_row, p->bitmaps, p->bm_words);
+          KernelScope ks(p, "sym_bitmap", st);
+          k_sym_bitmap<<<(unsigned)n, c.threads, smem, st>>>(a, rows, p->nnz_row, p->bitmaps, p->bm_words);
         }
         e = cudaGetLastError();
         break;
       }
       case kSymGlobalBin: {
         {
-          KernelScope ks(p, "sym_global");
-          k_sym_global<<<(unsigned)p->gtab_blocks, c.threads, 0, p->stream>>>(a, rows, n, p->nnz_row,
+          KernelScope ks(p, "sym_global", st);
+          k_sym_global<<<(unsigned)p->gtab_blocks, c.threads, 0, st>>>(a, rows, n, p->nnz_row,
                                                                               (int32_t *)p->gtab, p->gtab_slots);
         }
         e = cudaGetLastError();
@@ -198,6 +218,7 @@ cudaError_t launch_symbolic(spgemm_plan_s *p) {
       default: break;
     }
   }
+  if (concurrent && e == cudaSuccess) e = join(p);
   return e;
 }
 
