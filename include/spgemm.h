@@ -198,6 +198,35 @@ SPGEMM_API int spgemm(const spgemm_csr *A, const spgemm_csr *B, int dtype, unsig
            spgemm_alloc_fn alloc, void *alloc_ctx,
            int32_t **c_row_ptr, int32_t **c_col_idx, void **c_vals, int64_t *nnz_c);
 
+/*
+ * Symbolic phase for callers that cannot allocate device memory.  The paper
+ * has no counterpart: this entry point exists for callers that must not
+ * reach the CUDA allocator while they run (code inside an allocator or
+ * memory-pool callback, a latency-bound loop that never calls into the
+ * driver's allocator, a host whose device memory is owned by another
+ * framework).
+ *
+ * Same result as spgemm_plan_create + spgemm_symbolic: c_row_ptr (device,
+ * A->nrows+1 int32, caller-owned) receives the row pointers of C = A*B and
+ * *nnz_c (host) receives nnz(C).  A and B are device CSR as for
+ * spgemm_plan_create; their values are not read.  Work is ordered on
+ * `stream`, which is synchronised once before the call returns.
+ *
+ * It allocates nothing: no cudaMalloc, no cudaFree, no allocating library
+ * routine.  Its scratch is one static device array of 32 MiB + 256 bytes
+ * that every GPU holds from the moment the library is loaded on it until the
+ * process exits.  That array holds 64 hash tables of 131072 keys; a row of C
+ * whose key bound min(flop_i, ncols(B)) is 131072 or more is refused with
+ * SPGEMM_ERR_INVALID_ARGUMENT and a message in spgemm_last_error().
+ *
+ * The first call on a device looks up the array's device address; make
+ * that first call before any stream capture.  Every call shares the array
+ * (the call clears the counters it needs): calls that overlap on the GPU,
+ * from different streams or threads, race and give wrong results.
+ */
+SPGEMM_API int spgemm_symbolic_noalloc(const spgemm_csr *A, const spgemm_csr *B, int32_t *c_row_ptr,
+                                       int64_t *nnz_c, void *stream);
+
 /* Human-readable name of a status code (static string). */
 SPGEMM_API const char *spgemm_status_string(int status);
 

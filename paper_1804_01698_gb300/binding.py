@@ -65,7 +65,7 @@ ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 EXPORTED = ("spgemm_plan_create", "spgemm_symbolic", "spgemm_numeric", "spgemm_plan_destroy",
             "spgemm_plan_workspace_bytes", "spgemm_plan_stats", "spgemm_plan_row_flop", "spgemm_plan_sym_bins",
             "spgemm_plan_row_nnz", "spgemm_plan_kernel_times", "spgemm", "spgemm_status_string",
-            "spgemm_last_error")
+            "spgemm_last_error", "spgemm_symbolic_noalloc")
 
 
 def library_path() -> str:
@@ -94,6 +94,7 @@ def library():
     lib.spgemm_plan_sym_bins.argtypes = [P, P, P]
     lib.spgemm_plan_row_nnz.argtypes = [P, P]
     lib.spgemm_plan_kernel_times.argtypes = [P, ctypes.POINTER(KernelTime), I32, ctypes.POINTER(I32)]
+    lib.spgemm_symbolic_noalloc.argtypes = [ctypes.POINTER(CsrDesc), ctypes.POINTER(CsrDesc), P, ctypes.POINTER(I64), P]
     lib.spgemm.argtypes = [ctypes.POINTER(CsrDesc), ctypes.POINTER(CsrDesc), I32, ctypes.c_uint, P, ALLOC_FN, P,
                            ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(I64)]
     for name in EXPORTED:
@@ -298,6 +299,21 @@ def spgemm_plan_row_nnz(plan: Plan) -> torch.Tensor:
 
 def spgemm_status_string(status: int) -> str:
     return library().spgemm_status_string(status).decode()
+
+
+def spgemm_symbolic_noalloc(A: DeviceCSR, B: DeviceCSR, c_row_ptr: torch.Tensor, stream=None) -> int:
+    """Row pointers of C = A*B into the caller's c_row_ptr (int32, A.nrows+1, on A's
+    device) without any device allocation by the library; returns nnz(C).
+    For callers that must not allocate device memory while they run: the
+    library uses a static device array instead (one call at a time per GPU)."""
+    lib = library()
+    a, b = A.desc(), B.desc()
+    nnz = ctypes.c_int64()
+    s = stream if stream is not None else torch.cuda.current_stream(A.row_ptr.device)
+    with torch.cuda.device(A.row_ptr.device):
+        _check(lib.spgemm_symbolic_noalloc(ctypes.byref(a), ctypes.byref(b), c_row_ptr.data_ptr(), ctypes.byref(nnz),
+                                           _stream_ptr(s)), "spgemm_symbolic_noalloc")
+    return int(nnz.value)
 
 
 def spgemm(A: DeviceCSR, B: DeviceCSR, sorted_output: bool = True, stream=None) -> DeviceCSR:

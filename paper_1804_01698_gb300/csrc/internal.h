@@ -181,5 +181,7 @@ int64_t bitmap_capacity(int dtype, int bm_words);
 // Raises a kernel's dynamic shared memory limit to at least `bytes` (once per
 // kernel, device and size; the static arrays count against the default 48 KB).
 cudaError_t set_dynamic_smem(const void *kernel, size_t bytes);
+// Text returned by spgemm_last_error() on this thread.
+void set_last_error(const std::string &text);
 int max_smem_per_block();
 }  // namespace sg

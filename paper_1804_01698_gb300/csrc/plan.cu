@@ -349,11 +349,15 @@ int64_t bitmap_capacity(int dtype, int bm_words) {
 
 }  // namespace sg
 
+namespace {
+thread_local std::string g_last_error;
+}  // namespace
+
+void sg::set_last_error(const std::string &text) { g_last_error = text; }
+
 using namespace sg;
 
 namespace {
-
-thread_local std::string g_last_error;
 
 int fail_cuda(cudaError_t e, const char *where) {
   g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
