@@ -158,14 +158,12 @@ def kernel_units(name: str, stats: dict) -> tuple[int, str]:
     """Useful multiply-adds (products) one launch of `name` performs, from the
     plan's per-bin flop totals."""
     kind, _, size = name.rpartition("_")
-    if name == "num_bitmap":
-        return stats["num_bin_flop"][9], "numeric"
-    if name == "num_global":
-        return stats["num_bin_flop"][10], "numeric"
-    if name == "sym_bitmap":
-        return stats["sym_bin_flop"][10], "symbolic"
-    if name == "sym_global":
-        return stats["sym_bin_flop"][11], "symbolic"
+    named = {"num_bitmap_l": ("num", 9), "num_global": ("num", 10), "num_bitmap_s": ("num", 11),
+             "num_bitmap_m": ("num", 12), "sym_bitmap_heavy": ("sym", 10), "sym_bitmap_mid": ("sym", 11),
+             "sym_global": ("sym", 12)}
+    if name in named:
+        phase, b = named[name]
+        return stats[f"{phase}_bin_flop"][b], "numeric" if phase == "num" else "symbolic"
     if size.isdigit():
         table = int(size)
         if kind.startswith("num_"):

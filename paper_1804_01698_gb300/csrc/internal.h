@@ -33,13 +33,19 @@ struct BinCfg {
   int64_t cap;  // largest bound this bin accepts
 };
 
-constexpr int kNumHashBins = 10;  // warp 64..1024, block 2048..32768
-constexpr int kSymBitmapBin = 10;
-constexpr int kSymGlobalBin = 11;
-constexpr int kNumSymBins = 12;
-constexpr int kNumBitmapBin = 9;   // numeric bins 0..8 are hash bins
+constexpr int kNumHashBins = 10;     // warp 64..1024, block 2048..32768
+constexpr int kSymBitmapBin = 10;    // bitmap rows with bound > kBitmapMidMax (1024 threads)
+constexpr int kSymBitmapMidBin = 11; // bitmap rows with bound <= kBitmapMidMax (256 threads)
+constexpr int kSymGlobalBin = 12;
+constexpr int kNumSymBins = 13;
+// numeric bins 0..8 are hash bins; bitmap rows become work items in three
+// classes by row size: small (3 blocks per SM), medium (2), large (1, rank
+// windows for rows longer than one block holds)
+constexpr int kNumBitmapBin = 9;     // large class
 constexpr int kNumGlobalBin = 10;
-constexpr int kNumNumBins = 11;
+constexpr int kNumBitmapSBin = 11;   // small class
+constexpr int kNumBitmapMBin = 12;   // medium class
+constexpr int kNumNumBins = 13;
 constexpr int kWarpsPerBlock = 4;  // warp bins: rows per block
 // shared memory kept free beside a bitmap kernel's dynamic allocation for
 // its static arrays (staging of 256 entries, reductions)
@@ -52,10 +58,13 @@ extern const BinCfg kSymBins[kNumSymBins];
 // Numeric bins 0..8: tables 64 .. 16384 slots, same load factors.
 extern const BinCfg kNumBins[kNumNumBins];
 
-// Heavy-row threshold: rows whose bound exceeds the largest numeric block
-// table go to the heavy bins (the symbolic bitmap bin takes them early so
-// that its bitmaps can be reused by the numeric phase).
-constexpr int64_t kHeavyBound = 12288;       // 3/4 of 16384
+// Rows whose symbolic bound exceeds kBitmapMinBound use a column bitmap
+// when B has at most kBitmapMaxCols columns: the symbolic phase builds and
+// saves the bitmap, the numeric phase turns it into output positions.
+// Without bitmaps, rows above the largest shared-memory table (3/4 of 32768
+// keys) use global-memory hash tables.
+constexpr int64_t kBitmapMinBound = 3072;
+constexpr int64_t kBitmapMidMax = 24576;
 constexpr int64_t kBlockSymMax = 24576;      // 3/4 of 32768 (global-table inputs)
 constexpr int64_t kBitmapMaxCols = 1 << 18;  // bitmap + prefix <= 64 KB
 
@@ -72,8 +81,9 @@ struct DevCounters {
   unsigned long long max_bound_global;  // largest symbolic bound in the global bin
   unsigned long long nnz_c;
   unsigned long long max_nnz_global;    // largest nnz in the numeric global bin
-  unsigned long long bm_items;          // numeric bitmap work items (row windows)
-  unsigned long long bm_cursor;
+  unsigned long long bm_items[3];       // numeric bitmap work items per class (small, medium, large)
+  unsigned long long bm_cursor[3];
+  unsigned long long bm_flop[3];        // flop of the rows of each class
   unsigned int err;
   unsigned int pad;
 };
@@ -127,7 +137,9 @@ struct spgemm_plan_s {
   int64_t num_count[sg::kNumNumBins], num_off[sg::kNumNumBins + 1];
   int64_t sym_flop[sg::kNumSymBins], num_flop[sg::kNumNumBins];
   int64_t total_flop, max_flop, nnz_c;
-  int64_t bm_cap;  // values per numeric bitmap window
+  int64_t bm_cap[3];      // values per numeric bitmap window, per class
+  int bm_threads[3];       // threads per block, per class
+  int64_t bm_item_off[4];  // item offsets per class
   int32_t launches;
   const int32_t *c_rp;
 
@@ -177,7 +189,7 @@ cudaError_t join(spgemm_plan_s *p);
 // Launchers (return a cudaError_t from the launch).
 cudaError_t launch_symbolic(spgemm_plan_s *p);
 cudaError_t launch_numeric(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_ci, void *c_v);
-int64_t bitmap_capacity(int dtype, int bm_words);
+int64_t bitmap_capacity(int dtype, int bm_words, int64_t budget);
 // Raises a kernel's dynamic shared memory limit to at least `bytes` (once per
 // kernel, device and size; the static arrays count against the default 48 KB).
 cudaError_t set_dynamic_smem(const void *kernel, size_t bytes);

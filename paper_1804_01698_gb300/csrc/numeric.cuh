@@ -432,7 +432,8 @@ template <typename T>
 cudaError_t launch_numeric_t(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_ci, T *c_v) {
   Args a{p->m, p->n, p->k, p->arp, p->aci, p->brp, p->bci, p->av, p->bv, p->G, &p->dc->err};
   // heavy bins first, each bin on the next side stream
-  static const int order[kNumNumBins] = {kNumBitmapBin, kNumGlobalBin, 8, 7, 6, 5, 4, 3, 2, 1, 0};
+  static const int order[kNumNumBins] = {kNumBitmapBin, kNumBitmapMBin, kNumBitmapSBin, kNumGlobalBin, 8, 7, 6, 5,
+                                         4, 3, 2, 1, 0};
   const bool concurrent = !(p->flags & SPGEMM_SERIAL);
   cudaError_t e = concurrent ? fork(p) : cudaSuccess;
   int launched = 0;
@@ -453,15 +454,18 @@ cudaError_t launch_numeric_t(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_c
       case 6: e = num_block<T, 4096>(p, st, a, rows, n, c.threads, c_rp, c_ci, c_v); break;
       case 7: e = num_block<T, 8192>(p, st, a, rows, n, c.threads, c_rp, c_ci, c_v); break;
       case 8: e = num_block<T, 16384>(p, st, a, rows, n, c.threads, c_rp, c_ci, c_v); break;
+      case kNumBitmapSBin:
+      case kNumBitmapMBin:
       case kNumBitmapBin: {
-        const size_t smem = (size_t)p->bm_cap * sizeof(T) + (size_t)p->bm_words * 8;
+        const int cls = b == kNumBitmapSBin ? 0 : b == kNumBitmapMBin ? 1 : 2;
+        const size_t smem = (size_t)p->bm_cap[cls] * sizeof(T) + (size_t)p->bm_words * 8;
         e = prep_num(k_num_bitmap<T>, smem);
         if (e != cudaSuccess) break;
         {
-          KernelScope ks(p, "num_bitmap", st);
-          k_num_bitmap<T><<<(unsigned)n, c.threads, smem, st>>>(a, p->perm + p->sym_off[kSymBitmapBin],
-                                                                       p->bm_items, p->bitmaps, p->bm_words,
-                                                                       (int)p->bm_cap, c_rp, c_ci, c_v);
+          KernelScope ks(p, cls == 0 ? "num_bitmap_s" : cls == 1 ? "num_bitmap_m" : "num_bitmap_l", st);
+          k_num_bitmap<T><<<(unsigned)n, p->bm_threads[cls], smem, st>>>(
+              a, p->perm + p->sym_off[kSymBitmapBin], p->bm_items + p->bm_item_off[cls], p->bitmaps, p->bm_words,
+              (int)p->bm_cap[cls], c_rp, c_ci, c_v);
         }
         e = cudaGetLastError();
         break;

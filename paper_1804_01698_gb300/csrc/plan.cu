@@ -32,7 +32,8 @@ const BinCfg kSymBins[kNumSymBins] = {
     {kWarp, 1024, kWarpsPerBlock * 32, 512},   {kBlock, 2048, 256, 1536},
     {kBlock, 4096, 512, 3072},                 {kBlock, 8192, 1024, 6144},
     {kBlock, 16384, 1024, 12288},              {kBlock, 32768, 1024, 24576},
-    {kBitmap, 0, 1024, INT64_MAX},             {kGlobal, 0, 1024, INT64_MAX}};
+    {kBitmap, 0, 1024, INT64_MAX},             {kBitmap, 0, 256, kBitmapMidMax},
+    {kGlobal, 0, 1024, INT64_MAX}};
 
 const BinCfg kNumBins[kNumNumBins] = {
     {kWarp, 64, kWarpsPerBlock * 32, 32},      {kWarp, 128, kWarpsPerBlock * 32, 64},
@@ -40,7 +41,8 @@ const BinCfg kNumBins[kNumNumBins] = {
     {kWarp, 1024, kWarpsPerBlock * 32, 512},   {kBlock, 2048, 256, 1536},
     {kBlock, 4096, 512, 3072},                 {kBlock, 8192, 1024, 6144},
     {kBlock, 16384, 1024, 12288},              {kBitmap, 0, 1024, INT64_MAX},
-    {kGlobal, 0, 1024, INT64_MAX}};
+    {kGlobal, 0, 1024, INT64_MAX},             {kBitmap, 0, 512, INT64_MAX},
+    {kBitmap, 0, 1024, INT64_MAX}};
 
 cudaError_t launch_numeric_f64(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_ci, void *c_v);
 cudaError_t launch_numeric_f32(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_ci, void *c_v);
@@ -57,11 +59,15 @@ __device__ __forceinline__ int hash_bin_of(int64_t b) {
 
 __device__ __forceinline__ int sym_bin_of(int64_t b, bool bitmap_ok) {
   if (b <= 0) return 255;
+  if (bitmap_ok && b > kBitmapMinBound) return b > kBitmapMidMax ? kSymBitmapBin : kSymBitmapMidBin;
   const int t = hash_bin_of(b);
   if (t < 9) return t;
-  if (bitmap_ok) return kSymBitmapBin;
   if (b <= kBlockSymMax) return 9;
   return kSymGlobalBin;
+}
+
+__device__ __forceinline__ bool is_bitmap_row(int sym_bin) {
+  return sym_bin == kSymBitmapBin || sym_bin == kSymBitmapMidBin;
 }
 
 __device__ __forceinline__ int num_bin_of(int64_t nnz) {
@@ -70,7 +76,9 @@ __device__ __forceinline__ int num_bin_of(int64_t nnz) {
   return t < 9 ? t : kNumGlobalBin;
 }
 
-// 8 lanes per row of A, 32 rows per 256-thread block.
+// One warp per row of A, 8 rows per 256-thread block; every lane keeps four
+// independent gathers of B's row_ptr in flight, so a long row of A costs
+// len/128 dependent steps instead of len/8.
 __global__ void __launch_bounds__(256)
     k_row_flop(Args a, int64_t nnz_a, int64_t nnz_b, int bitmap_ok, int64_t *__restrict__ flop,
                uint8_t *__restrict__ rbin, int32_t *__restrict__ nnz_row, DevCounters *dc) {
@@ -83,8 +91,8 @@ __global__ void __launch_bounds__(256)
   }
   if (threadIdx.x == 0) s_tot = s_max = s_maxg = 0;
   __syncthreads();
-  const int sub = threadIdx.x & 7;
-  const int64_t row = (int64_t)blockIdx.x * 32 + (threadIdx.x >> 3);
+  const int sub = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   int64_t f = 0;
   if (row < a.m) {
     int64_t r0 = a.arp[row], r1 = a.arp[row + 1];
@@ -92,23 +100,29 @@ __global__ void __launch_bounds__(256)
       if (sub == 0) raise_err(a.err, kErrCsr);
       r0 = r1 = 0;
     }
-    for (int64_t j = r0 + sub; j < r1; j += 8) {
-      const int32_t kk = a.aci[j];
-      if ((uint64_t)(int64_t)kk >= (uint64_t)a.n) {
-        raise_err(a.err, kErrCsr);
-        continue;
+    for (int64_t j0 = r0 + sub; j0 < r1; j0 += 128) {
+      int32_t kk[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) kk[u] = j0 + 32 * u < r1 ? __ldg(a.aci + j0 + 32 * u) : -1;
+      int64_t b0[4], b1[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool ok = j0 + 32 * u < r1 && (uint64_t)(int64_t)kk[u] < (uint64_t)a.n;
+        b0[u] = ok ? __ldg(a.brp + kk[u]) : 0;
+        b1[u] = ok ? __ldg(a.brp + kk[u] + 1) : 0;
+        if (j0 + 32 * u < r1 && !ok) raise_err(a.err, kErrCsr);
       }
-      const int64_t b0 = a.brp[kk], b1 = a.brp[kk + 1];
-      if (!(0 <= b0 && b0 <= b1 && b1 <= nnz_b)) {
-        raise_err(a.err, kErrCsr);
-        continue;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (!(0 <= b0[u] && b0[u] <= b1[u] && b1[u] <= nnz_b)) {
+          raise_err(a.err, kErrCsr);
+          continue;
+        }
+        f += b1[u] - b0[u];
       }
-      f += b1 - b0;
     }
   }
-  f += __shfl_xor_sync(0xffffffffu, f, 4);
-  f += __shfl_xor_sync(0xffffffffu, f, 2);
-  f += __shfl_xor_sync(0xffffffffu, f, 1);
+  f = warp_sum(f);
   if (sub == 0 && row < a.m) {
     flop[row] = f;
     const int64_t bound = f < a.k ? f : a.k;
@@ -228,12 +242,10 @@ __global__ void __launch_bounds__(256)
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < m) {
     int b = 255;
-    if (rbin[i] != kSymBitmapBin) {
+    if (!is_bitmap_row(rbin[i])) {
       const int32_t z = nnz_row[i];
       b = num_bin_of(z);
       if (b == kNumGlobalBin) atomicMax(&s_maxg, (unsigned long long)z);
-    } else if (nnz_row[i] > 0) {
-      atomicAdd(&hflop[kNumBitmapBin], (unsigned long long)flop[i]);  // rows of the bitmap items
     }
     rbin2[i] = (uint8_t)b;
     if (b != 255) {
@@ -247,26 +259,62 @@ __global__ void __launch_bounds__(256)
   if (threadIdx.x == 0 && s_maxg) atomicMax(&dc->max_nnz_global, s_maxg);
 }
 
-__global__ void __launch_bounds__(256)
-    k_bm_items_count(const int32_t *__restrict__ rows, int64_t n, const int32_t *__restrict__ nnz_row, int cap,
-                     DevCounters *dc) {
-  __shared__ long long red[33];
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  long long w = 0;
-  if (t < n) w = (nnz_row[rows[t]] + (long long)cap - 1) / cap;
-  w = block_sum(w, red);
-  if (threadIdx.x == 0 && w) atomicAdd(&dc->bm_items, (unsigned long long)w);
+struct BmCaps {
+  long long cap[3];  // small, medium, large (0 = class unused)
+  long long off[3];  // item offsets of the classes (fill only)
+};
+
+// Class of a bitmap row with nnz entries and its number of work items.
+__device__ __forceinline__ int bm_class(long long nnz, const BmCaps &c, long long *windows) {
+  if (nnz <= 0) {
+    *windows = 0;
+    return 0;
+  }
+  if (nnz <= c.cap[0]) {
+    *windows = 1;
+    return 0;
+  }
+  if (nnz <= c.cap[1]) {
+    *windows = 1;
+    return 1;
+  }
+  *windows = (nnz + c.cap[2] - 1) / c.cap[2];
+  return 2;
 }
 
 __global__ void __launch_bounds__(256)
-    k_bm_items_fill(const int32_t *__restrict__ rows, int64_t n, const int32_t *__restrict__ nnz_row, int cap,
+    k_bm_items_count(const int32_t *__restrict__ rows, int64_t n, const int32_t *__restrict__ nnz_row,
+                     const int64_t *__restrict__ flop, BmCaps caps, DevCounters *dc) {
+  __shared__ unsigned long long s_items[3], s_flop[3];
+  if (threadIdx.x < 3) s_items[threadIdx.x] = s_flop[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) {
+    const int32_t i = rows[t];
+    long long w;
+    const int c = bm_class(nnz_row[i], caps, &w);
+    if (w > 0) {
+      atomicAdd(&s_items[c], (unsigned long long)w);
+      atomicAdd(&s_flop[c], (unsigned long long)flop[i]);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 3 && s_items[threadIdx.x]) {
+    atomicAdd(&dc->bm_items[threadIdx.x], s_items[threadIdx.x]);
+    atomicAdd(&dc->bm_flop[threadIdx.x], s_flop[threadIdx.x]);
+  }
+}
+
+__global__ void __launch_bounds__(256)
+    k_bm_items_fill(const int32_t *__restrict__ rows, int64_t n, const int32_t *__restrict__ nnz_row, BmCaps caps,
                     DevCounters *dc, int2 *__restrict__ items) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
-  const int w = (int)((nnz_row[rows[t]] + (long long)cap - 1) / cap);
+  long long w;
+  const int c = bm_class(nnz_row[rows[t]], caps, &w);
   if (w == 0) return;
-  const unsigned long long base = atomicAdd(&dc->bm_cursor, (unsigned long long)w);
-  for (int q = 0; q < w; ++q) items[base + q] = make_int2((int)t, q);
+  const unsigned long long base = caps.off[c] + atomicAdd(&dc->bm_cursor[c], (unsigned long long)w);
+  for (int q = 0; q < (int)w; ++q) items[base + q] = make_int2((int)t, q);
 }
 
 // ---------------------------------------------------------------------------
@@ -338,10 +386,11 @@ cudaError_t join(spgemm_plan_s *p) {
 
 static size_t value_size(int dtype) { return dtype == SPGEMM_F32 ? 4 : 8; }
 
-// Values per numeric bitmap window: what shared memory holds after the
-// bitmap and its prefix counts (a little is kept for static shared data).
-int64_t bitmap_capacity(int dtype, int bm_words) {
-  const int64_t avail = (int64_t)max_smem_per_block() - kStaticSmemReserve - (int64_t)bm_words * 8;
+// Values per numeric bitmap window for a block of `budget` bytes of shared
+// memory: what remains after the bitmap with its prefix counts and the
+// block's static arrays.
+int64_t bitmap_capacity(int dtype, int bm_words, int64_t budget) {
+  const int64_t avail = budget - kStaticSmemReserve - (int64_t)bm_words * 8;
   int64_t cap = avail / (int64_t)value_size(dtype);
   cap = (cap / 256) * 256;
   return cap > 0 ? cap : 0;
@@ -528,12 +577,17 @@ int spgemm_plan_create(spgemm_plan_t *out, const spgemm_csr *A, const spgemm_csr
   p->flags = flags;
   p->stream = (cudaStream_t)stream;
   p->device = dev;
-  const double avg_b = p->n > 0 ? (double)p->nnz_b / (double)p->n : 0.0;
-  p->G = avg_b >= 24 ? 32 : avg_b >= 12 ? 16 : avg_b >= 6 ? 8 : 4;
+  p->G = 32;  // set from the flop pass below
   p->bitmap_ok = p->k <= kBitmapMaxCols;
   p->bm_words = (int)((p->k + 31) / 32);
-  p->bm_cap = bitmap_capacity(dtype, p->bm_words);
-  if (p->bitmap_ok && p->bm_cap < 256) p->bitmap_ok = false;
+  // bitmap classes: 3, 2 and 1 blocks per SM (228 KB per SM, 1 KB per block kept by the system)
+  p->bm_cap[2] = bitmap_capacity(dtype, p->bm_words, max_smem_per_block());
+  p->bm_cap[1] = bitmap_capacity(dtype, p->bm_words, 110 * 1024);
+  p->bm_cap[0] = bitmap_capacity(dtype, p->bm_words, 72 * 1024);
+  p->bm_threads[0] = kNumBins[kNumBitmapSBin].threads;
+  p->bm_threads[1] = kNumBins[kNumBitmapMBin].threads;
+  p->bm_threads[2] = kNumBins[kNumBitmapBin].threads;
+  if (p->bitmap_ok && p->bm_cap[2] < 256) p->bitmap_ok = false;
 
   // fixed workspace: counters, then per-row arrays
   const int64_t m = p->m;
@@ -580,7 +634,7 @@ int spgemm_plan_create(spgemm_plan_t *out, const spgemm_csr *A, const spgemm_csr
     Args a{p->m, p->n, p->k, p->arp, p->aci, p->brp, p->bci, p->av, p->bv, p->G, &p->dc->err};
     {
       KernelScope ks(p, "row_flop");
-      k_row_flop<<<(unsigned)((m + 31) / 32), 256, 0, p->stream>>>(a, p->nnz_a, p->nnz_b, p->bitmap_ok ? 1 : 0,
+      k_row_flop<<<(unsigned)((m + 7) / 8), 256, 0, p->stream>>>(a, p->nnz_a, p->nnz_b, p->bitmap_ok ? 1 : 0,
                                                                     p->flop, p->rbin, p->nnz_row, p->dc);
     }
     e = cudaGetLastError();
@@ -590,14 +644,19 @@ int spgemm_plan_create(spgemm_plan_t *out, const spgemm_csr *A, const spgemm_csr
   if (rc == SPGEMM_OK) {
     p->total_flop = (int64_t)p->hc->total_flop;
     p->max_flop = (int64_t)p->hc->max_flop;
+    // lanes per stored a_ik: the mean length of the B rows the products come
+    // from (flop / nnz(A)), so that long rows get whole warps
+    const double per_entry = p->nnz_a > 0 ? (double)p->total_flop / (double)p->nnz_a : 0.0;
+    p->G = per_entry >= 24 ? 32 : per_entry >= 12 ? 16 : per_entry >= 6 ? 8 : 4;
     p->sym_off[0] = 0;
     for (int b = 0; b < kNumSymBins; ++b) {
       p->sym_flop[b] = (int64_t)p->hc->sym_flop[b];
       p->sym_count[b] = (int64_t)p->hc->sym_count[b];
       p->sym_off[b + 1] = p->sym_off[b] + p->sym_count[b];
     }
-    if (p->sym_count[kSymBitmapBin] > 0) {
-      p->bitmaps_bytes = (size_t)p->sym_count[kSymBitmapBin] * p->bm_words * 4;
+    const int64_t nbm = p->sym_count[kSymBitmapBin] + p->sym_count[kSymBitmapMidBin];
+    if (nbm > 0) {
+      p->bitmaps_bytes = (size_t)nbm * p->bm_words * 4;
       e = cudaMallocAsync((void **)&p->bitmaps, p->bitmaps_bytes, p->stream);
       if (e != cudaSuccess) {
         p->bitmaps = nullptr;
@@ -660,11 +719,12 @@ int spgemm_symbolic(spgemm_plan_t p, int32_t *c_row_ptr, int64_t *nnz_c) {
       k_num_classify<<<(unsigned)((m + 255) / 256), 256, 0, p->stream>>>(p->nnz_row, p->rbin, p->flop, m, p->rbin2,
                                                                          p->dc);
     }
-    const int64_t nbm = p->sym_count[kSymBitmapBin];
+    const int64_t nbm = p->sym_count[kSymBitmapBin] + p->sym_count[kSymBitmapMidBin];
     if (nbm > 0) {
       KernelScope ks(p, "bm_items_count");
+      BmCaps caps{{p->bm_cap[0], p->bm_cap[1], p->bm_cap[2]}, {0, 0, 0}};
       k_bm_items_count<<<(unsigned)((nbm + 255) / 256), 256, 0, p->stream>>>(
-          p->perm + p->sym_off[kSymBitmapBin], nbm, p->nnz_row, (int)p->bm_cap, p->dc);
+          p->perm + p->sym_off[kSymBitmapBin], nbm, p->nnz_row, p->flop, caps, p->dc);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail_cuda(e, "row_ptr scan");
@@ -678,8 +738,14 @@ int spgemm_symbolic(spgemm_plan_t p, int32_t *c_row_ptr, int64_t *nnz_c) {
     p->num_count[b] = (int64_t)p->hc->num_count[b];
     p->num_off[b + 1] = p->num_off[b] + p->num_count[b];
   }
-  // the bitmap bin holds work items (row, rank window), not rows of perm2
-  p->num_count[kNumBitmapBin] = (int64_t)p->hc->bm_items;
+  // the bitmap bins hold work items (row, rank window), not rows of perm2
+  const int bm_bins[3] = {kNumBitmapSBin, kNumBitmapMBin, kNumBitmapBin};
+  p->bm_item_off[0] = 0;
+  for (int c = 0; c < 3; ++c) {
+    p->num_count[bm_bins[c]] = (int64_t)p->hc->bm_items[c];
+    p->num_flop[bm_bins[c]] = (int64_t)p->hc->bm_flop[c];
+    p->bm_item_off[c + 1] = p->bm_item_off[c] + p->num_count[bm_bins[c]];
+  }
   *nnz_c = p->nnz_c;
   p->c_rp = c_row_ptr;
   p->state = 1;
@@ -695,7 +761,7 @@ int spgemm_numeric(spgemm_plan_t p, const int32_t *c_row_ptr, int32_t *c_col_idx
   cudaError_t e = cudaSuccess;
   int rc = SPGEMM_OK;
   if (p->nnz_c > 0) {
-    const int64_t nitems = p->num_count[kNumBitmapBin];
+    const int64_t nitems = p->bm_item_off[3];
     if (nitems > 0) {
       p->bm_items_bytes = (size_t)nitems * sizeof(int2);
       e = cudaMallocAsync((void **)&p->bm_items, p->bm_items_bytes, p->stream);
@@ -703,10 +769,11 @@ int spgemm_numeric(spgemm_plan_t p, const int32_t *c_row_ptr, int32_t *c_col_idx
         p->bm_items = nullptr;
         return fail_cuda(e, "allocating bitmap work items");
       }
-      const int64_t nbm = p->sym_count[kSymBitmapBin];
+      const int64_t nbm = p->sym_count[kSymBitmapBin] + p->sym_count[kSymBitmapMidBin];
       KernelScope ks(p, "bm_items_fill");
+      BmCaps caps{{p->bm_cap[0], p->bm_cap[1], p->bm_cap[2]}, {p->bm_item_off[0], p->bm_item_off[1], p->bm_item_off[2]}};
       k_bm_items_fill<<<(unsigned)((nbm + 255) / 256), 256, 0, p->stream>>>(
-          p->perm + p->sym_off[kSymBitmapBin], nbm, p->nnz_row, (int)p->bm_cap, p->dc, p->bm_items);
+          p->perm + p->sym_off[kSymBitmapBin], nbm, p->nnz_row, caps, p->dc, p->bm_items);
     }
     if (p->num_count[kNumGlobalBin] > 0) {
       const int64_t slots = pow2_above((int64_t)p->hc->max_nnz_global * 4 / 3);

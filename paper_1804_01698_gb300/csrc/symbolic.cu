@@ -173,7 +173,7 @@ static cudaError_t sym_block(spgemm_plan_s *p, cudaStream_t st, const Args &a, c
 cudaError_t launch_symbolic(spgemm_plan_s *p) {
   Args a{p->m, p->n, p->k, p->arp, p->aci, p->brp, p->bci, p->av, p->bv, p->G, &p->dc->err};
   // heavy bins first, each bin on the next side stream
-  static const int order[kNumSymBins] = {kSymBitmapBin, kSymGlobalBin, 9, 8, 7, 6, 5, 4, 3, 2, 1, 0};
+  static const int order[kNumSymBins] = {kSymBitmapBin, kSymBitmapMidBin, kSymGlobalBin, 9, 8, 7, 6, 5, 4, 3, 2, 1, 0};
   const bool concurrent = !(p->flags & SPGEMM_SERIAL);
   cudaError_t e = concurrent ? fork(p) : cudaSuccess;
   int launched = 0;
@@ -195,13 +195,16 @@ cudaError_t launch_symbolic(spgemm_plan_s *p) {
       case 7: e = sym_block<8192>(p, st, a, rows, n, c.threads); break;
       case 8: e = sym_block<16384>(p, st, a, rows, n, c.threads); break;
       case 9: e = sym_block<32768>(p, st, a, rows, n, c.threads); break;
-      case kSymBitmapBin: {
+      case kSymBitmapBin:
+      case kSymBitmapMidBin: {
+        // bitmaps of both bins are stored in perm order from the first bitmap bin on
         const size_t smem = (size_t)p->bm_words * sizeof(uint32_t);
         e = prep(k_sym_bitmap, smem);
         if (e != cudaSuccess) break;
         {
-          KernelScope ks(p, "sym_bitmap", st);
-          k_sym_bitmap<<<(unsigned)n, c.threads, smem, st>>>(a, rows, p->nnz_row, p->bitmaps, p->bm_words);
+          KernelScope ks(p, b == kSymBitmapBin ? "sym_bitmap_heavy" : "sym_bitmap_mid", st);
+          uint32_t *bm = p->bitmaps + (size_t)(p->sym_off[b] - p->sym_off[kSymBitmapBin]) * p->bm_words;
+          k_sym_bitmap<<<(unsigned)n, c.threads, smem, st>>>(a, rows, p->nnz_row, bm, p->bm_words);
         }
         e = cudaGetLastError();
         break;

@@ -40,6 +40,20 @@ def host_vals(m: CSR, dtype) -> CSR:
 
 # ------------------------------------------------------------ a1, a2, a3, a4
 
+def expected_sym_bin(bound: int, k: int):
+    """The documented symbolic bin rule: hash bins by key bound, column bitmaps
+    for rows above 3072 when B has at most 2^18 columns, global tables above
+    the largest shared-memory table otherwise."""
+    if bound <= 0:
+        return None
+    if k <= 1 << 18 and bound > 3072:
+        return 10 if bound > 24576 else 11
+    for b, cap in enumerate(HASH_CAPS):
+        if bound <= cap:
+            return b
+    return 9 if bound <= 24576 else 12
+
+
 @pytest.mark.parametrize("name", ["er", "rmat", "tall"])
 def test_flop_bins_counts_rowptr(name):
     from paper_1804_01698_gb300 import binding as sg
@@ -59,13 +73,11 @@ def test_flop_bins_counts_rowptr(name):
         perm = perm.cpu().numpy()
         bound = np.minimum(ref_flop, B.ncols)
         assert sorted(perm.tolist()) == np.nonzero(bound > 0)[0].tolist()     # a2: a permutation
-        lo = 0
-        for b, cap in enumerate(HASH_CAPS):                                   # a2: the bin rule
+        expect = np.array([-1 if b is None else b for b in (expected_sym_bin(int(x), B.ncols) for x in bound)])
+        for b in range(len(offs) - 1):                                        # a2: the bin rule
             rows = perm[offs[b]:offs[b + 1]]
-            assert np.all((bound[rows] > lo) & (bound[rows] <= cap)), b
-            lo = cap
-        heavy = perm[offs[len(HASH_CAPS)]:]
-        assert np.all(bound[heavy] > HASH_CAPS[-1])
+            assert np.all(expect[rows] == b), b
+            assert len(rows) == int((expect == b).sum()), b
         nnz_c = plan.symbolic()
         ref_nnz = oracle.symbolic(A, B)
         assert np.array_equal(plan.row_nnz().cpu().numpy(), ref_nnz)          # a3 bit-exact
@@ -109,6 +121,13 @@ def test_rmat16_f64(rmat16, sorted_output):
     A, B, expect = rmat16
     C, stats = gpu_product(A, B, torch.float64, sorted_output)
     assert stats["total_flop"] == GOLDEN["rmat16_ef16_f64"]["total_flop"]
+    # every kind of bin takes part: hash bins, both bitmap bins, all three
+    # bitmap item classes (small, medium, large)
+    assert all(stats["sym_bin_rows"][b] > 0 for b in range(7))
+    assert stats["sym_bin_rows"][10] > 0 and stats["sym_bin_rows"][11] > 0
+    assert all(stats["num_bin_rows"][b] > 0 for b in range(7))
+    assert all(stats["num_bin_rows"][b] > 0 for b in (9, 11, 12))
+    assert sum(stats["num_bin_flop"]) == stats["total_flop"]
     assert_matches_oracle(C, A, B, sorted_output, expect=expect)
     _golden_check(C, "rmat16_ef16_f64")
 
@@ -154,18 +173,6 @@ def test_float32_uniform_values_within_tolerance():
     assert_matches_oracle(C, A, A, True)
 
 
-def test_every_bin_is_exercised():
-    """The inputs above reach every symbolic and numeric bin; checked here on one
-    mixed input so that a bin that never runs does not go unnoticed."""
-    A = inputs.rmat(15, 16, seed=51)
-    C, st = gpu_product(A, A, torch.float64, True)
-    assert all(st["sym_bin_rows"][b] > 0 for b in range(9))
-    assert st["sym_bin_rows"][10] > 0            # bitmap heavy rows
-    assert all(st["num_bin_rows"][b] > 0 for b in range(9))
-    assert st["num_bin_rows"][9] > 0             # bitmap work items
-    assert_matches_oracle(C, A, A, True)
-
-
 # ------------------------------------------------------------ heavy rows
 
 def _heavy_rows(nrows_a, entries, ncols_b, b_row_len, seed):
@@ -202,7 +209,7 @@ def test_global_table_rows(sorted_output, dt):
         A, B = int_valued(A, 74), int_valued(B, 75)
     A, B = host_vals(A, dtype), host_vals(B, dtype)
     C, st = gpu_product(A, B, dtype, sorted_output)
-    assert st["sym_bin_rows"][11] == 5 and st["sym_bin_rows"][9] == 7
+    assert st["sym_bin_rows"][12] == 5 and st["sym_bin_rows"][9] == 7
     assert st["num_bin_rows"][10] >= 5
     assert_matches_oracle(C, A, B, sorted_output)
 
