@@ -179,53 +179,77 @@ __device__ __forceinline__ void for_row_products(int64_t a0, int64_t a1, int gro
 
 
 // ---------------------------------------------------------------------------
-// Staged, segmented row loop.  The stored a_ik of a row are processed in
-// rounds of up to kStageN entries.  Per round, the metadata of each entry
-// (start and length of row k of B, a_ik) is loaded cooperatively into shared
-// memory, so the dependent loads col_idx(A) -> row_ptr(B) are issued in
-// bulk.  Every B row is cut into segments of SEG = G * U * kSegIters entries
-// and the segments of the round are numbered by a prefix sum; groups of G
-// lanes claim segment numbers from a shared counter, find the owning entry
-// by binary search over the prefix, and stride over the segment with U loads
-// in flight per lane.  A long row of B is thereby shared by many groups and
-// no group waits for another at the end of the round.
+// Staged, flattened row loop.  The stored a_ik of a row are processed in
+// rounds of up to kStageN entries.  Per round, the start of row k of B and
+// a_ik of each entry are staged in shared memory (the dependent loads
+// col_idx(A) -> row_ptr(B) are issued in bulk), together with the exclusive
+// prefix sum of the B row lengths.  The round's products then form one
+// flat index range [0, total): product p belongs to the last entry e with
+// pre[e] <= p and reads B entry bstart[e] + (p - pre[e]).  Groups of G lanes
+// claim chunks of the range from a shared counter (dynamic balance); inside
+// a chunk lane l takes products l, l+G, l+2G, ..., finds its first entry by
+// binary search and then advances its entry cursor incrementally, so short
+// rows of B keep every lane busy and consecutive lanes still read
+// consecutive entries of B.  U products per lane are gathered before any is
+// handed to f(col, a_ik, b_kj).
 constexpr int kStageN = 256;  // entries staged per round (block form)
-constexpr int kSegIters = 2;  // strided iterations per claimed segment
 
-template <typename T> struct Stage {
-  int2 *meta;  // (start, length) of the B row of each staged entry
-  T *a;        // a_ik of each staged entry
-  int *segoff; // exclusive prefix of segment counts, one slot per entry + total
-  int *next;   // next unclaimed segment
+// One staged entry: products [start, end) of the round read B entries
+// off + p, and carry a_ik.  16 bytes, read with one shared-memory load.
+template <typename T> struct alignas(16) Entry {
+  int end;
+  int off;
+  T a;
 };
 
+template <typename T> struct Stage {
+  Entry<T> *ent;    // kStageN entries
+  int *next;        // next unclaimed chunk
+  long long *wsum;  // scratch for the scan (8 warp totals)
+};
+
+// Processes flat products [p0, p1) of a staged round of n entries, lane l
+// of the group taking p0 + l, p0 + l + G, ...  All indices of a round fit in
+// int32 (a round ends before its product count passes 2^31 - 1).
 template <int U, bool NEED_VAL, typename T, typename F>
-__device__ __forceinline__ void process_segment(const Stage<T> &st, int n, int seg, int SEG, int G, int lig,
-                                                const int32_t *__restrict__ bci, const T *__restrict__ bv,
-                                                int32_t ncols, uint32_t *err, F &&f) {
-  int lo = 0, hi = n - 1;  // largest e with segoff[e] <= seg
+__device__ __forceinline__ void process_flat(const Entry<T> *ent, int n, int p0, int p1, int G, int lig,
+                                             const int32_t *__restrict__ bci, const T *__restrict__ bv, int32_t ncols,
+                                             uint32_t *err, F &&f) {
+  int p = p0 + lig;
+  if (p >= p1) return;
+  int lo = 0, hi = n - 1;  // first entry e with end[e] > p
   while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (st.segoff[mid] <= seg) lo = mid;
-    else hi = mid - 1;
+    const int mid = (lo + hi) >> 1;
+    if (ent[mid].end > p) hi = mid;
+    else lo = mid + 1;
   }
-  const int2 m = st.meta[lo];
-  const T a = NEED_VAL ? st.a[lo] : T(0);
-  const int32_t q0 = m.x + (seg - st.segoff[lo]) * SEG;
-  const int32_t qe = min(m.x + m.y, q0 + SEG);
-  for (int32_t q = q0 + lig; q < qe; q += G * U) {
+  int e = lo;
+  Entry<T> cur = ent[e];
+  while (p < p1) {
+    int32_t q[U];
+    T au[U];
+    bool ok[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      ok[u] = p < p1;
+      if (ok[u]) {
+        while (p >= cur.end) cur = ent[++e];
+        q[u] = cur.off + p;
+        au[u] = cur.a;
+      }
+      p += G;
+    }
     int32_t c[U];
     T v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int32_t qq = q + u * G;
-      c[u] = qq < qe ? __ldg(bci + qq) : -1;
-      if (NEED_VAL) v[u] = qq < qe ? __ldg(bv + qq) : T(0);
+      c[u] = ok[u] ? __ldg(bci + q[u]) : -1;
+      if (NEED_VAL) v[u] = ok[u] ? __ldg(bv + q[u]) : T(0);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      if (q + u * G < qe) {
-        if ((uint32_t)c[u] < (uint32_t)ncols) f(c[u], a, NEED_VAL ? v[u] : T(0));
+      if (ok[u]) {
+        if ((uint32_t)c[u] < (uint32_t)ncols) f(c[u], NEED_VAL ? au[u] : T(0), NEED_VAL ? v[u] : T(0));
         else raise_err(err, kErrCsr);
       }
     }
@@ -233,8 +257,6 @@ __device__ __forceinline__ void process_segment(const Stage<T> &st, int n, int s
 }
 
 // Block-wide form: every thread of the block calls it (blockDim.x >= kStageN).
-// st.meta/st.a hold kStageN entries, st.segoff kStageN + 1, plus 8 ints of
-// scratch after them (st.segoff[kStageN + 1 ...]).
 template <int U, bool NEED_VAL, typename T, typename F>
 __device__ __forceinline__ void block_row_products(int64_t a0, int64_t a1, int G, const int32_t *__restrict__ aci,
                                                    const T *__restrict__ av, const int32_t *__restrict__ brp,
@@ -243,79 +265,86 @@ __device__ __forceinline__ void block_row_products(int64_t a0, int64_t a1, int G
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, lig = tid & (G - 1);
   const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
   const int leader = lane & ~(G - 1);
-  const int SEG = G * U * kSegIters;
-  int *wsum = st.segoff + kStageN + 1;  // 8 warp totals
-  for (int64_t j0 = a0; j0 < a1; j0 += kStageN) {
-    const int n = (int)((a1 - j0) < kStageN ? (a1 - j0) : kStageN);
-    int nseg = 0;
-    if (tid < n) {
+  const int ngroups = blockDim.x / G;
+  int64_t j0 = a0;
+  while (j0 < a1) {
+    const int n0 = (int)((a1 - j0) < kStageN ? (a1 - j0) : kStageN);
+    long long len = 0;
+    int32_t bs = 0;
+    T av_t = T(0);
+    if (tid < n0) {
       const int32_t kk = __ldg(aci + j0 + tid);
-      const int32_t bs = __ldg(brp + kk), be = __ldg(brp + kk + 1);
-      st.meta[tid] = make_int2(bs, be - bs);
-      if (NEED_VAL) st.a[tid] = __ldg(av + j0 + tid);
-      nseg = (be - bs + SEG - 1) / SEG;
+      bs = __ldg(brp + kk);
+      len = __ldg(brp + kk + 1) - bs;
+      if (NEED_VAL) av_t = __ldg(av + j0 + tid);
     }
-    // exclusive scan of nseg over the first kStageN threads (8 warps)
-    int inc = nseg;
+    // inclusive scan of the lengths over the first kStageN threads (8 warps)
+    long long inc = len;
     if (wid < kStageN / 32) {
-      inc = warp_incl_scan(nseg);
-      if (lane == 31) wsum[wid] = inc;
+      inc = warp_incl_scan(len);
+      if (lane == 31) st.wsum[wid] = inc;
     }
     if (tid == 0) *st.next = 0;
     __syncthreads();
     if (wid < kStageN / 32) {
-      int base = 0;
-      for (int w = 0; w < wid; ++w) base += wsum[w];
-      if (tid < n) st.segoff[tid] = base + inc - nseg;
-      if (tid == kStageN - 1) st.segoff[kStageN] = base + inc;
+      long long base = 0;
+      for (int w = 0; w < wid; ++w) base += st.wsum[w];
+      inc += base;
     }
+    // the round keeps the entries whose products end below 2^31 (at least one)
+    const bool keep = tid < n0 && (tid == 0 || inc <= 2147483647LL);
+    const int n = __syncthreads_count(keep);
+    if (keep) st.ent[tid] = Entry<T>{(int)inc, (int)(bs - (inc - len)), av_t};
     __syncthreads();
-    const int total = st.segoff[kStageN];
+    const int total = st.ent[n - 1].end;
+    // chunk size: about four chunks per group, between 4 and 32 products per lane
+    long long chunk = ((long long)total + 4LL * ngroups - 1) / (4LL * ngroups);
+    chunk = chunk < 4LL * G ? 4LL * G : chunk > 32LL * G ? 32LL * G : chunk;
+    chunk = (chunk + G - 1) / G * G;
+    const int nchunks = (int)(((long long)total + chunk - 1) / chunk);
     for (;;) {
-      int seg = 0;
-      if (lig == 0) seg = atomicAdd(st.next, 1);
-      seg = __shfl_sync(gmask, seg, leader);
-      if (seg >= total) break;
-      process_segment<U, NEED_VAL>(st, n, seg, SEG, G, lig, bci, bv, ncols, err, f);
+      int cidx = 0;
+      if (lig == 0) cidx = atomicAdd(st.next, 1);
+      cidx = __shfl_sync(gmask, cidx, leader);
+      if (cidx >= nchunks) break;
+      const long long p0 = (long long)cidx * chunk;
+      const long long p1 = p0 + chunk < total ? p0 + chunk : total;
+      process_flat<U, NEED_VAL>(st.ent, n, (int)p0, (int)p1, G, lig, bci, bv, ncols, err, f);
     }
     __syncthreads();
+    j0 += n;
   }
 }
 
-// Warp form: the 32 lanes of one warp work on one row; `st` points to this
-// warp's own staging area (32 entries, segoff 33 ints).
+// Warp form: the 32 lanes of one warp work on one row as one group;
+// `st` points to this warp's own staging area (32 entries).
 template <int U, bool NEED_VAL, typename T, typename F>
-__device__ __forceinline__ void warp_row_products(int64_t a0, int64_t a1, int G, const int32_t *__restrict__ aci,
+__device__ __forceinline__ void warp_row_products(int64_t a0, int64_t a1, int /*G*/, const int32_t *__restrict__ aci,
                                                   const T *__restrict__ av, const int32_t *__restrict__ brp,
                                                   const int32_t *__restrict__ bci, const T *__restrict__ bv,
                                                   int32_t ncols, uint32_t *err, Stage<T> st, F &&f) {
-  const int lane = threadIdx.x & 31, lig = lane & (G - 1);
-  const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
-  const int leader = lane & ~(G - 1);
-  const int SEG = G * U * kSegIters;
-  for (int64_t j0 = a0; j0 < a1; j0 += 32) {
-    const int n = (int)((a1 - j0) < 32 ? (a1 - j0) : 32);
-    int nseg = 0;
-    if (lane < n) {
+  const int lane = threadIdx.x & 31;
+  int64_t j0 = a0;
+  while (j0 < a1) {
+    const int n0 = (int)((a1 - j0) < 32 ? (a1 - j0) : 32);
+    long long len = 0;
+    int32_t bs = 0;
+    T av_t = T(0);
+    if (lane < n0) {
       const int32_t kk = __ldg(aci + j0 + lane);
-      const int32_t bs = __ldg(brp + kk), be = __ldg(brp + kk + 1);
-      st.meta[lane] = make_int2(bs, be - bs);
-      if (NEED_VAL) st.a[lane] = __ldg(av + j0 + lane);
-      nseg = (be - bs + SEG - 1) / SEG;
+      bs = __ldg(brp + kk);
+      len = __ldg(brp + kk + 1) - bs;
+      if (NEED_VAL) av_t = __ldg(av + j0 + lane);
     }
-    const int inc = warp_incl_scan(nseg);
-    st.segoff[lane] = inc - nseg;
-    const int total = __shfl_sync(0xffffffffu, inc, 31);
-    if (lane == 0) *st.next = 0;
+    const long long inc = warp_incl_scan(len);
+    const bool keep = lane < n0 && (lane == 0 || inc <= 2147483647LL);
+    const int n = __popc(__ballot_sync(0xffffffffu, keep));
+    if (keep) st.ent[lane] = Entry<T>{(int)inc, (int)(bs - (inc - len)), av_t};
     __syncwarp();
-    for (;;) {
-      int seg = 0;
-      if (lig == 0) seg = atomicAdd(st.next, 1);
-      seg = __shfl_sync(gmask, seg, leader);
-      if (seg >= total) break;
-      process_segment<U, NEED_VAL>(st, n, seg, SEG, G, lig, bci, bv, ncols, err, f);
-    }
+    const int total = st.ent[n - 1].end;
+    process_flat<U, NEED_VAL>(st.ent, n, 0, total, 32, lane, bci, bv, ncols, err, f);
     __syncwarp();
+    j0 += n;
   }
 }
 

@@ -49,7 +49,7 @@ constexpr int kNumNumBins = 13;
 constexpr int kWarpsPerBlock = 4;  // warp bins: rows per block
 // shared memory kept free beside a bitmap kernel's dynamic allocation for
 // its static arrays (staging of 256 entries, reductions)
-constexpr int kStaticSmemReserve = 256 * 20 + 1024;
+constexpr int kStaticSmemReserve = 256 * 20 + 2048;
 
 // Symbolic bins 0..9: tables 64 .. 32768 slots, load factor 1/2 for warp
 // tables and 3/4 for block tables (the bound overestimates the key count

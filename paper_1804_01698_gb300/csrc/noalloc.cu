@@ -46,8 +46,8 @@ constexpr uint32_t kErrTooLarge = 16u;
 __global__ void __launch_bounds__(1024, 1)
     k_noalloc_count(Args a, int64_t nnz_a, int64_t nnz_b, int32_t *__restrict__ c_row_ptr, unsigned char *scratch) {
   __shared__ long long red[33];
-  __shared__ int2 s_meta[kStageN];
-  __shared__ int s_segoff[kStageN + 1 + 8];
+  __shared__ Entry<int32_t> s_ent[kStageN];
+  __shared__ long long s_wsum[8];
   __shared__ int s_next;
   NoallocHeader *hdr = reinterpret_cast<NoallocHeader *>(scratch);
   int32_t *tab = reinterpret_cast<int32_t *>(scratch + kNoallocHeader) + (size_t)blockIdx.x * kNoallocSlots;
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(1024, 1)
         const uint32_t mask = (uint32_t)(S - 1);
         block_row_products<4, false, int32_t>(
             r0, r1, G, a.aci, (const int32_t *)nullptr, a.brp, a.bci, (const int32_t *)nullptr, (int32_t)a.k, a.err,
-            Stage<int32_t>{s_meta, nullptr, s_segoff, &s_next}, [&](int32_t c, int32_t, int32_t) {
+            Stage<int32_t>{s_ent, &s_next, s_wsum}, [&](int32_t c, int32_t, int32_t) {
               uint32_t h = hash_slot(c, mask);
               for (uint32_t probe = 0; probe <= mask; ++probe) {
                 const int32_t old = atomicCAS(tab + h, kEmpty, c);

@@ -80,9 +80,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 8)
     k_num_warp(Args a, const int32_t *__restrict__ rows, int64_t nrows, const int32_t *__restrict__ c_rp,
                int32_t *__restrict__ c_ci, T *__restrict__ c_v, int sorted) {
   extern __shared__ __align__(16) unsigned char sm_num_warp[];
-  __shared__ int2 s_meta[kWarpsPerBlock][32];
-  __shared__ int s_segoff[kWarpsPerBlock][33];
-  __shared__ T s_a[kWarpsPerBlock][32];
+  __shared__ Entry<T> s_ent[kWarpsPerBlock][32];
   __shared__ int s_next[kWarpsPerBlock];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
@@ -97,17 +95,41 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 8)
   const int32_t i = rows[w];
   const int G = a.G;
   warp_row_products<kUN, true, T>(a.arp[i], a.arp[i + 1], G, a.aci, (const T *)a.av, a.brp, a.bci, (const T *)a.bv,
-                                  (int32_t)a.k, a.err, Stage<T>{s_meta[warp], s_a[warp], s_segoff[warp], &s_next[warp]},
+                                  (int32_t)a.k, a.err, Stage<T>{s_ent[warp], &s_next[warp], nullptr},
                                  [&](int32_t c, T av, T bv) { insert_acc<T, false>(keys, vals, S - 1, c, av, bv, a.err); });
   __syncwarp();
   const int32_t rp = c_rp[i];
   const int32_t nnz = c_rp[i + 1] - rp;
   if (sorted) {
-    bitonic_sort(reinterpret_cast<uint32_t *>(keys), vals, S, lane, 32, [] { __syncwarp(); });
+    // Compact the occupied slots to the front (in place: chunk by chunk, every
+    // lane reads its slot before any lane writes, and a chunk only writes
+    // positions at or below its own), pad to the next power of two with the
+    // empty key (-1, largest as unsigned) and sort only that prefix.
+    int base = 0;
+    for (int s0 = 0; s0 < S; s0 += 32) {
+      const int32_t kk = keys[s0 + lane];
+      const T vv = vals[s0 + lane];
+      const bool occ = kk != kEmpty;
+      const unsigned m = __ballot_sync(0xffffffffu, occ);
+      __syncwarp();
+      if (occ) {
+        const int pos = base + __popc(m & ((1u << lane) - 1u));
+        keys[pos] = kk;
+        vals[pos] = vv;
+      }
+      base += __popc(m);
+      __syncwarp();
+    }
+    int P = 32;
+    while (P < base) P <<= 1;
+    for (int r = base + lane; r < P; r += 32) keys[r] = kEmpty;
+    __syncwarp();
+    bitonic_sort(reinterpret_cast<uint32_t *>(keys), vals, P, lane, 32, [] { __syncwarp(); });
     for (int r = lane; r < nnz; r += 32) {
       c_ci[rp + r] = keys[r];
       c_v[rp + r] = vals[r];
     }
+    if (lane == 0 && base != nnz) raise_err(a.err, kErrProbe);
   } else {
     int base = 0;
     for (int s0 = 0; s0 < S; s0 += 32) {
@@ -134,9 +156,8 @@ __global__ void __launch_bounds__(1024, 1)
                 int32_t *__restrict__ c_ci, T *__restrict__ c_v, int sort_mode, int words) {
   extern __shared__ __align__(16) unsigned char sm_num_block[];
   __shared__ int red[33];
-  __shared__ int2 s_meta[kStageN];
-  __shared__ int s_segoff[kStageN + 1 + 8];
-  __shared__ T s_a[kStageN];
+  __shared__ Entry<T> s_ent[kStageN];
+  __shared__ long long s_wsum[8];
   __shared__ int s_next;
   __shared__ int cursor;
   int32_t *keys = reinterpret_cast<int32_t *>(sm_num_block);
@@ -150,7 +171,7 @@ __global__ void __launch_bounds__(1024, 1)
   const int32_t i = rows[blockIdx.x];
   const int G = a.G;
   block_row_products<kUN, true, T>(a.arp[i], a.arp[i + 1], G, a.aci, (const T *)a.av, a.brp, a.bci,
-                                   (const T *)a.bv, (int32_t)a.k, a.err, Stage<T>{s_meta, s_a, s_segoff, &s_next},
+                                   (const T *)a.bv, (int32_t)a.k, a.err, Stage<T>{s_ent, &s_next, s_wsum},
                                  [&](int32_t c, T av, T bv) { insert_acc<T, false>(keys, vals, S - 1, c, av, bv, a.err); });
   __syncthreads();
   const int32_t rp = c_rp[i];
@@ -224,9 +245,8 @@ __global__ void __launch_bounds__(1024, 1)
                  int32_t *__restrict__ c_ci, T *__restrict__ c_v) {
   extern __shared__ __align__(16) unsigned char sm_num_bm[];
   __shared__ int red[33];
-  __shared__ int2 s_meta[kStageN];
-  __shared__ int s_segoff[kStageN + 1 + 8];
-  __shared__ T s_a[kStageN];
+  __shared__ Entry<T> s_ent[kStageN];
+  __shared__ long long s_wsum[8];
   __shared__ int s_next;
   T *vals = reinterpret_cast<T *>(sm_num_bm);
   uint32_t *bm = reinterpret_cast<uint32_t *>(sm_num_bm + (size_t)cap * sizeof(T));
@@ -256,7 +276,7 @@ __global__ void __launch_bounds__(1024, 1)
   __syncthreads();
   const int G = a.G;
   block_row_products<kUN, true, T>(a.arp[i], a.arp[i + 1], G, a.aci, (const T *)a.av, a.brp, a.bci,
-                                   (const T *)a.bv, (int32_t)a.k, a.err, Stage<T>{s_meta, s_a, s_segoff, &s_next},
+                                   (const T *)a.bv, (int32_t)a.k, a.err, Stage<T>{s_ent, &s_next, s_wsum},
                                  [&](int32_t c, T av, T bv) {
                                    const uint32_t word = bm[c >> 5];
                                    const int r = pre[c >> 5] + __popc(word & ((1u << (c & 31)) - 1u));
@@ -294,9 +314,8 @@ __global__ void __launch_bounds__(1024, 1)
                  T *__restrict__ c_v, int sorted, int win_words) {
   extern __shared__ __align__(16) unsigned char sm_num_gl[];
   __shared__ int red[33];
-  __shared__ int2 s_meta[kStageN];
-  __shared__ int s_segoff[kStageN + 1 + 8];
-  __shared__ T s_a[kStageN];
+  __shared__ Entry<T> s_ent[kStageN];
+  __shared__ long long s_wsum[8];
   __shared__ int s_next;
   __shared__ int cursor;
   int32_t *keys = keys_all + (size_t)blockIdx.x * S;
@@ -313,7 +332,7 @@ __global__ void __launch_bounds__(1024, 1)
     __syncthreads();
     const int32_t i = rows[r];
     block_row_products<kUN, true, T>(a.arp[i], a.arp[i + 1], G, a.aci, (const T *)a.av, a.brp, a.bci,
-                                   (const T *)a.bv, (int32_t)a.k, a.err, Stage<T>{s_meta, s_a, s_segoff, &s_next},
+                                   (const T *)a.bv, (int32_t)a.k, a.err, Stage<T>{s_ent, &s_next, s_wsum},
                                    [&](int32_t c, T av, T bv) { insert_acc<T, true>(keys, vals, mask, c, av, bv, a.err); });
     __syncthreads();
     const int32_t rp = c_rp[i];

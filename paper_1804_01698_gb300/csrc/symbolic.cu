@@ -39,8 +39,7 @@ template <int S>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, 8)
     k_sym_warp(Args a, const int32_t *__restrict__ rows, int64_t nrows, int32_t *__restrict__ nnz_row) {
   extern __shared__ int32_t sm_sym_warp[];
-  __shared__ int2 s_meta[kWarpsPerBlock][32];
-  __shared__ int s_segoff[kWarpsPerBlock][33];
+  __shared__ Entry<int32_t> s_ent[kWarpsPerBlock][32];
   __shared__ int s_next[kWarpsPerBlock];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
@@ -51,7 +50,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 8)
   const int32_t i = rows[w];
   const int G = a.G;
   int cnt = 0;
-  Stage<int32_t> st{s_meta[warp], nullptr, s_segoff[warp], &s_next[warp]};
+  Stage<int32_t> st{s_ent[warp], &s_next[warp], nullptr};
   warp_row_products<kU, false, int32_t>(a.arp[i], a.arp[i + 1], G, a.aci, (const int32_t *)nullptr, a.brp, a.bci,
                                         (const int32_t *)nullptr, (int32_t)a.k, a.err, st,
                                         [&](int32_t c, int32_t, int32_t) { cnt += insert_key<false>(tab, S - 1, c, a.err); });
@@ -64,8 +63,8 @@ __global__ void __launch_bounds__(1024, 1)
     k_sym_block(Args a, const int32_t *__restrict__ rows, int32_t *__restrict__ nnz_row) {
   extern __shared__ int32_t sm_sym_block[];
   __shared__ int red[33];
-  __shared__ int2 s_meta[kStageN];
-  __shared__ int s_segoff[kStageN + 1 + 8];
+  __shared__ Entry<int32_t> s_ent[kStageN];
+  __shared__ long long s_wsum[8];
   __shared__ int s_next;
   int32_t *tab = sm_sym_block;
   for (int s = threadIdx.x; s < S; s += blockDim.x) tab[s] = kEmpty;
@@ -75,7 +74,7 @@ __global__ void __launch_bounds__(1024, 1)
   int cnt = 0;
   block_row_products<kU, false, int32_t>(a.arp[i], a.arp[i + 1], G, a.aci, (const int32_t *)nullptr,
                                          a.brp, a.bci, (const int32_t *)nullptr, (int32_t)a.k, a.err,
-                                         Stage<int32_t>{s_meta, nullptr, s_segoff, &s_next},
+                                         Stage<int32_t>{s_ent, &s_next, s_wsum},
                                        [&](int32_t c, int32_t, int32_t) { cnt += insert_key<false>(tab, S - 1, c, a.err); });
   cnt = block_sum(cnt, red);
   if (threadIdx.x == 0) nnz_row[i] = cnt;
@@ -87,8 +86,8 @@ __global__ void __launch_bounds__(1024, 1)
                  uint32_t *__restrict__ bitmaps, int words) {
   extern __shared__ uint32_t sm_bm[];
   __shared__ int red[33];
-  __shared__ int2 s_meta[kStageN];
-  __shared__ int s_segoff[kStageN + 1 + 8];
+  __shared__ Entry<int32_t> s_ent[kStageN];
+  __shared__ long long s_wsum[8];
   __shared__ int s_next;
   for (int w = threadIdx.x; w < words; w += blockDim.x) sm_bm[w] = 0u;
   __syncthreads();
@@ -96,7 +95,7 @@ __global__ void __launch_bounds__(1024, 1)
   const int G = a.G;
   block_row_products<kU, false, int32_t>(a.arp[i], a.arp[i + 1], G, a.aci, (const int32_t *)nullptr,
                                          a.brp, a.bci, (const int32_t *)nullptr, (int32_t)a.k, a.err,
-                                         Stage<int32_t>{s_meta, nullptr, s_segoff, &s_next},
+                                         Stage<int32_t>{s_ent, &s_next, s_wsum},
                                        [&](int32_t c, int32_t, int32_t) { atomicOr(sm_bm + (c >> 5), 1u << (c & 31)); });
   __syncthreads();
   int cnt = 0;
@@ -116,8 +115,8 @@ __global__ void __launch_bounds__(1024, 1)
     k_sym_global(Args a, const int32_t *__restrict__ rows, int64_t nrows, int32_t *__restrict__ nnz_row,
                  int32_t *__restrict__ tables, int64_t S) {
   __shared__ int red[33];
-  __shared__ int2 s_meta[kStageN];
-  __shared__ int s_segoff[kStageN + 1 + 8];
+  __shared__ Entry<int32_t> s_ent[kStageN];
+  __shared__ long long s_wsum[8];
   __shared__ int s_next;
   int32_t *tab = tables + (size_t)blockIdx.x * S;
   const uint32_t mask = (uint32_t)(S - 1);
@@ -129,7 +128,7 @@ __global__ void __launch_bounds__(1024, 1)
     int cnt = 0;
     block_row_products<kU, false, int32_t>(a.arp[i], a.arp[i + 1], G, a.aci, (const int32_t *)nullptr,
                                          a.brp, a.bci, (const int32_t *)nullptr, (int32_t)a.k, a.err,
-                                         Stage<int32_t>{s_meta, nullptr, s_segoff, &s_next},
+                                         Stage<int32_t>{s_ent, &s_next, s_wsum},
                                          [&](int32_t c, int32_t, int32_t) { cnt += insert_key<true>(tab, mask, c, a.err); });
     cnt = block_sum(cnt, red);
     if (threadIdx.x == 0) nnz_row[i] = cnt;
