@@ -249,8 +249,8 @@ __global__ void __launch_bounds__(1024, 1)
   __shared__ long long s_wsum[8];
   __shared__ int s_next;
   T *vals = reinterpret_cast<T *>(sm_num_bm);
-  uint32_t *bm = reinterpret_cast<uint32_t *>(sm_num_bm + (size_t)cap * sizeof(T));
-  int32_t *pre = reinterpret_cast<int32_t *>(bm + words);
+  // word w of the row's column bitmap and the number of set bits before it
+  uint2 *rk = reinterpret_cast<uint2 *>(sm_num_bm + (size_t)cap * sizeof(T));
   const int2 item = items[blockIdx.x];
   const int32_t i = bm_rows[item.x];
   const int32_t rp = c_rp[i];
@@ -263,14 +263,14 @@ __global__ void __launch_bounds__(1024, 1)
   int local = 0;
   for (int w = w0; w < w1; ++w) {
     const uint32_t b = src[w];
-    bm[w] = b;
+    rk[w].x = b;
     local += __popc(b);
   }
   int tot;
   int run = block_excl_scan(local, red, &tot);
   for (int w = w0; w < w1; ++w) {
-    pre[w] = run;
-    run += __popc(bm[w]);
+    rk[w].y = (uint32_t)run;
+    run += __popc(rk[w].x);
   }
   for (int r = threadIdx.x; r < hi - lo; r += blockDim.x) vals[r] = T(0);
   __syncthreads();
@@ -278,26 +278,47 @@ __global__ void __launch_bounds__(1024, 1)
   block_row_products<kUN, true, T>(a.arp[i], a.arp[i + 1], G, a.aci, (const T *)a.av, a.brp, a.bci,
                                    (const T *)a.bv, (int32_t)a.k, a.err, Stage<T>{s_ent, &s_next, s_wsum},
                                  [&](int32_t c, T av, T bv) {
-                                   const uint32_t word = bm[c >> 5];
-                                   const int r = pre[c >> 5] + __popc(word & ((1u << (c & 31)) - 1u));
+                                   const uint2 word = rk[c >> 5];
+                                   const int r = (int)word.y + __popc(word.x & ((1u << (c & 31)) - 1u));
                                    if (r >= lo && r < hi) {
                                      if (!Val<T>::acc_shared(vals + (r - lo), av, bv)) raise_err(a.err, kErrRetry);
                                    }
                                  });
   __syncthreads();
-  // store ranks [lo, hi): each thread expands the set bits of its words
-  for (int w = threadIdx.x; w < words; w += blockDim.x) {
-    uint32_t b = bm[w];
-    int r = pre[w];
-    if (r >= hi || r + __popc(b) <= lo) continue;
-    while (b) {
-      const int bit = __ffs(b) - 1;
-      b &= b - 1u;
-      if (r >= lo && r < hi) {
-        c_ci[rp + r] = w * 32 + bit;
-        c_v[rp + r] = vals[r - lo];
+  // Store ranks [lo, hi) in rank order with coalesced writes: a warp takes
+  // 32 consecutive bitmap words, and its lanes walk the words' entries 32 at
+  // a time; the lane of entry j finds the word holding it by binary search
+  // over the words' prefix counts (shuffles) and its column with __fns.
+  {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int w0 = warp * 32; w0 < words; w0 += nw * 32) {
+      const int w = w0 + lane;
+      const bool valid = w < words;
+      const uint2 mine = valid ? rk[w] : make_uint2(0u, 0u);
+      const int pre0 = __shfl_sync(0xffffffffu, (int)mine.y, 0);
+      // entries before this lane's word, within the 32 words (lanes past the
+      // last word sort after every entry)
+      const int first = valid ? (int)mine.y - pre0 : 0x3fffffff;
+      const int last = min(31, words - 1 - w0);
+      const int total = __shfl_sync(0xffffffffu, first + (valid ? __popc(mine.x) : 0), last);
+      if (pre0 >= hi || pre0 + total <= lo) continue;
+      for (int j0 = 0; j0 < total; j0 += 32) {
+        const int j = j0 + lane;
+        int l = 0;  // last lane whose word starts at or before entry j
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const int f = __shfl_sync(0xffffffffu, first, l + step);
+          if (f <= j) l += step;
+        }
+        const unsigned bits = __shfl_sync(0xffffffffu, mine.x, l);
+        const int fl = __shfl_sync(0xffffffffu, first, l);
+        const int r = pre0 + j;
+        if (j < total && r >= lo && r < hi) {
+          const int col = (w0 + l) * 32 + (int)__fns(bits, 0, j - fl + 1);
+          c_ci[rp + r] = col;
+          c_v[rp + r] = vals[r - lo];
+        }
       }
-      ++r;
     }
   }
   if (threadIdx.x == 0 && tot != nnz) raise_err(a.err, kErrProbe);
