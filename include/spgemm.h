@@ -199,6 +199,36 @@ SPGEMM_API int spgemm(const spgemm_csr *A, const spgemm_csr *B, int dtype, unsig
            int32_t **c_row_ptr, int32_t **c_col_idx, void **c_vals, int64_t *nnz_c);
 
 /*
+ * Batched products C_p = A_p * B_p, p = 0 .. nprod-1, in one plan (batching
+ * of independent products; the paper's products are single).  A and B are
+ * HOST arrays of nprod device CSR descriptors.  The batch is packed on the
+ * device into the block-diagonal product diag(A_p) * diag(B_p) (a copy of
+ * the operands, owned by the batch) and runs with the launches and host
+ * synchronisations of one product.
+ *
+ * spgemm_batch_create     packs, checks every product's indices
+ *                         (SPGEMM_ERR_INVALID_CSR names none in particular),
+ *                         runs the flop pass and binning; syncs `stream`.
+ * spgemm_batch_symbolic   c_row_ptr (device, sum of nrows(A_p) + 1 int32)
+ *                         receives the packed row pointers, *nnz_c the total,
+ *                         row_off (host, nprod + 1, optional) the first row
+ *                         of each product: product p owns rows
+ *                         row_off[p] .. row_off[p+1]-1 and entries
+ *                         c_row_ptr[row_off[p]] .. c_row_ptr[row_off[p+1]]-1.
+ * spgemm_batch_numeric    columns (local to each product) and values.
+ * spgemm_batch_plan       the underlying plan (statistics, timings).
+ * Sizes of the packed batch must fit int32 indexing
+ * (SPGEMM_ERR_INDEX_OVERFLOW otherwise).
+ */
+typedef struct spgemm_batch_s *spgemm_batch_t;
+SPGEMM_API int spgemm_batch_create(spgemm_batch_t *out, int64_t nprod, const spgemm_csr *A, const spgemm_csr *B,
+                                   int dtype, unsigned flags, void *stream);
+SPGEMM_API int spgemm_batch_symbolic(spgemm_batch_t batch, int32_t *c_row_ptr, int64_t *nnz_c, int64_t *row_off);
+SPGEMM_API int spgemm_batch_numeric(spgemm_batch_t batch, const int32_t *c_row_ptr, int32_t *c_col_idx, void *c_vals);
+SPGEMM_API spgemm_plan_t spgemm_batch_plan(spgemm_batch_t batch);
+SPGEMM_API int spgemm_batch_destroy(spgemm_batch_t batch);
+
+/*
  * Symbolic phase for callers that cannot allocate device memory.  The paper
  * has no counterpart: this entry point exists for callers that must not
  * reach the CUDA allocator while they run (code inside an allocator or

@@ -65,7 +65,8 @@ ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 EXPORTED = ("spgemm_plan_create", "spgemm_symbolic", "spgemm_numeric", "spgemm_plan_destroy",
             "spgemm_plan_workspace_bytes", "spgemm_plan_stats", "spgemm_plan_row_flop", "spgemm_plan_sym_bins",
             "spgemm_plan_row_nnz", "spgemm_plan_kernel_times", "spgemm", "spgemm_status_string",
-            "spgemm_last_error", "spgemm_symbolic_noalloc")
+            "spgemm_last_error", "spgemm_symbolic_noalloc", "spgemm_batch_create", "spgemm_batch_symbolic",
+            "spgemm_batch_numeric", "spgemm_batch_destroy")
 
 
 def library_path() -> str:
@@ -94,6 +95,13 @@ def library():
     lib.spgemm_plan_sym_bins.argtypes = [P, P, P]
     lib.spgemm_plan_row_nnz.argtypes = [P, P]
     lib.spgemm_plan_kernel_times.argtypes = [P, ctypes.POINTER(KernelTime), I32, ctypes.POINTER(I32)]
+    lib.spgemm_batch_create.argtypes = [ctypes.POINTER(P), I64, ctypes.POINTER(CsrDesc), ctypes.POINTER(CsrDesc), I32,
+                                        ctypes.c_uint, P]
+    lib.spgemm_batch_symbolic.argtypes = [P, P, ctypes.POINTER(I64), P]
+    lib.spgemm_batch_numeric.argtypes = [P, P, P, P]
+    lib.spgemm_batch_destroy.argtypes = [P]
+    lib.spgemm_batch_plan.argtypes = [P]
+    lib.spgemm_batch_plan.restype = P
     lib.spgemm_symbolic_noalloc.argtypes = [ctypes.POINTER(CsrDesc), ctypes.POINTER(CsrDesc), P, ctypes.POINTER(I64), P]
     lib.spgemm.argtypes = [ctypes.POINTER(CsrDesc), ctypes.POINTER(CsrDesc), I32, ctypes.c_uint, P, ALLOC_FN, P,
                            ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(I64)]
@@ -346,3 +354,117 @@ def spgemm(A: DeviceCSR, B: DeviceCSR, sorted_output: bool = True, stream=None) 
     esz = torch.empty(0, dtype=A.vals.dtype).element_size()
     cvt = keep[cv.value][: n * esz].view(A.vals.dtype)
     return DeviceCSR(A.nrows, B.ncols, rpt, cit, cvt)
+
+
+class Batch:
+    """Independent products C_p = A_p * B_p run as one plan (block-diagonal
+    packing on the device); mirrors spgemm_batch_create / _symbolic / _numeric."""
+
+    def __init__(self, As, Bs, sorted_output: bool = True, stream=None, timing: bool = False, serial: bool = False):
+        self.lib = library()
+        if len(As) != len(Bs) or not As:
+            raise ValueError("need the same positive number of A and B operands")
+        self.dtype = As[0].vals.dtype
+        if self.dtype not in _DTYPES or any(m.vals.dtype != self.dtype for m in list(As) + list(Bs)):
+            raise TypeError("all operands must share one value dtype among int64, float32, float64")
+        self.As, self.Bs = list(As), list(Bs)
+        self.device = As[0].row_ptr.device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        flags = (SPGEMM_SORTED if sorted_output else SPGEMM_UNSORTED) | (SPGEMM_TIMING if timing else 0) | \
+            (SPGEMM_SERIAL if serial else 0)
+        n = len(As)
+        self._a = (CsrDesc * n)(*[m.desc() for m in As])
+        self._b = (CsrDesc * n)(*[m.desc() for m in Bs])
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(self.lib.spgemm_batch_create(ctypes.byref(h), n, self._a, self._b, _DTYPES[self.dtype], flags,
+                                                _stream_ptr(self.stream)), "spgemm_batch_create")
+        self.handle = h
+        self.nprod = n
+        self.m = sum(a.nrows for a in As)
+        self.c_row_ptr = None
+        self.nnz_c = None
+        self.row_off = None
+
+    def symbolic(self) -> int:
+        self.c_row_ptr = torch.empty(self.m + 1, dtype=torch.int32, device=self.device)
+        nnz = ctypes.c_int64()
+        off = (ctypes.c_int64 * (self.nprod + 1))()
+        with torch.cuda.device(self.device):
+            _check(self.lib.spgemm_batch_symbolic(self.handle, self.c_row_ptr.data_ptr(), ctypes.byref(nnz), off),
+                   "spgemm_batch_symbolic")
+        self.nnz_c = int(nnz.value)
+        self.row_off = list(off)
+        return self.nnz_c
+
+    def numeric(self):
+        """Returns (c_row_ptr, c_col_idx, c_vals) of the packed C; columns are local to each product."""
+        ci = torch.empty(max(self.nnz_c, 0), dtype=torch.int32, device=self.device)
+        cv = torch.empty(max(self.nnz_c, 0), dtype=self.dtype, device=self.device)
+        with torch.cuda.device(self.device):
+            _check(self.lib.spgemm_batch_numeric(self.handle, self.c_row_ptr.data_ptr(),
+                                                 ci.data_ptr() if self.nnz_c else None,
+                                                 cv.data_ptr() if self.nnz_c else None), "spgemm_batch_numeric")
+        self.c_col_idx, self.c_vals = ci, cv
+        return self.c_row_ptr, ci, cv
+
+    def product(self, p: int, row_ptr_host=None) -> DeviceCSR:
+        """Product p of the batch as a DeviceCSR view (row_ptr rebased to 0)."""
+        r0, r1 = self.row_off[p], self.row_off[p + 1]
+        rp = self.c_row_ptr[r0:r1 + 1]
+        if row_ptr_host is not None:
+            e0, e1 = int(row_ptr_host[r0]), int(row_ptr_host[r1])
+        else:
+            e0, e1 = int(rp[0].item()), int(rp[-1].item())
+        return DeviceCSR(r1 - r0, self.Bs[p].ncols, rp - e0, self.c_col_idx[e0:e1], self.c_vals[e0:e1])
+
+    def plan_stats(self) -> dict:
+        s = Stats()
+        status = self.lib.spgemm_plan_stats(self.lib.spgemm_batch_plan(self.handle), ctypes.byref(s))
+        out = {name: getattr(s, name) for name, _ in Stats._fields_}
+        for key in ("sym_bin_rows", "sym_bin_table", "sym_bin_flop"):
+            out[key] = list(getattr(s, key))[: s.n_sym_bins]
+        for key in ("num_bin_rows", "num_bin_table", "num_bin_flop"):
+            out[key] = list(getattr(s, key))[: s.n_num_bins]
+        out["status"] = status
+        return out
+
+    def kernel_times(self) -> dict:
+        buf = (KernelTime * 64)()
+        n = ctypes.c_int()
+        _check(self.lib.spgemm_plan_kernel_times(self.lib.spgemm_batch_plan(self.handle), buf, 64, ctypes.byref(n)),
+               "spgemm_plan_kernel_times")
+        return {buf[j].name.decode(): (float(buf[j].ms), int(buf[j].launches)) for j in range(min(n.value, 64))}
+
+    def destroy(self):
+        if getattr(self, "handle", None):
+            self.lib.spgemm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def spgemm_batch_create(As, Bs, sorted_output: bool = True, stream=None, timing: bool = False) -> Batch:
+    return Batch(As, Bs, sorted_output, stream, timing)
+
+
+def spgemm_batch_symbolic(batch: Batch) -> int:
+    return batch.symbolic()
+
+
+def spgemm_batch_numeric(batch: Batch):
+    return batch.numeric()
+
+
+def spgemm_batch_destroy(batch: Batch) -> None:
+    batch.destroy()

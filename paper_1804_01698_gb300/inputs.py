@@ -45,6 +45,7 @@ TAG_FRONTIER_COUNT = 4
 TAG_FRONTIER_ROWS = 5
 TAG_SHUFFLE = 6
 TAG_PERM = 7
+TAG_BATCH = 8
 
 
 def splitmix64(x: np.ndarray) -> np.ndarray:
@@ -239,6 +240,26 @@ def column_permutation(n: int, seed: int) -> np.ndarray:
 def relabel_columns(m: CSR, perm: np.ndarray) -> CSR:
     """Column j of the result is column perm^-1(j) of m, i.e. new col = perm[old col]."""
     return CSR(m.nrows, m.ncols, m.row_ptr, perm[m.col_idx].astype(np.int32), m.vals)
+
+
+def batch_sizes(count: int, seed: int, n_lo: int = 256, n_hi: int = 65536, k_lo: int = 2, k_hi: int = 32):
+    """Sizes of a batch of Erdos-Renyi products: n_i log-uniform in [n_lo, n_hi]
+    and k_i (nonzeros per row) uniform in {k_lo..k_hi}, k_i <= n_i."""
+    idx = np.arange(count, dtype=np.uint64)
+    un = draw_unit(seed, TAG_BATCH, 2 * idx)
+    uk = draw_unit(seed, TAG_BATCH, 2 * idx + np.uint64(1))
+    n = np.floor(np.exp(np.log(n_lo) + un * (np.log(n_hi) - np.log(n_lo)))).astype(np.int64)
+    n = np.clip(n, n_lo, n_hi)
+    k = k_lo + np.minimum((uk * (k_hi - k_lo + 1)).astype(np.int64), k_hi - k_lo)
+    return n, np.minimum(k, n)
+
+
+def er_batch(count: int, seed: int, n_lo: int = 256, n_hi: int = 65536, k_lo: int = 2, k_hi: int = 32,
+             kind: str = "uniform", dtype=np.float64) -> list:
+    """`count` square Erdos-Renyi matrices with the sizes of batch_sizes (each
+    with its own seed), for products A_i * A_i."""
+    n, k = batch_sizes(count, seed, n_lo, n_hi, k_lo, k_hi)
+    return [er_exact(int(n[i]), int(k[i]), seed=seed * 7919 + i + 1, kind=kind, dtype=dtype) for i in range(count)]
 
 
 # Workloads named by what they are, with their sizes.
