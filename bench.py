@@ -213,12 +213,112 @@ def run_reference(args) -> int:
     return 0
 
 
+# ---------------------------------------------------------------------------- batched products
+
+def waves_by_flop(flops, limit=2**31 - 1):
+    """Consecutive groups of products whose summed flop (a bound on nnz of C)
+    stays within int32 indexing."""
+    waves, cur, tot = [], [], 0
+    for i, f in enumerate(flops):
+        if cur and tot + f > limit:
+            waves.append(cur)
+            cur, tot = [], 0
+        cur.append(i)
+        tot += f
+    if cur:
+        waves.append(cur)
+    return waves
+
+
+def run_batch(args) -> int:
+    """2000 independent Erdos-Renyi products A_i*A_i (n_i log-uniform in
+    [256, 65536], k_i nonzeros per row uniform in {2..32}, FP64), timed as
+    one call per product and as packed batches (waves of products whose
+    summed flop fits int32 indexing).  Inputs are resident on the device."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1804_01698_gb300 import binding as sg
+    from paper_1804_01698_gb300 import inputs
+
+    count = int(args.workload.split("er")[-1]) if args.workload.startswith("batch_er") else 2000
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    t0 = time.time()
+    mats = inputs.er_batch(count, seed=inputs.SEED_BASE + 3)
+    gen_s = time.time() - t0
+    flops = [m.nrows * (m.nnz // max(m.nrows, 1)) ** 2 for m in mats]   # exactly k^2 per row
+    dm = [sg.to_device(m, dev) for m in mats]
+    stream = torch.cuda.current_stream(dev)
+    waves = waves_by_flop(flops)
+
+    def plain_pass():
+        launches = 0
+        for d in dm:
+            p = sg.Plan(d, d, True, stream=stream)
+            p.symbolic()
+            p.numeric()
+            launches += p.stats()["kernel_launches"]
+            p.destroy()
+        return launches
+
+    def batch_pass():
+        launches = 0
+        for w in waves:
+            b = sg.Batch([dm[i] for i in w], [dm[i] for i in w], True, stream=stream)
+            b.symbolic()
+            b.numeric()
+            launches += b.plan_stats()["kernel_launches"]
+            b.destroy()
+        return launches
+
+    def timed(fn, k, w):
+        for _ in range(w):
+            fn()
+        torch.cuda.synchronize()
+        ts, launches = [], 0
+        for _ in range(k):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            launches = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        return sum(ts) / len(ts), launches
+
+    with ClockSampler(0) as clocks:
+        t_batch, l_batch = timed(batch_pass, args.steps, max(1, args.warmup))
+        t_plain, l_plain = timed(plain_pass, args.steps, max(1, args.warmup))
+    flop = sum(flops)
+    line = {
+        "metric": "batched SpGEMM solves/s (products per second)", "value": count / t_batch, "unit": "solves/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": max(1, args.warmup), "ms_per_step": t_batch * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{count} Erdos-Renyi products A_i*A_i, n_i log-uniform in [256,65536], "
+                               "k_i uniform in {2..32} per row, FP64, sorted output",
+                   "products": count, "flop": flop, "nnz_a": sum(m.nnz for m in mats), "waves": len(waves),
+                   "generation_s": gen_s, "l2": "inputs larger than L2"},
+        "batched": {"solves_per_s": count / t_batch, "gflops": 2 * flop / t_batch / 1e9, "s_per_pass": t_batch,
+                    "kernel_launches": l_batch},
+        "one_call_per_product": {"solves_per_s": count / t_plain, "gflops": 2 * flop / t_plain / 1e9,
+                                 "s_per_pass": t_plain, "kernel_launches": l_plain},
+        "speedup": t_plain / t_batch,
+        "gpu_launches": l_batch * args.steps,
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------------------- GPU arm
 
 def main() -> int:
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload.startswith("batch_"):
+        return run_batch(args)
 
     import torch
     import torch.distributed as dist

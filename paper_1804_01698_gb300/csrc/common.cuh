@@ -3,6 +3,7 @@
 // reductions and scans, and the device error word.
 #pragma once
 
+#include <climits>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -118,6 +119,27 @@ template <typename T> __device__ __forceinline__ T block_sum(T v, T *scratch) {
   __syncthreads();
   return r;
 }
+
+// Block-wide minimum / maximum of an int; same calling rules as block_sum.
+__device__ __forceinline__ int block_min(int v, int *scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (lane == 0) scratch[wid] = v;
+  __syncthreads();
+  int r = threadIdx.x < nw ? scratch[threadIdx.x] : INT_MAX;
+  if (wid == 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r = min(r, __shfl_xor_sync(0xffffffffu, r, o));
+  }
+  if (threadIdx.x == 0) scratch[0] = r;
+  __syncthreads();
+  r = scratch[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ int block_max(int v, int *scratch) { return -block_min(-v, scratch); }
 
 // Block-wide exclusive scan; returns this thread's exclusive prefix and the
 // block total through *total.  Same calling rules as block_sum.

@@ -67,6 +67,7 @@ constexpr int64_t kBitmapMinBound = 3072;
 constexpr int64_t kBitmapMidMax = 24576;
 constexpr int64_t kBlockSymMax = 24576;      // 3/4 of 32768 (global-table inputs)
 constexpr int64_t kBitmapMaxCols = 1 << 18;  // bitmap + prefix <= 64 KB
+constexpr int64_t kSortWindowWords = 2048;   // block-bin sort: 65536-column window per row
 
 // Device counters of a plan (zeroed at creation).
 struct DevCounters {

@@ -16,6 +16,7 @@
 // so they are smaller than the symbolic tables.
 #pragma once
 
+#include <algorithm>
 #include <string>
 
 #include "common.cuh"
@@ -183,38 +184,63 @@ __global__ void __launch_bounds__(1024, 1)
       c_v[rp + r] = vals[r];
     }
   } else if (sort_mode == 2) {
-    uint32_t *bm = reinterpret_cast<uint32_t *>(sm_num_block + (size_t)S * (sizeof(int32_t) + sizeof(T)));
-    int32_t *pre = reinterpret_cast<int32_t *>(bm + words);
-    for (int w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0u;
-    __syncthreads();
-    for (int s = threadIdx.x; s < S; s += blockDim.x) {
-      const int32_t kk = keys[s];
-      if (kk != kEmpty) atomicOr(bm + (kk >> 5), 1u << (kk & 31));
-    }
-    __syncthreads();
-    // exclusive prefix of popcounts: each thread owns a contiguous run of words
-    const int per = (words + blockDim.x - 1) / blockDim.x;
-    const int w0 = threadIdx.x * per, w1 = min(words, w0 + per);
-    int local = 0;
-    for (int w = w0; w < w1; ++w) local += __popc(bm[w]);
-    int tot;
-    int run = block_excl_scan(local, red, &tot);
-    for (int w = w0; w < w1; ++w) {
-      pre[w] = run;
-      run += __popc(bm[w]);
-    }
-    __syncthreads();
+    // Rank by a bitmap over the row's own column window [cmin, cmax] (the
+    // words of shared memory reserved for it hold `words` x 32 columns); a row
+    // whose columns spread wider is sorted with the bitonic network instead.
+    int cmin = INT_MAX, cmax = -1;
     for (int s = threadIdx.x; s < S; s += blockDim.x) {
       const int32_t kk = keys[s];
       if (kk != kEmpty) {
-        const int r = pre[kk >> 5] + __popc(bm[kk >> 5] & ((1u << (kk & 31)) - 1u));
-        if (r < nnz) {
-          c_ci[rp + r] = kk;
-          c_v[rp + r] = vals[s];
-        }
+        cmin = min(cmin, (int)kk);
+        cmax = max(cmax, (int)kk);
       }
     }
-    if (threadIdx.x == 0 && tot != nnz) raise_err(a.err, kErrProbe);
+    cmin = block_min(cmin, red);
+    cmax = block_max(cmax, red);
+    const int base = cmin & ~31;
+    const int used = nnz > 0 ? ((cmax - base) >> 5) + 1 : 0;
+    if (used <= words) {
+      uint32_t *bm = reinterpret_cast<uint32_t *>(sm_num_block + (size_t)S * (sizeof(int32_t) + sizeof(T)));
+      int32_t *pre = reinterpret_cast<int32_t *>(bm + words);
+      for (int w = threadIdx.x; w < used; w += blockDim.x) bm[w] = 0u;
+      __syncthreads();
+      for (int s = threadIdx.x; s < S; s += blockDim.x) {
+        const int32_t kk = keys[s];
+        if (kk != kEmpty) atomicOr(bm + ((kk - base) >> 5), 1u << ((kk - base) & 31));
+      }
+      __syncthreads();
+      // exclusive prefix of popcounts: each thread owns a contiguous run of words
+      const int per = (used + blockDim.x - 1) / blockDim.x;
+      const int w0 = threadIdx.x * per, w1 = min(used, w0 + per);
+      int local = 0;
+      for (int w = w0; w < w1; ++w) local += __popc(bm[w]);
+      int tot;
+      int run = block_excl_scan(local, red, &tot);
+      for (int w = w0; w < w1; ++w) {
+        pre[w] = run;
+        run += __popc(bm[w]);
+      }
+      __syncthreads();
+      for (int s = threadIdx.x; s < S; s += blockDim.x) {
+        const int32_t kk = keys[s];
+        if (kk != kEmpty) {
+          const int o = kk - base;
+          const int r = pre[o >> 5] + __popc(bm[o >> 5] & ((1u << (o & 31)) - 1u));
+          if (r < nnz) {
+            c_ci[rp + r] = kk;
+            c_v[rp + r] = vals[s];
+          }
+        }
+      }
+      if (threadIdx.x == 0 && tot != nnz) raise_err(a.err, kErrProbe);
+    } else {
+      bitonic_sort(reinterpret_cast<uint32_t *>(keys), vals, S, (int)threadIdx.x, (int)blockDim.x,
+                   [] { __syncthreads(); });
+      for (int r = threadIdx.x; r < nnz; r += blockDim.x) {
+        c_ci[rp + r] = keys[r];
+        c_v[rp + r] = vals[r];
+      }
+    }
   } else {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int s0 = warp * 32; s0 < S; s0 += nw * 32) {
@@ -450,9 +476,12 @@ static cudaError_t num_block(spgemm_plan_s *p, cudaStream_t st, const Args &a, c
                              int threads, const int32_t *c_rp, int32_t *c_ci, T *c_v) {
   size_t smem = (size_t)S * (sizeof(int32_t) + sizeof(T));
   int mode = 0;
+  // sorted output: rank by a bitmap over each row's column window of up to
+  // kSortWindowWords x 32 columns (the whole of B's columns when they fit)
+  const int words = (int)std::min<int64_t>(p->bm_words, kSortWindowWords);
   if (p->flags & SPGEMM_SORTED) {
-    const size_t extra = (size_t)p->bm_words * 8;
-    if (p->k <= kBitmapMaxCols && smem + extra <= (size_t)max_smem_per_block()) {
+    const size_t extra = (size_t)words * 8;
+    if (smem + extra + kStaticSmemReserve <= (size_t)max_smem_per_block()) {
       mode = 2;
       smem += extra;
     } else {
@@ -463,7 +492,7 @@ static cudaError_t num_block(spgemm_plan_s *p, cudaStream_t st, const Args &a, c
   if (e != cudaSuccess) return e;
   {
     KernelScope ks(p, "num_block_" + std::to_string(S), st);
-    k_num_block<T, S><<<(unsigned)n, threads, smem, st>>>(a, rows, c_rp, c_ci, c_v, mode, p->bm_words);
+    k_num_block<T, S><<<(unsigned)n, threads, smem, st>>>(a, rows, c_rp, c_ci, c_v, mode, words);
   }
   return cudaGetLastError();
 }

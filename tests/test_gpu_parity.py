@@ -308,3 +308,18 @@ def test_out_of_range_column_is_an_error_not_a_fault(where):
     # the context is still usable
     C, _ = gpu_product(inputs.er_exact(64, 4, seed=103), inputs.er_exact(64, 4, seed=104), torch.float64, True)
     assert C.nnz > 0
+
+
+@pytest.mark.parametrize("sorted_output", [True, False])
+def test_block_rows_wider_than_the_sort_window(sorted_output):
+    # ~1200 products per row: block bins.  B has 2^20 columns and half of each
+    # row's entries spread over all of them, so every row of C spans far more
+    # than the 65536-column window of the bitmap sort: the bitonic fallback.
+    A = inputs.er_exact(300, 30, seed=121, ncols=400)
+    B1 = inputs.er_exact(400, 40, seed=122, ncols=1 << 20)
+    narrow = inputs.er_exact(400, 40, seed=123, ncols=3000)
+    B = CSR(400, 1 << 20, B1.row_ptr, np.where(np.arange(B1.nnz) % 40 < 20, B1.col_idx, narrow.col_idx).astype(np.int32),
+            B1.vals)
+    C, st = gpu_product(A, B, torch.float64, sorted_output)
+    assert sum(st["num_bin_rows"][5:9]) > 0
+    assert_matches_oracle(C, A, B, sorted_output)
