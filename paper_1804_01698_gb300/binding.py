@@ -418,6 +418,12 @@ class Batch:
             e0, e1 = int(rp[0].item()), int(rp[-1].item())
         return DeviceCSR(r1 - r0, self.Bs[p].ncols, rp - e0, self.c_col_idx[e0:e1], self.c_vals[e0:e1])
 
+    def workspace_bytes(self) -> int:
+        v = ctypes.c_size_t()
+        _check(self.lib.spgemm_plan_workspace_bytes(self.lib.spgemm_batch_plan(self.handle), ctypes.byref(v)),
+               "spgemm_plan_workspace_bytes")
+        return int(v.value)
+
     def plan_stats(self) -> dict:
         s = Stats()
         status = self.lib.spgemm_plan_stats(self.lib.spgemm_batch_plan(self.handle), ctypes.byref(s))

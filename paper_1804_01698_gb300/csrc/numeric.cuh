@@ -75,6 +75,83 @@ __device__ __forceinline__ void bitonic_sort(uint32_t *keys, T *vals, int n, int
   }
 }
 
+// Compare-exchange of registers r and r | JR of every lane (strides of 32 or
+// more of the bitonic network below), ascending where bit kk of the element
+// index is clear.
+template <typename T, int R, int JR>
+__device__ __forceinline__ void reg_stage(uint32_t (&k)[R], T (&v)[R], int kk) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    if ((r & JR) == 0) {
+      const bool asc = ((r * 32) & kk) == 0;
+      const int q = r | JR;
+      if ((k[r] > k[q]) == asc) {
+        const uint32_t tk = k[r];
+        k[r] = k[q];
+        k[q] = tk;
+        const T tv = v[r];
+        v[r] = v[q];
+        v[q] = tv;
+      }
+    }
+  }
+}
+
+// Sorted store of a warp's row: the nnz compacted (key, value) pairs are
+// sorted by a bitonic network held in registers, element e = r * 32 + lane
+// in register r of lane `lane`; strides of 32 or more swap registers of one
+// lane, shorter strides exchange with lane ^ stride by shuffles.  The stage
+// loops stay loops (only the register index is unrolled) to keep the code
+// small.  Padding keys (-1, the largest as unsigned) sort last and are not
+// stored.
+template <typename T, int R>
+__device__ __forceinline__ void warp_sort_store(const int32_t *keys, const T *vals, int nnz, int lane,
+                                                int32_t *__restrict__ out_ci, T *__restrict__ out_v) {
+  uint32_t k[R];
+  T v[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int e = r * 32 + lane;
+    k[r] = e < nnz ? (uint32_t)keys[e] : 0xffffffffu;
+    v[r] = e < nnz ? vals[e] : T(0);
+  }
+#pragma unroll 1
+  for (int kk = 2; kk <= 32 * R; kk <<= 1) {
+#pragma unroll 1
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      if (j >= 32) {
+        switch (j >> 5) {
+          case 1: reg_stage<T, R, 1>(k, v, kk); break;
+          case 2: if (R > 2) reg_stage<T, R, (R > 2 ? 2 : 1)>(k, v, kk); break;
+          case 4: if (R > 4) reg_stage<T, R, (R > 4 ? 4 : 1)>(k, v, kk); break;
+          default: if (R > 8) reg_stage<T, R, (R > 8 ? 8 : 1)>(k, v, kk); break;
+        }
+      } else {
+        const bool lower = (lane & j) == 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int e = r * 32 + lane;
+          const uint32_t pk = __shfl_xor_sync(0xffffffffu, k[r], j);
+          const T pv = __shfl_xor_sync(0xffffffffu, v[r], j);
+          const bool asc = (e & kk) == 0;
+          if ((lower == asc) ? (pk < k[r]) : (pk > k[r])) {
+            k[r] = pk;
+            v[r] = pv;
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int e = r * 32 + lane;
+    if (e < nnz) {
+      out_ci[e] = (int32_t)k[r];
+      out_v[e] = v[r];
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 template <typename T, int S>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, 8)
@@ -121,14 +198,22 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 8)
       base += __popc(m);
       __syncwarp();
     }
-    int P = 32;
-    while (P < base) P <<= 1;
-    for (int r = base + lane; r < P; r += 32) keys[r] = kEmpty;
-    __syncwarp();
-    bitonic_sort(reinterpret_cast<uint32_t *>(keys), vals, P, lane, 32, [] { __syncwarp(); });
-    for (int r = lane; r < nnz; r += 32) {
-      c_ci[rp + r] = keys[r];
-      c_v[rp + r] = vals[r];
+    const int cnt = min(base, nnz);
+    if (cnt <= 32) warp_sort_store<T, 1>(keys, vals, cnt, lane, c_ci + rp, c_v + rp);
+    else if (cnt <= 64) warp_sort_store<T, 2>(keys, vals, cnt, lane, c_ci + rp, c_v + rp);
+    else if (cnt <= 128) warp_sort_store<T, 4>(keys, vals, cnt, lane, c_ci + rp, c_v + rp);
+    else if (cnt <= 256) warp_sort_store<T, 8>(keys, vals, cnt, lane, c_ci + rp, c_v + rp);
+    else {
+      // longer rows: the same network in shared memory (measured faster here)
+      int P = 512;
+      while (P < cnt) P <<= 1;
+      for (int r = cnt + lane; r < P; r += 32) keys[r] = kEmpty;
+      __syncwarp();
+      bitonic_sort(reinterpret_cast<uint32_t *>(keys), vals, P, lane, 32, [] { __syncwarp(); });
+      for (int r = lane; r < cnt; r += 32) {
+        c_ci[rp + r] = keys[r];
+        c_v[rp + r] = vals[r];
+      }
     }
     if (lane == 0 && base != nnz) raise_err(a.err, kErrProbe);
   } else {

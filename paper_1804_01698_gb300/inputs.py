@@ -46,6 +46,8 @@ TAG_FRONTIER_ROWS = 5
 TAG_SHUFFLE = 6
 TAG_PERM = 7
 TAG_BATCH = 8
+TAG_ARRIVAL = 9
+TAG_MIX = 10
 
 
 def splitmix64(x: np.ndarray) -> np.ndarray:
@@ -260,6 +262,32 @@ def er_batch(count: int, seed: int, n_lo: int = 256, n_hi: int = 65536, k_lo: in
     with its own seed), for products A_i * A_i."""
     n, k = batch_sizes(count, seed, n_lo, n_hi, k_lo, k_hi)
     return [er_exact(int(n[i]), int(k[i]), seed=seed * 7919 + i + 1, kind=kind, dtype=dtype) for i in range(count)]
+
+
+def poisson_arrivals(count: int, rate: float, seed: int) -> np.ndarray:
+    """Arrival times (seconds) of a Poisson process of the given rate."""
+    u = draw_unit(seed, TAG_ARRIVAL, np.arange(count, dtype=np.uint64))
+    return np.cumsum(-np.log(u) / rate)
+
+
+def serving_mix(count: int, seed: int, g_lo: int = 8, g_hi: int = 48, n_lo: int = 256, n_hi: int = 65536) -> list:
+    """The serving mix: request i is, with probability 1/2 each, an
+    Erdos-Renyi product A*A (sizes as er_batch) or an AMG-style product A*P
+    (3D 7-point Poisson matrix on a g^3 grid, g uniform in {g_lo..g_hi}, times
+    the 2x2x2 aggregation prolongator).  Returns a list of (A, B) pairs."""
+    idx = np.arange(count, dtype=np.uint64)
+    pick = draw_unit(seed, TAG_MIX, 2 * idx) < 0.5
+    ug = draw_unit(seed, TAG_MIX, 2 * idx + np.uint64(1))
+    g = g_lo + np.minimum((ug * (g_hi - g_lo + 1)).astype(np.int64), g_hi - g_lo)
+    n, k = batch_sizes(count, seed, n_lo, n_hi)
+    out = []
+    for i in range(count):
+        if pick[i]:
+            a = er_exact(int(n[i]), int(k[i]), seed=seed * 7919 + i + 1)
+            out.append((a, a))
+        else:
+            out.append((poisson7(int(g[i])), aggregation(int(g[i]))))
+    return out
 
 
 # Workloads named by what they are, with their sizes.
