@@ -23,55 +23,95 @@ namespace sg {
 struct BatchDev {
   spgemm_csr a, b;
   long long a_row, a_nnz, b_row, b_nnz, b_col;  // offsets of this product in the packed operands
+  long long chunk0;                              // first pack chunk of this product
 };
 
-// Block p copies product p into the packed operands and checks its indices.
+// Elements of each operand array one block copies: a product of n elements
+// in its largest array gets ceil(n / kPackChunk) blocks, so the copy of a
+// large product spreads over the GPU instead of one SM.
+constexpr int64_t kPackChunk = 8192;
+constexpr int kPackUnroll = 8;
+
+int64_t pack_chunks(const spgemm_csr &a, const spgemm_csr &b) {
+  int64_t n = a.nrows + 1;
+  if (a.nnz > n) n = a.nnz;
+  if (b.nrows + 1 > n) n = b.nrows + 1;
+  if (b.nnz > n) n = b.nnz;
+  return (n + kPackChunk - 1) / kPackChunk;
+}
+
+// dst[i] = op(src[i], i) for i in [lo, hi): kPackUnroll loads in flight per
+// thread before the stores.
+template <typename W, typename Op>
+__device__ __forceinline__ void pack_range(const W *__restrict__ src, W *__restrict__ dst, int64_t lo, int64_t hi,
+                                           Op op) {
+  for (int64_t base = lo + threadIdx.x; base < hi; base += (int64_t)blockDim.x * kPackUnroll) {
+    W v[kPackUnroll];
+#pragma unroll
+    for (int u = 0; u < kPackUnroll; ++u) {
+      const int64_t i = base + (int64_t)u * blockDim.x;
+      if (i < hi) v[u] = src[i];
+    }
+#pragma unroll
+    for (int u = 0; u < kPackUnroll; ++u) {
+      const int64_t i = base + (int64_t)u * blockDim.x;
+      if (i < hi) dst[i] = op(v[u], i);
+    }
+  }
+}
+
+// Copies one operand (row pointers shifted by `nnz_off`, column indices by
+// `col_off`, values as words) of a product: chunk `c` of each array.
+template <typename W>
+__device__ __forceinline__ void pack_operand(const spgemm_csr &m, int64_t c, long long row_at, long long nnz_off,
+                                             long long col_off, int32_t *rp, int32_t *ci, unsigned char *vals,
+                                             uint32_t *err) {
+  const int64_t lo = c * kPackChunk;
+  const int32_t nnz = (int32_t)m.nnz;
+  const int64_t ncols = m.ncols;
+  // row pointers 0..nrows are checked; 0..nrows-1 are written (the packed
+  // array's last entry is written by the host)
+  {
+    const int64_t hi = lo + kPackChunk < m.nrows + 1 ? lo + kPackChunk : m.nrows + 1;
+    const int64_t nrows = m.nrows;
+    pack_range<int32_t>(m.row_ptr, rp + row_at, lo, hi < nrows ? hi : nrows, [&](int32_t x, int64_t) {
+      if (x < 0 || x > nnz) raise_err(err, kErrCsr);
+      return (int32_t)(x + nnz_off);
+    });
+    if (threadIdx.x == 0 && lo == 0 && m.row_ptr[0] != 0) raise_err(err, kErrCsr);
+    if (threadIdx.x == 0 && lo <= nrows && nrows < hi && m.row_ptr[nrows] != nnz) raise_err(err, kErrCsr);
+  }
+  const int64_t hi = lo + kPackChunk < m.nnz ? lo + kPackChunk : m.nnz;
+  if (lo >= hi) return;
+  pack_range<int32_t>(m.col_idx, ci + nnz_off, lo, hi, [&](int32_t c2, int64_t) {
+    if ((uint64_t)(int64_t)c2 >= (uint64_t)ncols) raise_err(err, kErrCsr);
+    return (int32_t)(c2 + col_off);
+  });
+  pack_range<W>(static_cast<const W *>(m.vals), reinterpret_cast<W *>(vals) + nnz_off, lo, hi,
+                [](W v, int64_t) { return v; });
+}
+
+// Block b copies chunk (b - chunk0[p]) of product p, the product found by a
+// binary search over the products' first chunks; indices are checked.
 __global__ void __launch_bounds__(256)
-    k_batch_pack(const BatchDev *__restrict__ d, int vsize, int32_t *__restrict__ arp, int32_t *__restrict__ aci,
-                 unsigned char *__restrict__ av, int32_t *__restrict__ brp, int32_t *__restrict__ bci,
-                 unsigned char *__restrict__ bv, uint32_t *err) {
-  const BatchDev p = d[blockIdx.x];
-  // A_p: rows, then entries (columns shifted by the rows of B before p)
-  for (int64_t r = threadIdx.x; r < p.a.nrows; r += blockDim.x) {
-    const int32_t x = p.a.row_ptr[r];
-    if (x < 0 || x > p.a.nnz) raise_err(err, kErrCsr);
-    arp[p.a_row + r] = (int32_t)(x + p.a_nnz);
+    k_batch_pack(const BatchDev *__restrict__ d, int64_t nprod, int vsize, int32_t *__restrict__ arp,
+                 int32_t *__restrict__ aci, unsigned char *__restrict__ av, int32_t *__restrict__ brp,
+                 int32_t *__restrict__ bci, unsigned char *__restrict__ bv, uint32_t *err) {
+  const int64_t blk = blockIdx.x;
+  int64_t lo = 0, hi = nprod - 1;  // last product whose first chunk is <= blk
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (d[mid].chunk0 <= blk) lo = mid;
+    else hi = mid - 1;
   }
-  if (threadIdx.x == 0 && (p.a.row_ptr[0] != 0 || p.a.row_ptr[p.a.nrows] != p.a.nnz)) raise_err(err, kErrCsr);
-  for (int64_t j = threadIdx.x; j < p.a.nnz; j += blockDim.x) {
-    const int32_t c = p.a.col_idx[j];
-    if ((uint64_t)(int64_t)c >= (uint64_t)p.a.ncols) raise_err(err, kErrCsr);
-    aci[p.a_nnz + j] = (int32_t)(c + p.b_row);
-  }
+  const BatchDev &p = d[lo];
+  const int64_t c = blk - p.chunk0;
   if (vsize == 8) {
-    const unsigned long long *src = static_cast<const unsigned long long *>(p.a.vals);
-    unsigned long long *dst = reinterpret_cast<unsigned long long *>(av) + p.a_nnz;
-    for (int64_t t = threadIdx.x; t < p.a.nnz; t += blockDim.x) dst[t] = src[t];
+    pack_operand<unsigned long long>(p.a, c, p.a_row, p.a_nnz, p.b_row, arp, aci, av, err);
+    pack_operand<unsigned long long>(p.b, c, p.b_row, p.b_nnz, p.b_col, brp, bci, bv, err);
   } else {
-    const uint32_t *src = static_cast<const uint32_t *>(p.a.vals);
-    uint32_t *dst = reinterpret_cast<uint32_t *>(av) + p.a_nnz;
-    for (int64_t t = threadIdx.x; t < p.a.nnz; t += blockDim.x) dst[t] = src[t];
-  }
-  // B_p: columns shifted by the columns of B before p
-  for (int64_t r = threadIdx.x; r < p.b.nrows; r += blockDim.x) {
-    const int32_t x = p.b.row_ptr[r];
-    if (x < 0 || x > p.b.nnz) raise_err(err, kErrCsr);
-    brp[p.b_row + r] = (int32_t)(x + p.b_nnz);
-  }
-  if (threadIdx.x == 0 && (p.b.row_ptr[0] != 0 || p.b.row_ptr[p.b.nrows] != p.b.nnz)) raise_err(err, kErrCsr);
-  for (int64_t j = threadIdx.x; j < p.b.nnz; j += blockDim.x) {
-    const int32_t c = p.b.col_idx[j];
-    if ((uint64_t)(int64_t)c >= (uint64_t)p.b.ncols) raise_err(err, kErrCsr);
-    bci[p.b_nnz + j] = (int32_t)(c + p.b_col);
-  }
-  if (vsize == 8) {
-    const unsigned long long *src = static_cast<const unsigned long long *>(p.b.vals);
-    unsigned long long *dst = reinterpret_cast<unsigned long long *>(bv) + p.b_nnz;
-    for (int64_t t = threadIdx.x; t < p.b.nnz; t += blockDim.x) dst[t] = src[t];
-  } else {
-    const uint32_t *src = static_cast<const uint32_t *>(p.b.vals);
-    uint32_t *dst = reinterpret_cast<uint32_t *>(bv) + p.b_nnz;
-    for (int64_t t = threadIdx.x; t < p.b.nnz; t += blockDim.x) dst[t] = src[t];
+    pack_operand<uint32_t>(p.a, c, p.a_row, p.a_nnz, p.b_row, arp, aci, av, err);
+    pack_operand<uint32_t>(p.b, c, p.b_row, p.b_nnz, p.b_col, brp, bci, bv, err);
   }
 }
 
@@ -132,20 +172,22 @@ int spgemm_batch_create(spgemm_batch_t *out, int64_t nprod, const spgemm_csr *A,
   if (dtype != SPGEMM_I64 && dtype != SPGEMM_F32 && dtype != SPGEMM_F64) return SPGEMM_ERR_INVALID_ARGUMENT;
   const int vsize = dtype == SPGEMM_F32 ? 4 : 8;
   std::vector<BatchDev> h((size_t)nprod);
-  long long am = 0, an = 0, bm = 0, bn = 0, bk = 0;
+  long long am = 0, an = 0, bm = 0, bn = 0, bk = 0, chunks = 0;
   for (int64_t p = 0; p < nprod; ++p) {
     if (bad(A[p]) || bad(B[p]) || A[p].ncols != B[p].nrows) {
       set_last_error("product " + std::to_string(p) + ": bad descriptor or inner dimensions differ");
       return SPGEMM_ERR_INVALID_ARGUMENT;
     }
-    h[p] = BatchDev{A[p], B[p], am, an, bm, bn, bk};
+    h[p] = BatchDev{A[p], B[p], am, an, bm, bn, bk, chunks};
+    chunks += pack_chunks(A[p], B[p]);
     am += A[p].nrows;
     an += A[p].nnz;
     bm += B[p].nrows;
     bn += B[p].nnz;
     bk += B[p].ncols;
   }
-  if (am >= INT32_MAX || an > INT32_MAX || bm >= INT32_MAX || bn > INT32_MAX || bk > INT32_MAX) {
+  if (am >= INT32_MAX || an > INT32_MAX || bm >= INT32_MAX || bn > INT32_MAX || bk > INT32_MAX ||
+      chunks > INT32_MAX) {
     set_last_error("the packed batch exceeds int32 indexing");
     return SPGEMM_ERR_INDEX_OVERFLOW;
   }
@@ -214,8 +256,9 @@ int spgemm_batch_create(spgemm_batch_t *out, int64_t nprod, const spgemm_csr *A,
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->arp + am, &a_end, 4, cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->brp + bm, &b_end, 4, cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) {
-    k_batch_pack<<<(unsigned)nprod, 256, 0, b->stream>>>(d_desc, vsize, b->arp, b->aci, (unsigned char *)b->av,
-                                                          b->brp, b->bci, (unsigned char *)b->bv, b->d_err);
+    k_batch_pack<<<(unsigned)chunks, 256, 0, b->stream>>>(d_desc, nprod, vsize, b->arp, b->aci,
+                                                           (unsigned char *)b->av, b->brp, b->bci,
+                                                           (unsigned char *)b->bv, b->d_err);
     e = cudaGetLastError();
   }
   uint32_t err = 0;

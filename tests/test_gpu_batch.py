@@ -82,3 +82,25 @@ def test_bad_product_is_reported():
     with pytest.raises(sg.SpgemmError) as ei:
         sg.Batch([dg, db], [dg, dg], True)
     assert ei.value.status == -2
+
+
+@pytest.mark.parametrize("where", ["col_idx", "row_ptr_end"])
+def test_bad_index_in_a_later_pack_chunk_is_reported(where):
+    """The pack kernel splits a large product over several blocks; a bad
+    entry far into the product (past the first 8192-element chunk) is
+    still found."""
+    from paper_1804_01698_gb300 import binding as sg
+    small = inputs.er_exact(50, 3, seed=521)
+    big = inputs.er_exact(20000, 3, seed=522)           # 20001 row pointers, 60000 entries
+    if where == "col_idx":
+        ci = big.col_idx.copy()
+        ci[40000] = -1
+        big = CSR(big.nrows, big.ncols, big.row_ptr, ci, big.vals)
+    else:
+        rp = big.row_ptr.copy()
+        rp[-1] -= 1                                      # last row pointer != nnz
+        big = CSR(big.nrows, big.ncols, rp, big.col_idx, big.vals)
+    ds, db = sg.to_device(small), sg.to_device(big)
+    with pytest.raises(sg.SpgemmError) as ei:
+        sg.Batch([ds, db], [ds, sg.to_device(inputs.er_exact(20000, 2, seed=523))], True)
+    assert ei.value.status == -2
