@@ -14,6 +14,10 @@ the same workload instead (rank 0 only; other ranks exit at once).
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
                         [--unsorted] [--impl reference]
+Workloads: the named single products of inputs.WORKLOADS (default
+rmat16_ef16_f64; also er4096_k8_f64, rmat18_frontier1024_f32,
+tc_rmat16_lu_f64), batch_er2000 (batched products), serve_mix (serving
+loop) and sweep_rmat (density and size sweeps).
 For N > 1 launch under torch.distributed.run: each rank runs an
 independent replica on its own GPU (weak scaling); timing takes the maximum
 over ranks.
@@ -403,6 +407,80 @@ def run_serve(args) -> int:
     return 0
 
 
+def run_sweep(args) -> int:
+    """Scaling with density and with size, as Sec. 5.4.1 and 5.4.2 measure
+    them: C = A*A for R-MAT matrices of G500 skew (.57,.19,.19,.05) and of
+    uniform (ER, .25 each) parameters, (a) at scale 16 with edge factor 2 to
+    64 and (b) at edge factor 16 with scale 8 to 17; FP64, sorted and
+    unsorted output.  Each point is timed like the headline step (plan,
+    symbolic, allocation of C, numeric; L2 flushed between steps)."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1804_01698_gb300 import binding as sg
+    from paper_1804_01698_gb300 import inputs
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    kinds = {"g500": (0.57, 0.19, 0.19, 0.05), "er": (0.25, 0.25, 0.25, 0.25)}
+    points = [("density", kind, 16, ef) for kind in kinds for ef in (2, 4, 8, 16, 32, 64)]
+    points += [("size", kind, sc, 16) for kind in kinds for sc in (8, 10, 12, 14, 16, 17)]
+    steps = max(1, min(args.steps, 5))
+    rows, launches = [], 0
+    with ClockSampler(0) as clocks:
+        for sweep, kind, scale, ef in points:
+            A = inputs.rmat(scale, ef, abcd=kinds[kind], seed=inputs.SEED_BASE + 7 + scale * 100 + ef)
+            dA = sg.to_device(A, dev)
+            row = {"sweep": sweep, "kind": kind, "scale": scale, "edge_factor": ef, "nnz_a": A.nnz}
+            for sorted_flag in (True, False):
+                ts = []
+                for it in range(steps + 1):
+                    flush.fill_(it & 0xFF)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    plan = sg.Plan(dA, dA, sorted_flag, stream=stream)
+                    nnz = plan.symbolic()
+                    C = plan.numeric()
+                    e1.record(stream)
+                    e1.synchronize()
+                    st = plan.stats()
+                    if st["status"] != 0:
+                        raise RuntimeError(f"device error status {st['status']}")
+                    if it > 0:                       # the first run is the warm-up
+                        ts.append(e0.elapsed_time(e1))
+                        launches += st["kernel_launches"]
+                    plan.destroy()
+                    del C
+                flop = st["total_flop"]
+                ms = statistics.median(ts)
+                row["flop"], row["nnz_c"] = flop, nnz
+                row["sorted_gflops" if sorted_flag else "unsorted_gflops"] = 2 * flop / (ms * 1e-3) / 1e9
+                row["sorted_ms" if sorted_flag else "unsorted_ms"] = ms
+            row["compression_ratio"] = row["flop"] / row["nnz_c"] if row["nnz_c"] else None
+            rows.append(row)
+            print(json.dumps(row), file=sys.stderr, flush=True)
+            del dA
+    g16 = next(r for r in rows if r["sweep"] == "density" and r["kind"] == "g500" and r["edge_factor"] == 16)
+    line = {
+        "metric": "SpGEMM GFLOP/s (2*flop per second)", "value": g16["sorted_gflops"], "unit": "GFLOP/s",
+        "n_gpus": 1, "steps": steps, "warmup": 1, "ms_per_step": g16["sorted_ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "R-MAT A*A sweeps: scale 16 with edge factor 2..64, and edge factor 16 with scale "
+                               "8..17; G500 and ER parameters; FP64; sorted and unsorted",
+                   "headline_point": "G500 scale 16 EF 16, sorted", "l2": "256 MiB flush between steps",
+                   "timing": "median over steps per point"},
+        "sweep": rows,
+        "e2e": None,
+        "gpu_launches": launches,
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------------------- GPU arm
 
 def main() -> int:
@@ -413,6 +491,8 @@ def main() -> int:
         return run_batch(args)
     if args.workload.startswith("serve_mix"):
         return run_serve(args)
+    if args.workload == "sweep_rmat":
+        return run_sweep(args)
 
     import torch
     import torch.distributed as dist

@@ -290,11 +290,64 @@ def serving_mix(count: int, seed: int, g_lo: int = 8, g_hi: int = 48, n_lo: int 
     return out
 
 
+def undirected(m: CSR, dtype=np.float64) -> CSR:
+    """Adjacency matrix of the undirected simple graph behind m's pattern:
+    the pattern of m + m^T without the diagonal, values 1."""
+    rows = np.repeat(np.arange(m.nrows, dtype=np.int64), np.diff(m.row_ptr))
+    cols = m.col_idx.astype(np.int64)
+    off = rows != cols
+    r = np.concatenate([rows[off], cols[off]])
+    c = np.concatenate([cols[off], rows[off]])
+    rp, ci = from_coo(m.nrows, m.nrows, r, c)
+    return CSR(m.nrows, m.nrows, rp, ci, np.ones(len(ci), dtype=dtype))
+
+
+def degree_order(g: CSR) -> np.ndarray:
+    """Vertices by increasing degree (ties by index): order[new] = old."""
+    deg = np.diff(g.row_ptr)
+    return np.lexsort((np.arange(g.nrows), deg)).astype(np.int64)
+
+
+def permute_symmetric(g: CSR, order: np.ndarray) -> CSR:
+    """P g P^T for the relabelling new = position of old in `order`."""
+    new_of_old = np.empty(g.nrows, dtype=np.int64)
+    new_of_old[order] = np.arange(g.nrows, dtype=np.int64)
+    rows = new_of_old[np.repeat(np.arange(g.nrows, dtype=np.int64), np.diff(g.row_ptr))]
+    cols = new_of_old[g.col_idx.astype(np.int64)]
+    rp, ci = from_coo(g.nrows, g.nrows, rows, cols)
+    return CSR(g.nrows, g.nrows, rp, ci, np.ones(len(ci), dtype=g.vals.dtype))
+
+
+def triangular_split(g: CSR) -> tuple[CSR, CSR]:
+    """(L, U): the strictly lower and strictly upper parts of g."""
+    rows = np.repeat(np.arange(g.nrows, dtype=np.int64), np.diff(g.row_ptr))
+    cols = g.col_idx.astype(np.int64)
+    parts = []
+    for keep in (cols < rows, cols > rows):
+        rp, ci = from_coo(g.nrows, g.nrows, rows[keep], cols[keep])
+        parts.append(CSR(g.nrows, g.nrows, rp, ci, np.ones(len(ci), dtype=g.vals.dtype)))
+    return parts[0], parts[1]
+
+
+def triangle_lu(scale: int, edge_factor: int, seed: int, dtype=np.float64) -> tuple[CSR, CSR, CSR]:
+    """The triangle-counting product of Sec. 5.6 on an R-MAT graph: the
+    undirected graph of R-MAT(scale, edge_factor), relabelled by increasing
+    degree, split into strictly lower L and strictly upper U.  Returns
+    (L, U, G) with G the relabelled adjacency matrix; (L*U)_ij counts the
+    wedges i-k-j with k < min(i, j)."""
+    g0 = undirected(rmat(scale, edge_factor, seed=seed, kind="ones"), dtype)
+    g = permute_symmetric(g0, degree_order(g0))
+    L, U = triangular_split(g)
+    return L, U, g
+
+
 # Workloads named by what they are, with their sizes.
 WORKLOADS = {
     "er4096_k8_f64": dict(desc="Erdos-Renyi A*A, n=4096, 8 distinct columns per row, FP64 U(-1,1), sorted output"),
     "rmat16_ef16_f64": dict(desc="R-MAT A*A, scale 16, edge factor 16, (.57,.19,.19,.05), FP64 U(-1,1)"),
     "rmat18_frontier1024_f32": dict(desc="R-MAT scale 18 EF 16 (values 1.0) times an n x 1024 frontier stack (1-4 per column), FP32, unsorted"),
+    "tc_rmat16_lu_f64": dict(desc="triangle counting L*U: undirected R-MAT scale 16 EF 16 graph ordered by increasing "
+                                  "degree, strictly lower times strictly upper part, values 1.0 FP64, sorted output"),
 }
 
 SEED_BASE = 20180404
@@ -313,4 +366,7 @@ def workload(name: str, dtype=None):
         a = rmat(18, 16, seed=SEED_BASE + 2, kind="ones", dtype=dt)
         f = frontier(a.ncols, 1024, 1, 4, seed=SEED_BASE + 2, kind="ones", dtype=dt)
         return a, f, False
+    if name == "tc_rmat16_lu_f64":
+        L, U, _ = triangle_lu(16, 16, seed=SEED_BASE + 6, dtype=dtype or np.float64)
+        return L, U, True
     raise KeyError(name)

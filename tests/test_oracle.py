@@ -342,3 +342,76 @@ def test_generators_shapes():
     big = inputs.rmat(12, 16, seed=3)
     rl = np.diff(big.row_ptr)
     assert rl[0] == rl.max()
+
+
+# ---------------------------------------------------------------- triangle counting L*U (Sec. 5.6)
+
+def _triangles_from_lu(L, U, G):
+    """sum over stored g_ij of (L*U)_ij, halved: each triangle a < b < c has
+    its wedge b-a-c counted at (b, c) and (c, b)."""
+    C, _ = oracle.spgemm(L, U)
+    dense_c = np.zeros((G.nrows, G.nrows))
+    rows = np.repeat(np.arange(C.nrows), np.diff(C.row_ptr))
+    dense_c[rows, C.col_idx] = C.vals
+    grow = np.repeat(np.arange(G.nrows), np.diff(G.row_ptr))
+    return dense_c[grow, G.col_idx].sum() / 2, C
+
+
+def test_triangle_count_from_lu_equals_trace_of_cube():
+    """Pinned by dense linear algebra: trace(G^3) / 6 counts the triangles
+    of an undirected simple graph."""
+    L, U, G = inputs.triangle_lu(9, 8, seed=601)
+    tri, _ = _triangles_from_lu(L, U, G)
+    d = np.zeros((G.nrows, G.nrows))
+    d[np.repeat(np.arange(G.nrows), np.diff(G.row_ptr)), G.col_idx] = 1.0
+    assert np.array_equal(d, d.T) and not d.diagonal().any()
+    assert tri == np.trace(d @ d @ d) / 6
+    assert tri > 100
+
+
+def test_lu_of_the_complete_graph_is_min_of_the_indices():
+    """K_n: (L*U)_ij = #{k < min(i, j)} = min(i, j), stored for i, j >= 1;
+    C(n, 3) triangles."""
+    n = 12
+    rows, cols = np.nonzero(~np.eye(n, dtype=bool))
+    rp, ci = inputs.from_coo(n, n, rows, cols)
+    G = inputs.CSR(n, n, rp, ci, np.ones(len(ci)))
+    G = inputs.permute_symmetric(G, inputs.degree_order(G))
+    L, U = inputs.triangular_split(G)
+    tri, C = _triangles_from_lu(L, U, G)
+    assert tri == n * (n - 1) * (n - 2) / 6
+    assert C.nnz == (n - 1) * (n - 1)
+    r = np.repeat(np.arange(n), np.diff(C.row_ptr))
+    assert np.array_equal(C.vals, np.minimum(r, C.col_idx).astype(float))
+
+
+def test_lu_of_a_star_has_one_entry():
+    """A star on n vertices has no triangle; ordered by degree its centre is
+    last, and (L*U) holds only (centre, centre) = n - 1."""
+    n = 9
+    rows = np.concatenate([np.zeros(n - 1, np.int64), np.arange(1, n)])
+    cols = np.concatenate([np.arange(1, n), np.zeros(n - 1, np.int64)])
+    rp, ci = inputs.from_coo(n, n, rows, cols)
+    G = inputs.CSR(n, n, rp, ci, np.ones(len(ci)))
+    order = inputs.degree_order(G)
+    assert order[-1] == 0
+    G = inputs.permute_symmetric(G, order)
+    L, U = inputs.triangular_split(G)
+    tri, C = _triangles_from_lu(L, U, G)
+    assert tri == 0
+    assert C.nnz == 1 and C.col_idx[0] == n - 1 and C.vals[0] == n - 1
+    assert np.diff(C.row_ptr)[n - 1] == 1
+
+
+def test_degree_order_and_split():
+    L, U, G = inputs.triangle_lu(8, 8, seed=602)
+    deg = np.diff(G.row_ptr)
+    assert np.all(np.diff(deg) >= 0)
+    assert L.nnz == U.nnz == G.nnz // 2
+    for M, lower in ((L, True), (U, False)):
+        r = np.repeat(np.arange(M.nrows), np.diff(M.row_ptr))
+        assert np.all(M.col_idx < r) if lower else np.all(M.col_idx > r)
+    # U is L transposed
+    lt = sorted(zip(L.col_idx.tolist(), np.repeat(np.arange(L.nrows), np.diff(L.row_ptr)).tolist()))
+    ut = list(zip(np.repeat(np.arange(U.nrows), np.diff(U.row_ptr)).tolist(), U.col_idx.tolist()))
+    assert lt == ut
