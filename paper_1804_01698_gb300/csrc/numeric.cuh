@@ -153,6 +153,80 @@ __device__ __forceinline__ void warp_sort_store(const int32_t *keys, const T *va
 }
 
 // ---------------------------------------------------------------------------
+// Sorted store of a warp's compacted row by bucket ranks: a counting sort on
+// a monotone bucket of the column, (col - cmin) >> shift with at most nb
+// buckets (nb = the power of two >= cnt), then each entry's rank inside its
+// bucket by comparison with the bucket's other entries.  The rank is the
+// entry's position in the sorted row, so it is stored there directly.
+// Space: the warp tables hold cnt <= S/2 entries, so after compaction the
+// upper halves of keys (bucket counters) and of vals (entry indices grouped
+// by bucket) are free.  Returns false, having stored nothing and left the
+// compacted entries in place, when a bucket holds more than kMaxBucket
+// entries (columns clustered within the range): the caller then sorts by
+// the bitonic network.
+constexpr int kMaxBucket = 32;
+
+template <typename T, int S>
+__device__ __forceinline__ bool bucket_sort_store(int32_t *keys, T *vals, int cnt, int lane,
+                                                  int32_t *__restrict__ out_ci, T *__restrict__ out_v) {
+  static_assert(S >= 64, "warp tables hold at least 64 slots");
+  int32_t *bcnt = keys + S / 2;
+  int32_t *grp = reinterpret_cast<int32_t *>(vals + S / 2);
+  int32_t lo = 0x7fffffff, hi = 0;
+  for (int e = lane; e < cnt; e += 32) {
+    const int32_t c = keys[e];
+    lo = min(lo, c);
+    hi = max(hi, c);
+  }
+  lo = __reduce_min_sync(0xffffffffu, lo);
+  hi = __reduce_max_sync(0xffffffffu, hi);
+  int nb = 32;
+  while (nb < cnt) nb <<= 1;  // nb <= S/2
+  const uint32_t span = (uint32_t)(hi - lo);
+  int shift = 0;
+  while ((span >> shift) >= (uint32_t)nb) ++shift;  // buckets 0 .. nb-1
+  for (int b = lane; b < nb; b += 32) bcnt[b] = 0;
+  __syncwarp();
+  for (int e = lane; e < cnt; e += 32) atomicAdd(&bcnt[(uint32_t)(keys[e] - lo) >> shift], 1);
+  __syncwarp();
+  // exclusive scan of the counters; lane l owns counters l*per .. l*per+per-1
+  const int per = nb >> 5;
+  int sum = 0, mx = 0;
+  for (int j = 0; j < per; ++j) {
+    const int v = bcnt[lane * per + j];
+    sum += v;
+    mx = max(mx, v);
+  }
+  if (__reduce_max_sync(0xffffffffu, mx) > kMaxBucket) return false;
+  int incl = sum;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += t;
+  }
+  int run = incl - sum;
+  for (int j = 0; j < per; ++j) {
+    const int v = bcnt[lane * per + j];
+    bcnt[lane * per + j] = run;
+    run += v;
+  }
+  __syncwarp();
+  // group entry indices by bucket; afterwards bcnt[b] is the end of bucket b
+  for (int e = lane; e < cnt; e += 32) grp[atomicAdd(&bcnt[(uint32_t)(keys[e] - lo) >> shift], 1)] = e;
+  __syncwarp();
+  for (int q = lane; q < cnt; q += 32) {
+    const int e = grp[q];
+    const int32_t c = keys[e];
+    const int b = (int)((uint32_t)(c - lo) >> shift);
+    const int b1 = bcnt[b];
+    int r = b > 0 ? bcnt[b - 1] : 0;
+    for (int t = r; t < b1; ++t) r += keys[grp[t]] < c;
+    out_ci[r] = c;
+    out_v[r] = vals[e];
+  }
+  return true;
+}
+
 template <typename T, int S>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, 8)
     k_num_warp(Args a, const int32_t *__restrict__ rows, int64_t nrows, const int32_t *__restrict__ c_rp,
@@ -200,7 +274,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 8)
     }
     const int cnt = min(base, nnz);
     if (cnt <= 32) warp_sort_store<T, 1>(keys, vals, cnt, lane, c_ci + rp, c_v + rp);
-    else if (cnt <= 64) warp_sort_store<T, 2>(keys, vals, cnt, lane, c_ci + rp, c_v + rp);
+    else if (bucket_sort_store<T, S>(keys, vals, cnt, lane, c_ci + rp, c_v + rp)) {
+    } else if (cnt <= 64) warp_sort_store<T, 2>(keys, vals, cnt, lane, c_ci + rp, c_v + rp);
     else if (cnt <= 128) warp_sort_store<T, 4>(keys, vals, cnt, lane, c_ci + rp, c_v + rp);
     else if (cnt <= 256) warp_sort_store<T, 8>(keys, vals, cnt, lane, c_ci + rp, c_v + rp);
     else {

@@ -323,3 +323,32 @@ def test_block_rows_wider_than_the_sort_window(sorted_output):
     C, st = gpu_product(A, B, torch.float64, sorted_output)
     assert sum(st["num_bin_rows"][5:9]) > 0
     assert_matches_oracle(C, A, B, sorted_output)
+
+
+@pytest.mark.parametrize("far", [False, True])
+def test_warp_rows_sorted_by_bucket_rank_and_by_the_fallback(far):
+    """Sorted warp-bin rows of 33..256 entries are ranked through buckets of
+    the row's column range; a row whose columns crowd one bucket (a cluster
+    plus one far column) takes the bitonic network instead.  Both must give
+    the oracle's sorted rows."""
+    rng = np.random.default_rng(7 if far else 8)
+    n, k = 600, 70000
+    rows, cols = [], []
+    for i in range(n):
+        width = 40 + (i % 200)                      # row sizes 40 .. 239 entries
+        base = int(rng.integers(0, k - 5000))
+        if far:                                      # cluster of `width` consecutive columns + one far column
+            cs = list(range(base, base + width)) + [k - 1 - (i % 7)]
+        else:                                        # spread over the whole range
+            cs = rng.choice(k, size=width, replace=False).tolist()
+        rows += [i] * len(cs)
+        cols += cs
+    rp, ci = inputs.from_coo(n, k, np.array(rows), np.array(cols))
+    B = CSR(n, k, rp, ci, rng.uniform(-1, 1, len(ci)))
+    A = inputs.er_exact(300, 1, seed=9, ncols=n)     # each row of C is one row of B
+    for dt in (torch.float64, torch.int64):
+        a, b = (A, B) if dt == torch.float64 else (A.with_vals(np.arange(A.nnz) % 5 - 2),
+                                                    B.with_vals(np.arange(B.nnz) % 7 - 3))
+        C, stats = gpu_product(a, b, dt, True)
+        assert stats["status"] == 0
+        assert_matches_oracle(C, a, b, True)
