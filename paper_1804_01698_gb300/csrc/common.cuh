@@ -56,6 +56,7 @@ template <> struct Val<double> {
     return false;
   }
   static __device__ __forceinline__ void acc_global(double *p, double a, double b) { atomicAdd(p, a * b); }
+  static __device__ __forceinline__ void add_global(double *p, double v) { atomicAdd(p, v); }
 };
 
 template <> struct Val<float> {
@@ -64,6 +65,7 @@ template <> struct Val<float> {
     return true;
   }
   static __device__ __forceinline__ void acc_global(float *p, float a, float b) { atomicAdd(p, a * b); }
+  static __device__ __forceinline__ void add_global(float *p, float v) { atomicAdd(p, v); }
 };
 
 template <> struct Val<int64_t> {
@@ -73,6 +75,9 @@ template <> struct Val<int64_t> {
   }
   static __device__ __forceinline__ void acc_global(int64_t *p, int64_t a, int64_t b) {
     atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)a * (unsigned long long)b);
+  }
+  static __device__ __forceinline__ void add_global(int64_t *p, int64_t v) {
+    atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
   }
 };
 

@@ -67,6 +67,23 @@ constexpr int64_t kBitmapMinBound = 3072;
 constexpr int64_t kBitmapMidMax = 24576;
 constexpr int64_t kBlockSymMax = 24576;      // 3/4 of 32768 (global-table inputs)
 constexpr int64_t kBitmapMaxCols = 1 << 18;  // bitmap + prefix <= 64 KB
+
+// A bitmap row whose flop is large next to its output is split over several
+// blocks, each taking a contiguous range of the row's stored a_ik (equal
+// flop) and adding its partial sums into C with global atomics.  Every part
+// keeps at least max(kSplitMinFlop, kSplitFlopPerEntry * nnz) products, so
+// the atomic adds stay a small fraction of its products.
+constexpr long long kSplitMinFlop = 65536;
+constexpr long long kSplitFlopPerEntry = 8;
+constexpr long long kSplitMaxParts = 64;
+
+__host__ __device__ inline int bm_split_parts(long long flop, long long nnz) {
+  const long long unit = kSplitMinFlop > kSplitFlopPerEntry * nnz ? kSplitMinFlop : kSplitFlopPerEntry * nnz;
+  long long parts = flop / unit;
+  if (parts < 1) parts = 1;
+  if (parts > kSplitMaxParts) parts = kSplitMaxParts;
+  return (int)parts;
+}
 constexpr int64_t kSortWindowWords = 2048;   // block-bin sort: 65536-column window per row
 
 // Device counters of a plan (zeroed at creation).
@@ -125,7 +142,7 @@ struct spgemm_plan_s {
   int32_t *perm2;  // rows grouped by numeric bin
   uint32_t *bitmaps;  // one bitmap per row of the symbolic bitmap bin
   size_t bitmaps_bytes;
-  int2 *bm_items;     // numeric bitmap work items (bitmap index, window)
+  int4 *bm_items;     // numeric bitmap work items (bitmap index, window, part, parts)
   size_t bm_items_bytes;
   void *gtab;         // global hash tables (heavy rows without bitmaps)
   size_t gtab_bytes;

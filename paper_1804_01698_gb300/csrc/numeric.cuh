@@ -422,12 +422,76 @@ __global__ void __launch_bounds__(1024, 1)
   }
 }
 
-// Heavy rows with a saved column bitmap.  Item (t, wdw): bitmap t of the
-// symbolic bitmap bin (row bm_rows[t]), output ranks [wdw*cap, (wdw+1)*cap).
+// Part `part` of `parts` of row i's stored a_ik: the contiguous range
+// [*j_lo, *j_hi) of entries whose products start in the part's equal share
+// of the row's flop (an entry belongs to the share holding its first
+// product).  Whole block.
+__device__ __forceinline__ void part_range(const Args &a, int32_t i, int part, int parts, int32_t *j_lo,
+                                           int32_t *j_hi) {
+  __shared__ long long s_ll[33];
+  const int32_t j0 = a.arp[i], j1 = a.arp[i + 1];
+  long long f = 0;
+  for (int32_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+    const int32_t c = a.aci[j];
+    f += a.brp[c + 1] - a.brp[c];
+  }
+  const long long F = block_sum(f, s_ll);
+  const long long lo_f = F / parts * part + F % parts * part / parts;
+  const long long hi_f = F / parts * (part + 1) + F % parts * (part + 1) / parts;
+  long long below_lo = 0, below_hi = 0, carry = 0;
+  for (int32_t base = j0; base < j1; base += blockDim.x) {
+    const int32_t j = base + threadIdx.x;
+    long long len = 0;
+    if (j < j1) {
+      const int32_t c = a.aci[j];
+      len = a.brp[c + 1] - a.brp[c];
+    }
+    long long tot;
+    const long long excl = carry + block_excl_scan(len, s_ll, &tot);
+    if (j < j1) {
+      below_lo += excl < lo_f;
+      below_hi += excl < hi_f;
+    }
+    carry += tot;
+  }
+  const long long n_lo = block_sum(below_lo, s_ll), n_hi = block_sum(below_hi, s_ll);
+  *j_lo = part == 0 ? j0 : j0 + (int32_t)n_lo;
+  *j_hi = part == parts - 1 ? j1 : j0 + (int32_t)n_hi;
+}
+
+// Values of the split bitmap rows start at zero: their parts add into them.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_bm_zero_split(const int32_t *__restrict__ bm_rows, int64_t nbm, const int64_t *__restrict__ flop,
+                    const int32_t *__restrict__ c_rp, T *__restrict__ c_v) {
+  for (int64_t t = blockIdx.x; t < nbm; t += gridDim.x) {
+    const int32_t i = bm_rows[t];
+    const int32_t rp = c_rp[i], nnz = c_rp[i + 1] - rp;
+    if (bm_split_parts(flop[i], nnz) < 2) continue;
+    for (int32_t r = threadIdx.x; r < nnz; r += blockDim.x) c_v[rp + r] = T(0);
+  }
+}
+
+// Rows whose flop is at least kAggregateMinRatio times their output size
+// send many products to the same columns at once (hub columns of skewed
+// graphs), and the compare-and-swap loops on those slots serialise.  In such
+// rows the lanes that are converged at an accumulation and hold the same
+// output rank first sum their products by shuffles (__match_any_sync), and
+// one of them adds the sum.  Measured: worth it only for such rows; for rows
+// of smaller ratio the match costs more than the contention it removes.
+constexpr long long kAggregateMinRatio = 32;
+
+// Heavy rows with a saved column bitmap.  Item (t, wdw, part, parts): bitmap
+// t of the symbolic bitmap bin (row bm_rows[t]), output ranks
+// [wdw*cap, (wdw+1)*cap), products of the part'th of `parts` ranges of the
+// row's stored a_ik.  A row in one part stores its values; a split row's
+// parts add theirs into C (zeroed by k_bm_zero_split) and part 0 stores
+// the columns.
 template <typename T>
 __global__ void __launch_bounds__(1024, 1)
-    k_num_bitmap(Args a, const int32_t *__restrict__ bm_rows, const int2 *__restrict__ items,
-                 const uint32_t *__restrict__ bitmaps, int words, int cap, const int32_t *__restrict__ c_rp,
+    k_num_bitmap(Args a, const int32_t *__restrict__ bm_rows, const int4 *__restrict__ items,
+                 const int64_t *__restrict__ flop, const uint32_t *__restrict__ bitmaps, int words, int cap,
+                 const int32_t *__restrict__ c_rp,
                  int32_t *__restrict__ c_ci, T *__restrict__ c_v) {
   extern __shared__ __align__(16) unsigned char sm_num_bm[];
   __shared__ int red[33];
@@ -437,8 +501,10 @@ __global__ void __launch_bounds__(1024, 1)
   T *vals = reinterpret_cast<T *>(sm_num_bm);
   // word w of the row's column bitmap and the number of set bits before it
   uint2 *rk = reinterpret_cast<uint2 *>(sm_num_bm + (size_t)cap * sizeof(T));
-  const int2 item = items[blockIdx.x];
+  const int4 item = items[blockIdx.x];
   const int32_t i = bm_rows[item.x];
+  const int part = item.z, parts = item.w;
+  const bool agg = flop[i] >= kAggregateMinRatio * (c_rp[i + 1] - c_rp[i]);
   const int32_t rp = c_rp[i];
   const int32_t nnz = c_rp[i + 1] - rp;
   const int32_t lo = item.y * cap;
@@ -459,14 +525,29 @@ __global__ void __launch_bounds__(1024, 1)
     run += __popc(rk[w].x);
   }
   for (int r = threadIdx.x; r < hi - lo; r += blockDim.x) vals[r] = T(0);
+  int32_t j_lo = a.arp[i], j_hi = a.arp[i + 1];
+  if (parts > 1) part_range(a, i, part, parts, &j_lo, &j_hi);
   __syncthreads();
   const int G = a.G;
-  block_row_products<kUN, true, T>(a.arp[i], a.arp[i + 1], G, a.aci, (const T *)a.av, a.brp, a.bci,
+  block_row_products<kUN, true, T>(j_lo, j_hi, G, a.aci, (const T *)a.av, a.brp, a.bci,
                                    (const T *)a.bv, (int32_t)a.k, a.err, Stage<T>{s_ent, &s_next, s_wsum},
                                  [&](int32_t c, T av, T bv) {
                                    const uint2 word = rk[c >> 5];
                                    const int r = (int)word.y + __popc(word.x & ((1u << (c & 31)) - 1u));
                                    if (r >= lo && r < hi) {
+                                     if (agg) {
+                                       const unsigned act = __activemask();
+                                       const unsigned grp = __match_any_sync(act, r);
+                                       const int ln = threadIdx.x & 31;
+                                       if (grp != (1u << ln)) {
+                                         const T v = av * bv;
+                                         T sum = T(0);
+                                         for (unsigned m = grp; m; m &= m - 1) sum += __shfl_sync(grp, v, __ffs(m) - 1);
+                                         if (ln == __ffs(grp) - 1 && !Val<T>::acc_shared(vals + (r - lo), sum, T(1)))
+                                           raise_err(a.err, kErrRetry);
+                                         return;
+                                       }
+                                     }
                                      if (!Val<T>::acc_shared(vals + (r - lo), av, bv)) raise_err(a.err, kErrRetry);
                                    }
                                  });
@@ -501,10 +582,16 @@ __global__ void __launch_bounds__(1024, 1)
         const int r = pre0 + j;
         if (j < total && r >= lo && r < hi) {
           const int col = (w0 + l) * 32 + (int)__fns(bits, 0, j - fl + 1);
-          c_ci[rp + r] = col;
-          c_v[rp + r] = vals[r - lo];
+          if (part == 0) c_ci[rp + r] = col;
+          if (parts == 1) c_v[rp + r] = vals[r - lo];
         }
       }
+    }
+  }
+  if (parts > 1) {
+    for (int r = threadIdx.x; r < hi - lo; r += blockDim.x) {
+      const T v = vals[r];
+      if (v != T(0)) Val<T>::add_global(c_v + rp + lo + r, v);
     }
   }
   if (threadIdx.x == 0 && tot != nnz) raise_err(a.err, kErrProbe);
@@ -664,7 +751,17 @@ cudaError_t launch_numeric_t(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_c
   static const int order[kNumNumBins] = {kNumBitmapBin, kNumBitmapMBin, kNumBitmapSBin, kNumGlobalBin, 8, 7, 6, 5,
                                          4, 3, 2, 1, 0};
   const bool concurrent = !(p->flags & SPGEMM_SERIAL);
-  cudaError_t e = concurrent ? fork(p) : cudaSuccess;
+  cudaError_t e = cudaSuccess;
+  const int64_t nbm = p->sym_count[kSymBitmapBin] + p->sym_count[kSymBitmapMidBin];
+  if (nbm > 0 && p->bm_item_off[3] > 0) {
+    // before the fork: every bitmap launch adds into the zeroed split rows
+    KernelScope ks(p, "bm_zero_split");
+    const int64_t grid = nbm < 4 * 152 ? nbm : 4 * 152;
+    k_bm_zero_split<T><<<(unsigned)grid, 256, 0, p->stream>>>(p->perm + p->sym_off[kSymBitmapBin], nbm, p->flop,
+                                                              c_rp, c_v);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && concurrent) e = fork(p);
   int launched = 0;
   for (int o = 0; o < kNumNumBins && e == cudaSuccess; ++o) {
     const int b = order[o];
@@ -693,7 +790,7 @@ cudaError_t launch_numeric_t(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_c
         {
           KernelScope ks(p, cls == 0 ? "num_bitmap_s" : cls == 1 ? "num_bitmap_m" : "num_bitmap_l", st);
           k_num_bitmap<T><<<(unsigned)n, p->bm_threads[cls], smem, st>>>(
-              a, p->perm + p->sym_off[kSymBitmapBin], p->bm_items + p->bm_item_off[cls], p->bitmaps, p->bm_words,
+              a, p->perm + p->sym_off[kSymBitmapBin], p->bm_items + p->bm_item_off[cls], p->flop, p->bitmaps, p->bm_words,
               (int)p->bm_cap[cls], c_rp, c_ci, c_v);
         }
         e = cudaGetLastError();

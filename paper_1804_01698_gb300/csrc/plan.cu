@@ -294,6 +294,7 @@ __global__ void __launch_bounds__(256)
     long long w;
     const int c = bm_class(nnz_row[i], caps, &w);
     if (w > 0) {
+      w *= bm_split_parts(flop[i], nnz_row[i]);
       atomicAdd(&s_items[c], (unsigned long long)w);
       atomicAdd(&s_flop[c], (unsigned long long)flop[i]);
     }
@@ -306,15 +307,18 @@ __global__ void __launch_bounds__(256)
 }
 
 __global__ void __launch_bounds__(256)
-    k_bm_items_fill(const int32_t *__restrict__ rows, int64_t n, const int32_t *__restrict__ nnz_row, BmCaps caps,
-                    DevCounters *dc, int2 *__restrict__ items) {
+    k_bm_items_fill(const int32_t *__restrict__ rows, int64_t n, const int32_t *__restrict__ nnz_row,
+                    const int64_t *__restrict__ flop, BmCaps caps, DevCounters *dc, int4 *__restrict__ items) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
+  const int32_t i = rows[t];
   long long w;
-  const int c = bm_class(nnz_row[rows[t]], caps, &w);
+  const int c = bm_class(nnz_row[i], caps, &w);
   if (w == 0) return;
-  const unsigned long long base = caps.off[c] + atomicAdd(&dc->bm_cursor[c], (unsigned long long)w);
-  for (int q = 0; q < (int)w; ++q) items[base + q] = make_int2((int)t, q);
+  const int parts = bm_split_parts(flop[i], nnz_row[i]);
+  const unsigned long long base = caps.off[c] + atomicAdd(&dc->bm_cursor[c], (unsigned long long)(w * parts));
+  for (int q = 0; q < (int)w; ++q)
+    for (int pt = 0; pt < parts; ++pt) items[base + (unsigned long long)q * parts + pt] = make_int4((int)t, q, pt, parts);
 }
 
 // ---------------------------------------------------------------------------
@@ -738,7 +742,7 @@ int spgemm_symbolic(spgemm_plan_t p, int32_t *c_row_ptr, int64_t *nnz_c) {
     p->num_count[b] = (int64_t)p->hc->num_count[b];
     p->num_off[b + 1] = p->num_off[b] + p->num_count[b];
   }
-  // the bitmap bins hold work items (row, rank window), not rows of perm2
+  // the bitmap bins hold work items (row, rank window, part), not rows of perm2
   const int bm_bins[3] = {kNumBitmapSBin, kNumBitmapMBin, kNumBitmapBin};
   p->bm_item_off[0] = 0;
   for (int c = 0; c < 3; ++c) {
@@ -763,7 +767,7 @@ int spgemm_numeric(spgemm_plan_t p, const int32_t *c_row_ptr, int32_t *c_col_idx
   if (p->nnz_c > 0) {
     const int64_t nitems = p->bm_item_off[3];
     if (nitems > 0) {
-      p->bm_items_bytes = (size_t)nitems * sizeof(int2);
+      p->bm_items_bytes = (size_t)nitems * sizeof(int4);
       e = cudaMallocAsync((void **)&p->bm_items, p->bm_items_bytes, p->stream);
       if (e != cudaSuccess) {
         p->bm_items = nullptr;
@@ -773,7 +777,7 @@ int spgemm_numeric(spgemm_plan_t p, const int32_t *c_row_ptr, int32_t *c_col_idx
       KernelScope ks(p, "bm_items_fill");
       BmCaps caps{{p->bm_cap[0], p->bm_cap[1], p->bm_cap[2]}, {p->bm_item_off[0], p->bm_item_off[1], p->bm_item_off[2]}};
       k_bm_items_fill<<<(unsigned)((nbm + 255) / 256), 256, 0, p->stream>>>(
-          p->perm + p->sym_off[kSymBitmapBin], nbm, p->nnz_row, caps, p->dc, p->bm_items);
+          p->perm + p->sym_off[kSymBitmapBin], nbm, p->nnz_row, p->flop, caps, p->dc, p->bm_items);
     }
     if (p->num_count[kNumGlobalBin] > 0) {
       const int64_t slots = pow2_above((int64_t)p->hc->max_nnz_global * 4 / 3);

@@ -352,3 +352,29 @@ def test_warp_rows_sorted_by_bucket_rank_and_by_the_fallback(far):
         C, stats = gpu_product(a, b, dt, True)
         assert stats["status"] == 0
         assert_matches_oracle(C, a, b, True)
+
+
+@pytest.mark.parametrize("sorted_output", [True, False])
+@pytest.mark.parametrize("dt", ["f64", "i64", "f32"])
+def test_heavy_bitmap_row_split_over_blocks(dt, sorted_output):
+    """A row whose flop dwarfs its output (600,000 products onto at most
+    5,000 columns) is split over several blocks by ranges of its stored
+    a_ik; their partial sums meet in C through global atomics.  Lighter
+    bitmap rows beside it stay whole."""
+    rng = np.random.default_rng(31)
+    kb, nb = 5000, 20000
+    B = inputs.er_exact(nb, 30, seed=32, ncols=kb)
+    rows = [np.full(nb, 0)] + [np.full(50 * r, r) for r in range(1, 8)]
+    cols = [np.arange(nb)] + [rng.choice(nb, size=50 * r, replace=False) for r in range(1, 8)]
+    rp, ci = inputs.from_coo(8, nb, np.concatenate(rows), np.concatenate(cols))
+    A = CSR(8, nb, rp, ci, rng.uniform(-1, 1, len(ci)))
+    if dt != "f64":   # small integers: exact in int64 and float32
+        A = A.with_vals(rng.integers(-2, 3, A.nnz).astype(np.float64))
+        B = B.with_vals(rng.integers(-2, 3, B.nnz).astype(np.float64))
+        if dt == "i64":
+            A, B = A.astype(np.int64), B.astype(np.int64)
+    C, stats = gpu_product(A, B, DT[dt], sorted_output)
+    assert stats["status"] == 0
+    assert stats["max_row_flop"] == 600000
+    assert sum(stats["num_bin_rows"][b] for b in (9, 11, 12)) > 7   # items: the split row counts its parts
+    assert_matches_oracle(C, A, B, sorted_output)
