@@ -17,7 +17,8 @@ Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
 Workloads: the named single products of inputs.WORKLOADS (default
 rmat16_ef16_f64; also er4096_k8_f64, rmat18_frontier1024_f32,
 tc_rmat16_lu_f64), batch_er2000 (batched products), serve_mix (serving
-loop) and sweep_rmat (density and size sweeps).
+loop), sweep_rmat (density and size sweeps) and ablate_probe (linear vs
+chunked hash probing).
 For N > 1 launch under torch.distributed.run: each rank runs an
 independent replica on its own GPU (weak scaling); timing takes the maximum
 over ranks.
@@ -481,6 +482,137 @@ def run_sweep(args) -> int:
     return 0
 
 
+def collision_factor(A, B, row_nnz, rows, chunk: bool) -> float:
+    """Probes per insertion (the collision factor c of Eq. 2) of the numeric
+    hash tables, simulated sequentially on the given rows: each row's table
+    has the size its bin gives it (warp tables of S = 64..1024 slots hold
+    up to S/2 keys, block tables of 2048..16384 slots up to 3S/4), keys
+    arrive in product order, slot = (col * 2654435761) mod S.  Linear
+    probing reads one slot per probe; chunked probing reads 4 (one probe)."""
+    caps = [(s, s // 2) for s in (64, 128, 256, 512, 1024)] + [(s, 3 * s // 4) for s in (2048, 4096, 8192, 16384)]
+    probes = inserts = 0
+    for i in rows:
+        nnz = int(row_nnz[i])
+        size = next((s for s, c in caps if nnz <= c), None)
+        if size is None or nnz == 0:
+            continue
+        mask = size - 1
+        tab = [-1] * size
+        for j in range(A.row_ptr[i], A.row_ptr[i + 1]):
+            k = A.col_idx[j]
+            for q in range(B.row_ptr[k], B.row_ptr[k + 1]):
+                col = int(B.col_idx[q])
+                h = (col * 2654435761) & 0xFFFFFFFF & mask
+                inserts += 1
+                if chunk:
+                    h &= ~3
+                    while True:
+                        probes += 1
+                        chunk4 = tab[h:h + 4]
+                        if col in chunk4:
+                            break
+                        if -1 in chunk4:
+                            tab[h + chunk4.index(-1)] = col
+                            break
+                        h = (h + 4) & mask
+                else:
+                    while True:
+                        probes += 1
+                        if tab[h] == col:
+                            break
+                        if tab[h] == -1:
+                            tab[h] = col
+                            break
+                        h = (h + 1) & mask
+    return probes / inserts if inserts else float("nan")
+
+
+def run_ablate_probe(args) -> int:
+    """Ablation of the hash probing of Sec. 4.2.1 (one slot per probe) against
+    the chunked probing of HashVector, Sec. 4.2.2 (4 slots per 16-byte load,
+    SPGEMM_PROBE_CHUNK4): whole products (concurrent bins, L2 flushed) and
+    the hash-table kernels alone (bins serialised, an event pair per
+    kernel), plus the collision factor c of Eq. 2 of each scheme."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1804_01698_gb300 import binding as sg
+    from paper_1804_01698_gb300 import inputs
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    er16 = inputs.rmat(16, 16, abcd=(0.25, 0.25, 0.25, 0.25), seed=inputs.SEED_BASE + 8)
+    cases = [("rmat16_ef16_f64", *inputs.workload("rmat16_ef16_f64")[:2]), ("er_rmat16_ef16_f64", er16, er16),
+             ("tc_rmat16_lu_f64", *inputs.workload("tc_rmat16_lu_f64")[:2])]
+    steps = max(1, min(args.steps, 10))
+    rows_out, launches = [], 0
+    rng = np.random.default_rng(5)
+    with ClockSampler(0) as clocks:
+        for name, A, B in cases:
+            dA = sg.to_device(A, dev)
+            dB = dA if B is A else sg.to_device(B, dev)
+            row = {"workload": name, "flop": None}
+            for probe in ("linear", "chunk4"):
+                for timing in (False, True):
+                    ts, kt = [], {}
+                    for it in range(steps + 1):
+                        flush.fill_(it & 0xFF)
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        plan = sg.Plan(dA, dB, True, stream=stream, timing=timing, serial=timing, probe=probe)
+                        plan.symbolic()
+                        C = plan.numeric()
+                        e1.record(stream)
+                        e1.synchronize()
+                        st = plan.stats()
+                        if st["status"] != 0:
+                            raise RuntimeError(f"device error status {st['status']}")
+                        if it > 0:
+                            ts.append(e0.elapsed_time(e1))
+                            launches += st["kernel_launches"]
+                            if timing:
+                                for k, (ms, _) in plan.kernel_times().items():
+                                    kt[k] = kt.get(k, 0.0) + ms / steps
+                        if probe == "linear" and not timing and it == 0:
+                            row_nnz = plan.row_nnz().cpu().numpy()
+                        plan.destroy()
+                        del C
+                    if timing:
+                        hash_ms = sum(v for k, v in kt.items() if k.startswith(("sym_warp", "sym_block", "num_warp",
+                                                                                   "num_block", "sym_global",
+                                                                                   "num_global")))
+                        row[probe + "_hash_kernels_ms"] = hash_ms
+                    else:
+                        row[probe + "_step_ms"] = statistics.median(ts)
+                row["flop"] = st["total_flop"]
+            hash_rows = np.nonzero((row_nnz > 0) & (row_nnz <= 12288))[0]
+            sample = rng.choice(hash_rows, size=min(300, len(hash_rows)), replace=False) if len(hash_rows) else []
+            row["c_linear"] = collision_factor(A, B, row_nnz, sample, False)
+            row["c_chunk4"] = collision_factor(A, B, row_nnz, sample, True)
+            row["c_sample_rows"] = len(sample)
+            rows_out.append(row)
+            print(json.dumps(row), file=sys.stderr, flush=True)
+            del dA, dB
+    head = rows_out[0]
+    line = {
+        "metric": "SpGEMM GFLOP/s (2*flop per second)", "value": 2 * head["flop"] / (head["linear_step_ms"] * 1e-3) / 1e9,
+        "unit": "GFLOP/s", "n_gpus": 1, "steps": steps, "warmup": 1, "ms_per_step": head["linear_step_ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "probing ablation: linear (Sec. 4.2.1) vs 4-slot chunks (Sec. 4.2.2) on R-MAT16 A*A, "
+                               "ER (R-MAT .25) scale 16 EF 16 A*A and triangle L*U of R-MAT16; FP64, sorted",
+                   "l2": "256 MiB flush between steps", "timing": "median over steps"},
+        "ablation": rows_out,
+        "e2e": None,
+        "gpu_launches": launches,
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------------------- GPU arm
 
 def main() -> int:
@@ -493,6 +625,8 @@ def main() -> int:
         return run_serve(args)
     if args.workload == "sweep_rmat":
         return run_sweep(args)
+    if args.workload == "ablate_probe":
+        return run_ablate_probe(args)
 
     import torch
     import torch.distributed as dist

@@ -87,6 +87,12 @@ typedef enum { SPGEMM_I64 = 0, SPGEMM_F32 = 1, SPGEMM_F64 = 2 } spgemm_dtype;
 #define SPGEMM_TIMING 4u   /* record CUDA events around every kernel (spgemm_plan_kernel_times) */
 #define SPGEMM_SERIAL 8u   /* run the bins of a phase one after another on the plan's stream
                               (default: concurrently on side streams joined back to it) */
+#define SPGEMM_PROBE_CHUNK4 16u /* hash tables probed 4 slots at a time: one 16-byte load reads the
+                                   chunk holding the key's slot, a key is claimed in the chunk's first
+                                   empty slot and the next chunk is tried only when this one is full
+                                   (the GPU form of HashVector's chunked probing, Sec. 4.2.2); the
+                                   default is one slot at a time (linear probing, Sec. 4.2.1).  The
+                                   result is the same either way. */
 
 /* A CSR operand (device pointers). */
 typedef struct {

@@ -26,6 +26,8 @@ _LIB = None
 
 SPGEMM_I64, SPGEMM_F32, SPGEMM_F64 = 0, 1, 2
 SPGEMM_UNSORTED, SPGEMM_SORTED, SPGEMM_VALIDATE, SPGEMM_TIMING, SPGEMM_SERIAL = 0, 1, 2, 4, 8
+SPGEMM_PROBE_CHUNK4 = 16
+_PROBES = {"linear": 0, "chunk4": SPGEMM_PROBE_CHUNK4}
 MAX_BINS = 24
 
 _DTYPES = {torch.int64: SPGEMM_I64, torch.float32: SPGEMM_F32, torch.float64: SPGEMM_F64}
@@ -164,7 +166,7 @@ class Plan:
     """A plan for C = A*B; methods mirror spgemm_symbolic / spgemm_numeric."""
 
     def __init__(self, A: DeviceCSR, B: DeviceCSR, sorted_output: bool = True, stream=None, timing: bool = False,
-                 serial: bool = False):
+                 serial: bool = False, probe: str = "linear"):
         self.lib = library()
         if A.vals.dtype != B.vals.dtype or A.vals.dtype not in _DTYPES:
             raise TypeError("A and B must share a value dtype among int64, float32, float64")
@@ -173,7 +175,7 @@ class Plan:
         self.device = A.row_ptr.device
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         flags = (SPGEMM_SORTED if sorted_output else SPGEMM_UNSORTED) | (SPGEMM_TIMING if timing else 0) | \
-            (SPGEMM_SERIAL if serial else 0)
+            (SPGEMM_SERIAL if serial else 0) | _PROBES[probe]
         self._a, self._b = A.desc(), B.desc()
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
@@ -360,7 +362,8 @@ class Batch:
     """Independent products C_p = A_p * B_p run as one plan (block-diagonal
     packing on the device); mirrors spgemm_batch_create / _symbolic / _numeric."""
 
-    def __init__(self, As, Bs, sorted_output: bool = True, stream=None, timing: bool = False, serial: bool = False):
+    def __init__(self, As, Bs, sorted_output: bool = True, stream=None, timing: bool = False, serial: bool = False,
+                 probe: str = "linear"):
         self.lib = library()
         if len(As) != len(Bs) or not As:
             raise ValueError("need the same positive number of A and B operands")
@@ -371,7 +374,7 @@ class Batch:
         self.device = As[0].row_ptr.device
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         flags = (SPGEMM_SORTED if sorted_output else SPGEMM_UNSORTED) | (SPGEMM_TIMING if timing else 0) | \
-            (SPGEMM_SERIAL if serial else 0)
+            (SPGEMM_SERIAL if serial else 0) | _PROBES[probe]
         n = len(As)
         self._a = (CsrDesc * n)(*[m.desc() for m in As])
         self._b = (CsrDesc * n)(*[m.desc() for m in Bs])

@@ -41,6 +41,63 @@ constexpr int kMaxCasRetries = 1 << 20;
 // compare-and-swap loop, because GB300's FP64 pipe is the scarce resource
 // and a separate multiply plus the hardware's own CAS-loop add would cost
 // two FP64 operations per product.
+// Four consecutive keys of a table, slot h a multiple of 4 (16-byte
+// aligned), read fresh: a volatile shared load, or an L2 load for tables in
+// global memory (other lanes claim slots with atomics, which L1 does not see).
+template <bool GLOBAL_MEM>
+__device__ __forceinline__ int4 load_chunk(const int32_t *tab, uint32_t h) {
+  if (GLOBAL_MEM) return __ldcg(reinterpret_cast<const int4 *>(tab + h));
+  int4 k;
+  const unsigned addr = (unsigned)__cvta_generic_to_shared(tab + h);
+  asm volatile("ld.volatile.shared.v4.s32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(k.x), "=r"(k.y), "=r"(k.z), "=r"(k.w)
+               : "r"(addr));
+  return k;
+}
+
+// Chunked probing (the GPU form of HashVector, Sec. 4.2.2): the table is
+// read 4 slots at a time from the chunk holding the key's hash slot, and a
+// key is claimed in the first empty slot of its chunk, moving to the next
+// chunk only when this one is full.  Slots are claimed in order within a
+// chunk and never freed, so a key is absent from the table when its chunk
+// has an empty slot and no match.  Returns the key's slot and sets *fresh
+// when this call claimed it; -1 after a failed bound (err raised).
+template <bool GLOBAL_MEM>
+__device__ __forceinline__ int chunk_find_or_claim(int32_t *tab, uint32_t mask, int32_t c, bool *fresh,
+                                                   uint32_t *err) {
+  uint32_t h = hash_slot(c, mask) & ~3u;
+  int retries = 0;
+  for (uint32_t chunk = 0; chunk <= (mask >> 2);) {
+    const int4 k4 = load_chunk<GLOBAL_MEM>(tab, h);
+    const int32_t kk[4] = {k4.x, k4.y, k4.z, k4.w};
+    int e = -1;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (e < 0 && kk[j] == c) {
+        *fresh = false;
+        return (int)(h + j);
+      }
+      if (e < 0 && kk[j] == kEmpty) e = j;
+    }
+    if (e < 0) {
+      h = (h + 4) & mask;
+      ++chunk;
+      continue;
+    }
+    const int32_t old = atomicCAS(tab + h + e, kEmpty, c);
+    if (old == kEmpty || old == c) {
+      *fresh = old == kEmpty;
+      return (int)(h + e);
+    }
+    if (++retries > kMaxCasRetries) {
+      raise_err(err, kErrRetry);
+      return -1;
+    }
+  }
+  raise_err(err, kErrProbe);
+  return -1;
+}
+
 template <typename T> struct Val;
 
 template <> struct Val<double> {

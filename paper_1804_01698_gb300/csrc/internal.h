@@ -113,6 +113,7 @@ struct Args {
   const void *av, *bv;
   int G;  // lanes per stored a_ik
   uint32_t *err;
+  int probe = 0;  // hash probing: 0 linear, 1 chunks of 4 slots (SPGEMM_PROBE_CHUNK4)
 };
 
 }  // namespace sg

@@ -29,7 +29,18 @@ constexpr int kUN = 4;  // B entries (column + value) loaded ahead per lane
 // Finds or claims the slot of key c and accumulates a*b there.
 template <typename T, bool GLOBAL_MEM>
 __device__ __forceinline__ void insert_acc(int32_t *keys, T *vals, uint32_t mask, int32_t c, T a, T b,
-                                           uint32_t *err) {
+                                           uint32_t *err, int probe) {
+  if (probe) {
+    bool fresh = false;
+    const int h = chunk_find_or_claim<GLOBAL_MEM>(keys, mask, c, &fresh, err);
+    if (h < 0) return;
+    if (GLOBAL_MEM) {
+      Val<T>::acc_global(vals + h, a, b);
+    } else if (!Val<T>::acc_shared(vals + h, a, b)) {
+      raise_err(err, kErrRetry);
+    }
+    return;
+  }
   uint32_t h = hash_slot(c, mask);
   for (uint32_t probe = 0; probe <= mask; ++probe) {
     const int32_t old = atomicCAS(keys + h, kEmpty, c);
@@ -248,7 +259,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 8)
   const int G = a.G;
   warp_row_products<kUN, true, T>(a.arp[i], a.arp[i + 1], G, a.aci, (const T *)a.av, a.brp, a.bci, (const T *)a.bv,
                                   (int32_t)a.k, a.err, Stage<T>{s_ent[warp], &s_next[warp], nullptr},
-                                 [&](int32_t c, T av, T bv) { insert_acc<T, false>(keys, vals, S - 1, c, av, bv, a.err); });
+                                 [&](int32_t c, T av, T bv) { insert_acc<T, false>(keys, vals, S - 1, c, av, bv, a.err, a.probe); });
   __syncwarp();
   const int32_t rp = c_rp[i];
   const int32_t nnz = c_rp[i + 1] - rp;
@@ -333,7 +344,7 @@ __global__ void __launch_bounds__(1024, 1)
   const int G = a.G;
   block_row_products<kUN, true, T>(a.arp[i], a.arp[i + 1], G, a.aci, (const T *)a.av, a.brp, a.bci,
                                    (const T *)a.bv, (int32_t)a.k, a.err, Stage<T>{s_ent, &s_next, s_wsum},
-                                 [&](int32_t c, T av, T bv) { insert_acc<T, false>(keys, vals, S - 1, c, av, bv, a.err); });
+                                 [&](int32_t c, T av, T bv) { insert_acc<T, false>(keys, vals, S - 1, c, av, bv, a.err, a.probe); });
   __syncthreads();
   const int32_t rp = c_rp[i];
   const int32_t nnz = c_rp[i + 1] - rp;
@@ -627,7 +638,7 @@ __global__ void __launch_bounds__(1024, 1)
     const int32_t i = rows[r];
     block_row_products<kUN, true, T>(a.arp[i], a.arp[i + 1], G, a.aci, (const T *)a.av, a.brp, a.bci,
                                    (const T *)a.bv, (int32_t)a.k, a.err, Stage<T>{s_ent, &s_next, s_wsum},
-                                   [&](int32_t c, T av, T bv) { insert_acc<T, true>(keys, vals, mask, c, av, bv, a.err); });
+                                   [&](int32_t c, T av, T bv) { insert_acc<T, true>(keys, vals, mask, c, av, bv, a.err, a.probe); });
     __syncthreads();
     const int32_t rp = c_rp[i];
     const int32_t nnz = c_rp[i + 1] - rp;
@@ -746,7 +757,8 @@ static cudaError_t num_block(spgemm_plan_s *p, cudaStream_t st, const Args &a, c
 
 template <typename T>
 cudaError_t launch_numeric_t(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_ci, T *c_v) {
-  Args a{p->m, p->n, p->k, p->arp, p->aci, p->brp, p->bci, p->av, p->bv, p->G, &p->dc->err};
+  Args a{p->m, p->n, p->k, p->arp, p->aci, p->brp, p->bci, p->av, p->bv, p->G, &p->dc->err,
+         (p->flags & SPGEMM_PROBE_CHUNK4) ? 1 : 0};
   // heavy bins first, each bin on the next side stream
   static const int order[kNumNumBins] = {kNumBitmapBin, kNumBitmapMBin, kNumBitmapSBin, kNumGlobalBin, 8, 7, 6, 5,
                                          4, 3, 2, 1, 0};

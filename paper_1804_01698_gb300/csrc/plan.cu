@@ -552,7 +552,8 @@ int spgemm_plan_create(spgemm_plan_t *out, const spgemm_csr *A, const spgemm_csr
   g_last_error.clear();
   if (!valid_csr_desc(A) || !valid_csr_desc(B) || A->ncols != B->nrows) return SPGEMM_ERR_INVALID_ARGUMENT;
   if (dtype != SPGEMM_I64 && dtype != SPGEMM_F32 && dtype != SPGEMM_F64) return SPGEMM_ERR_INVALID_ARGUMENT;
-  if (flags & ~(SPGEMM_SORTED | SPGEMM_VALIDATE | SPGEMM_TIMING | SPGEMM_SERIAL)) return SPGEMM_ERR_INVALID_ARGUMENT;
+  if (flags & ~(SPGEMM_SORTED | SPGEMM_VALIDATE | SPGEMM_TIMING | SPGEMM_SERIAL | SPGEMM_PROBE_CHUNK4))
+    return SPGEMM_ERR_INVALID_ARGUMENT;
 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -668,7 +669,9 @@ int spgemm_plan_create(spgemm_plan_t *out, const spgemm_csr *A, const spgemm_csr
       }
     }
     if (rc == SPGEMM_OK && p->sym_count[kSymGlobalBin] > 0)
-      rc = alloc_gtab(p, pow2_above((int64_t)p->hc->max_bound_global), 4, p->sym_count[kSymGlobalBin]);
+      // at least 64 slots: chunked probing reads 4 at a time
+      rc = alloc_gtab(p, std::max<int64_t>(64, pow2_above((int64_t)p->hc->max_bound_global)), 4,
+                      p->sym_count[kSymGlobalBin]);
     if (rc == SPGEMM_OK && m > 0) {
       Offsets o{};
       for (int b = 0; b < kNumSymBins; ++b) o.v[b] = p->sym_off[b];
@@ -780,7 +783,7 @@ int spgemm_numeric(spgemm_plan_t p, const int32_t *c_row_ptr, int32_t *c_col_idx
           p->perm + p->sym_off[kSymBitmapBin], nbm, p->nnz_row, p->flop, caps, p->dc, p->bm_items);
     }
     if (p->num_count[kNumGlobalBin] > 0) {
-      const int64_t slots = pow2_above((int64_t)p->hc->max_nnz_global * 4 / 3);
+      const int64_t slots = std::max<int64_t>(64, pow2_above((int64_t)p->hc->max_nnz_global * 4 / 3));
       rc = alloc_gtab(p, slots, 4 + value_size(p->dtype), p->num_count[kNumGlobalBin]);
       if (rc != SPGEMM_OK) return rc;
     }

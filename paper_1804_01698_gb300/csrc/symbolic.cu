@@ -9,8 +9,9 @@
 //                    the hash table lives in global memory (L2)
 //
 // Keys are inserted with atomicCAS on the int32 key (empty = -1) and
-// linear probing (Sec. 4.2.1); an insert that finds -1 claims the slot and
-// counts one new column.
+// linear probing (Sec. 4.2.1), or by chunks of 4 slots under
+// SPGEMM_PROBE_CHUNK4 (Sec. 4.2.2); an insert that finds -1 claims the slot
+// and counts one new column.
 #include <algorithm>
 #include <string>
 
@@ -23,7 +24,12 @@ constexpr int kU = 4;  // B entries loaded ahead per lane
 
 // Inserts key c into an S-slot table; returns 1 when c was new.
 template <bool GLOBAL_MEM>
-__device__ __forceinline__ int insert_key(int32_t *tab, uint32_t mask, int32_t c, uint32_t *err) {
+__device__ __forceinline__ int insert_key(int32_t *tab, uint32_t mask, int32_t c, uint32_t *err, int probe) {
+  if (probe) {
+    bool fresh = false;
+    chunk_find_or_claim<GLOBAL_MEM>(tab, mask, c, &fresh, err);
+    return fresh ? 1 : 0;
+  }
   uint32_t h = hash_slot(c, mask);
   for (uint32_t probe = 0; probe <= mask; ++probe) {
     const int32_t old = atomicCAS(tab + h, kEmpty, c);
@@ -53,7 +59,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 8)
   Stage<int32_t> st{s_ent[warp], &s_next[warp], nullptr};
   warp_row_products<kU, false, int32_t>(a.arp[i], a.arp[i + 1], G, a.aci, (const int32_t *)nullptr, a.brp, a.bci,
                                         (const int32_t *)nullptr, (int32_t)a.k, a.err, st,
-                                        [&](int32_t c, int32_t, int32_t) { cnt += insert_key<false>(tab, S - 1, c, a.err); });
+                                        [&](int32_t c, int32_t, int32_t) { cnt += insert_key<false>(tab, S - 1, c, a.err, a.probe); });
   cnt = warp_sum(cnt);
   if (lane == 0) nnz_row[i] = cnt;
 }
@@ -75,7 +81,7 @@ __global__ void __launch_bounds__(1024, 1)
   block_row_products<kU, false, int32_t>(a.arp[i], a.arp[i + 1], G, a.aci, (const int32_t *)nullptr,
                                          a.brp, a.bci, (const int32_t *)nullptr, (int32_t)a.k, a.err,
                                          Stage<int32_t>{s_ent, &s_next, s_wsum},
-                                       [&](int32_t c, int32_t, int32_t) { cnt += insert_key<false>(tab, S - 1, c, a.err); });
+                                       [&](int32_t c, int32_t, int32_t) { cnt += insert_key<false>(tab, S - 1, c, a.err, a.probe); });
   cnt = block_sum(cnt, red);
   if (threadIdx.x == 0) nnz_row[i] = cnt;
 }
@@ -129,7 +135,7 @@ __global__ void __launch_bounds__(1024, 1)
     block_row_products<kU, false, int32_t>(a.arp[i], a.arp[i + 1], G, a.aci, (const int32_t *)nullptr,
                                          a.brp, a.bci, (const int32_t *)nullptr, (int32_t)a.k, a.err,
                                          Stage<int32_t>{s_ent, &s_next, s_wsum},
-                                         [&](int32_t c, int32_t, int32_t) { cnt += insert_key<true>(tab, mask, c, a.err); });
+                                         [&](int32_t c, int32_t, int32_t) { cnt += insert_key<true>(tab, mask, c, a.err, a.probe); });
     cnt = block_sum(cnt, red);
     if (threadIdx.x == 0) nnz_row[i] = cnt;
   }
@@ -170,7 +176,8 @@ static cudaError_t sym_block(spgemm_plan_s *p, cudaStream_t st, const Args &a, c
 }
 
 cudaError_t launch_symbolic(spgemm_plan_s *p) {
-  Args a{p->m, p->n, p->k, p->arp, p->aci, p->brp, p->bci, p->av, p->bv, p->G, &p->dc->err};
+  Args a{p->m, p->n, p->k, p->arp, p->aci, p->brp, p->bci, p->av, p->bv, p->G, &p->dc->err,
+         (p->flags & SPGEMM_PROBE_CHUNK4) ? 1 : 0};
   // heavy bins first, each bin on the next side stream
   static const int order[kNumSymBins] = {kSymBitmapBin, kSymBitmapMidBin, kSymGlobalBin, 9, 8, 7, 6, 5, 4, 3, 2, 1, 0};
   const bool concurrent = !(p->flags & SPGEMM_SERIAL);

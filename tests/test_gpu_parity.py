@@ -378,3 +378,28 @@ def test_heavy_bitmap_row_split_over_blocks(dt, sorted_output):
     assert stats["max_row_flop"] == 600000
     assert sum(stats["num_bin_rows"][b] for b in (9, 11, 12)) > 7   # items: the split row counts its parts
     assert_matches_oracle(C, A, B, sorted_output)
+
+
+@pytest.mark.parametrize("sorted_output", [True, False])
+@pytest.mark.parametrize("dt", ["f64", "i64"])
+@pytest.mark.parametrize("shape", ["rmat12", "er", "global"])
+def test_chunked_probing_gives_the_same_product(shape, dt, sorted_output):
+    """SPGEMM_PROBE_CHUNK4 (4-slot chunks, Sec. 4.2.2) in every kind of hash
+    table: warp and block tables in shared memory (R-MAT, ER) and global
+    tables (B with 2^20 columns)."""
+    dtype = DT[dt]
+    if shape == "rmat12":
+        A = B = inputs.rmat(12, 16, seed=81)
+    elif shape == "er":
+        A = inputs.er_exact(3000, 11, seed=82, ncols=5000)
+        B = inputs.er_exact(5000, 7, seed=83, ncols=777)
+    else:
+        A, B = _heavy_rows(5, 40, 1 << 20, 1000, seed=84)
+    if dt != "f64":
+        A, B = int_valued(A, 85), int_valued(B, 86)
+    A, B = host_vals(A, dtype), host_vals(B, dtype)
+    C, st = gpu_product(A, B, dtype, sorted_output, probe="chunk4")
+    assert st["status"] == 0
+    if shape == "global":
+        assert st["sym_bin_rows"][12] == 5 and st["num_bin_rows"][10] >= 5
+    assert_matches_oracle(C, A, B, sorted_output)
