@@ -322,8 +322,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 8)
 
 // sort_mode: 0 unsorted, 1 bitonic sort of the table, 2 rank by column
 // bitmap (needs 2 * words * 4 bytes more shared memory).
+// Threads of the block bins (as kNumBins) and the blocks per SM their shared
+// memory allows (table, sort window and staging): the register budget is
+// set so that the registers do not cap the blocks per SM below that.
+template <int S> constexpr int num_block_threads() { return S <= 2048 ? 256 : S <= 4096 ? 512 : 1024; }
+template <int S> constexpr int num_block_min_blocks() { return S <= 2048 ? 5 : S <= 4096 ? 3 : 1; }
+
 template <typename T, int S>
-__global__ void __launch_bounds__(1024, 1)
+__global__ void __launch_bounds__(num_block_threads<S>(), num_block_min_blocks<S>())
     k_num_block(Args a, const int32_t *__restrict__ rows, const int32_t *__restrict__ c_rp,
                 int32_t *__restrict__ c_ci, T *__restrict__ c_v, int sort_mode, int words) {
   extern __shared__ __align__(16) unsigned char sm_num_block[];
@@ -471,16 +477,17 @@ __device__ __forceinline__ void part_range(const Args &a, int32_t i, int part, i
 }
 
 // Values of the split bitmap rows start at zero: their parts add into them.
+// One warp per bitmap row.
 template <typename T>
 __global__ void __launch_bounds__(256)
     k_bm_zero_split(const int32_t *__restrict__ bm_rows, int64_t nbm, const int64_t *__restrict__ flop,
                     const int32_t *__restrict__ c_rp, T *__restrict__ c_v) {
-  for (int64_t t = blockIdx.x; t < nbm; t += gridDim.x) {
-    const int32_t i = bm_rows[t];
-    const int32_t rp = c_rp[i], nnz = c_rp[i + 1] - rp;
-    if (bm_split_parts(flop[i], nnz) < 2) continue;
-    for (int32_t r = threadIdx.x; r < nnz; r += blockDim.x) c_v[rp + r] = T(0);
-  }
+  const int64_t t = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (t >= nbm) return;
+  const int32_t i = bm_rows[t];
+  const int32_t rp = c_rp[i], nnz = c_rp[i + 1] - rp;
+  if (bm_split_parts(flop[i], nnz) < 2) return;
+  for (int32_t r = threadIdx.x & 31; r < nnz; r += 32) c_v[rp + r] = T(0);
 }
 
 // Rows whose flop is at least kAggregateMinRatio times their output size
@@ -498,8 +505,8 @@ constexpr long long kAggregateMinRatio = 32;
 // row's stored a_ik.  A row in one part stores its values; a split row's
 // parts add theirs into C (zeroed by k_bm_zero_split) and part 0 stores
 // the columns.
-template <typename T>
-__global__ void __launch_bounds__(1024, 1)
+template <typename T, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
     k_num_bitmap(Args a, const int32_t *__restrict__ bm_rows, const int4 *__restrict__ items,
                  const int64_t *__restrict__ flop, const uint32_t *__restrict__ bitmaps, int words, int cap,
                  const int32_t *__restrict__ c_rp,
@@ -768,9 +775,8 @@ cudaError_t launch_numeric_t(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_c
   if (nbm > 0 && p->bm_item_off[3] > 0) {
     // before the fork: every bitmap launch adds into the zeroed split rows
     KernelScope ks(p, "bm_zero_split");
-    const int64_t grid = nbm < 4 * 152 ? nbm : 4 * 152;
-    k_bm_zero_split<T><<<(unsigned)grid, 256, 0, p->stream>>>(p->perm + p->sym_off[kSymBitmapBin], nbm, p->flop,
-                                                              c_rp, c_v);
+    k_bm_zero_split<T><<<(unsigned)((nbm + 7) / 8), 256, 0, p->stream>>>(p->perm + p->sym_off[kSymBitmapBin], nbm,
+                                                                         p->flop, c_rp, c_v);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && concurrent) e = fork(p);
@@ -797,11 +803,16 @@ cudaError_t launch_numeric_t(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_c
       case kNumBitmapBin: {
         const int cls = b == kNumBitmapSBin ? 0 : b == kNumBitmapMBin ? 1 : 2;
         const size_t smem = (size_t)p->bm_cap[cls] * sizeof(T) + (size_t)p->bm_words * 8;
-        e = prep_num(k_num_bitmap<T>, smem);
+        // register budgets that let each class keep its shared-memory occupancy:
+        // small 3 x 512 threads per SM (40 registers), medium 2 x 1024 (32),
+        // large 1 x 1024 (64).  Measured: the spills this costs in the small and
+        // medium forms are outweighed by the extra resident warps.
+        auto kern = cls == 0 ? k_num_bitmap<T, 512, 3> : cls == 1 ? k_num_bitmap<T, 1024, 2> : k_num_bitmap<T, 1024, 1>;
+        e = prep_num(kern, smem);
         if (e != cudaSuccess) break;
         {
           KernelScope ks(p, cls == 0 ? "num_bitmap_s" : cls == 1 ? "num_bitmap_m" : "num_bitmap_l", st);
-          k_num_bitmap<T><<<(unsigned)n, p->bm_threads[cls], smem, st>>>(
+          kern<<<(unsigned)n, p->bm_threads[cls], smem, st>>>(
               a, p->perm + p->sym_off[kSymBitmapBin], p->bm_items + p->bm_item_off[cls], p->flop, p->bitmaps, p->bm_words,
               (int)p->bm_cap[cls], c_rp, c_ci, c_v);
         }

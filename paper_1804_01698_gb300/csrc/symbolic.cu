@@ -64,8 +64,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 8)
   if (lane == 0) nnz_row[i] = cnt;
 }
 
+// Threads of the block bins (as kSymBins) and blocks per SM: a key table of
+// S slots leaves room for these, so the register budget is set to match.
+template <int S> constexpr int sym_block_threads() { return S <= 2048 ? 256 : S <= 4096 ? 512 : 1024; }
+template <int S> constexpr int sym_block_min_blocks() { return S <= 2048 ? 8 : S <= 4096 ? 4 : S <= 16384 ? 2 : 1; }
+
 template <int S>
-__global__ void __launch_bounds__(1024, 1)
+__global__ void __launch_bounds__(sym_block_threads<S>(), sym_block_min_blocks<S>())
     k_sym_block(Args a, const int32_t *__restrict__ rows, int32_t *__restrict__ nnz_row) {
   extern __shared__ int32_t sm_sym_block[];
   __shared__ int red[33];
