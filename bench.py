@@ -648,6 +648,7 @@ def main() -> int:
     __graft_entry__.build()
     from paper_1804_01698_gb300 import binding as sg
     from paper_1804_01698_gb300 import inputs
+    from paper_1804_01698_gb300.shard import max_over_ranks
 
     A, B, sorted_default = inputs.workload(args.workload)
     sorted_output = sorted_default and not args.unsorted
@@ -711,11 +712,7 @@ def main() -> int:
     # per-kernel durations: the same K steps again, bins serialised, an event pair per kernel
     ktimes, kt, _, _, _, _ = timed_steps(sorted_output, args.steps, 1, timing=True)
 
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(times), world, dist if world > 1 else None, dev)
     acc = workload_accounting(A, B, nnz_c, vsize)
     flop = acc["flop"]
     ms_per_step = total_ms / args.steps
@@ -801,11 +798,7 @@ def main() -> int:
             e1.synchronize()
             et.append(e0.elapsed_time(e1))
         barrier()
-        ems = sum(et)
-        if world > 1:
-            t = torch.tensor([ems], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = max_over_ranks(sum(et), world, dist if world > 1 else None, dev)
         e2e = {"value": world * args.steps * 2 * flop / (ems * 1e-3) / 1e9, "unit": "GFLOP/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ems / args.steps}
 
