@@ -57,9 +57,9 @@ __device__ __forceinline__ int hash_bin_of(int64_t b) {
   return 9;
 }
 
-__device__ __forceinline__ int sym_bin_of(int64_t b, bool bitmap_ok) {
+__device__ __forceinline__ int sym_bin_of(int64_t b, int64_t bitmap_min) {
   if (b <= 0) return 255;
-  if (bitmap_ok && b > kBitmapMinBound) return b > kBitmapMidMax ? kSymBitmapBin : kSymBitmapMidBin;
+  if (bitmap_min > 0 && b > bitmap_min) return b > kBitmapMidMax ? kSymBitmapBin : kSymBitmapMidBin;
   const int t = hash_bin_of(b);
   if (t < 9) return t;
   if (b <= kBlockSymMax) return 9;
@@ -80,7 +80,7 @@ __device__ __forceinline__ int num_bin_of(int64_t nnz) {
 // independent gathers of B's row_ptr in flight, so a long row of A costs
 // len/128 dependent steps instead of len/8.
 __global__ void __launch_bounds__(256)
-    k_row_flop(Args a, int64_t nnz_a, int64_t nnz_b, int bitmap_ok, int64_t *__restrict__ flop,
+    k_row_flop(Args a, int64_t nnz_a, int64_t nnz_b, int64_t bitmap_min, int64_t *__restrict__ flop,
                uint8_t *__restrict__ rbin, int32_t *__restrict__ nnz_row, DevCounters *dc) {
   __shared__ unsigned int hist[kNumSymBins];
   __shared__ unsigned long long hflop[kNumSymBins];
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(256)
   if (sub == 0 && row < a.m) {
     flop[row] = f;
     const int64_t bound = f < a.k ? f : a.k;
-    const int bin = sym_bin_of(bound, bitmap_ok != 0);
+    const int bin = sym_bin_of(bound, bitmap_min);
     rbin[row] = (uint8_t)bin;
     if (bin == 255) {
       nnz_row[row] = 0;
@@ -639,7 +639,8 @@ int spgemm_plan_create(spgemm_plan_t *out, const spgemm_csr *A, const spgemm_csr
     Args a{p->m, p->n, p->k, p->arp, p->aci, p->brp, p->bci, p->av, p->bv, p->G, &p->dc->err};
     {
       KernelScope ks(p, "row_flop");
-      k_row_flop<<<(unsigned)((m + 7) / 8), 256, 0, p->stream>>>(a, p->nnz_a, p->nnz_b, p->bitmap_ok ? 1 : 0,
+      k_row_flop<<<(unsigned)((m + 7) / 8), 256, 0, p->stream>>>(a, p->nnz_a, p->nnz_b,
+                                                                  p->bitmap_ok ? bitmap_min_bound(p->k) : 0,
                                                                     p->flop, p->rbin, p->nnz_row, p->dc);
     }
     e = cudaGetLastError();

@@ -42,11 +42,11 @@ def host_vals(m: CSR, dtype) -> CSR:
 
 def expected_sym_bin(bound: int, k: int):
     """The documented symbolic bin rule: hash bins by key bound, column bitmaps
-    for rows above 3072 when B has at most 2^18 columns, global tables above
-    the largest shared-memory table otherwise."""
+    for rows above max(512, ceil(k/32)/2) when B has at most 2^18 columns,
+    global tables above the largest shared-memory table otherwise."""
     if bound <= 0:
         return None
-    if k <= 1 << 18 and bound > 3072:
+    if k <= 1 << 18 and bound > max(512, (k + 31) // 32 // 2):
         return 10 if bound > 24576 else 11
     for b, cap in enumerate(HASH_CAPS):
         if bound <= cap:
@@ -123,9 +123,10 @@ def test_rmat16_f64(rmat16, sorted_output):
     assert stats["total_flop"] == GOLDEN["rmat16_ef16_f64"]["total_flop"]
     # every kind of bin takes part: hash bins, both bitmap bins, all three
     # bitmap item classes (small, medium, large)
-    assert all(stats["sym_bin_rows"][b] > 0 for b in range(7))
+    # (rows of bound above 1024 = 2048 bitmap words / 2 take bitmaps)
+    assert all(stats["sym_bin_rows"][b] > 0 for b in range(6))
     assert stats["sym_bin_rows"][10] > 0 and stats["sym_bin_rows"][11] > 0
-    assert all(stats["num_bin_rows"][b] > 0 for b in range(7))
+    assert all(stats["num_bin_rows"][b] > 0 for b in range(6))
     assert all(stats["num_bin_rows"][b] > 0 for b in (9, 11, 12))
     assert sum(stats["num_bin_flop"]) == stats["total_flop"]
     assert_matches_oracle(C, A, B, sorted_output, expect=expect)
@@ -402,4 +403,29 @@ def test_chunked_probing_gives_the_same_product(shape, dt, sorted_output):
     assert st["status"] == 0
     if shape == "global":
         assert st["sym_bin_rows"][12] == 5 and st["num_bin_rows"][10] >= 5
+    assert_matches_oracle(C, A, B, sorted_output)
+
+
+@pytest.mark.parametrize("sorted_output", [True, False])
+@pytest.mark.parametrize("dt", ["f64", "i64"])
+def test_block_bins_below_the_bitmap_threshold(dt, sorted_output):
+    """B with 2^18 columns: rows take bitmaps only above a bound of 4096
+    (2^13 words / 2), so rows of bound 600 .. 4000 fill the block hash bins
+    of 2048, 4096 and 8192 slots, beside warp-bin and bitmap rows."""
+    k = 1 << 18
+    B = inputs.er_exact(3000, 20, seed=95, ncols=k)
+    rng = np.random.default_rng(96)
+    degs = [30, 60, 100, 150, 200, 2, 10, 400] * 6          # flop 20 * deg
+    rows = np.concatenate([np.full(d, i) for i, d in enumerate(degs)])
+    cols = np.concatenate([rng.choice(3000, size=d, replace=False) for d in degs])
+    rp, ci = inputs.from_coo(len(degs), 3000, rows, cols)
+    A = CSR(len(degs), 3000, rp, ci, rng.uniform(-1, 1, len(ci)))
+    if dt != "f64":
+        A, B = int_valued(A, 97), int_valued(B, 98)
+    A, B = host_vals(A, DT[dt]), host_vals(B, DT[dt])
+    C, st = gpu_product(A, B, DT[dt], sorted_output)
+    assert st["status"] == 0
+    assert all(st["sym_bin_rows"][b] > 0 for b in (5, 6, 7))
+    assert all(st["num_bin_rows"][b] > 0 for b in (5, 6, 7))
+    assert st["sym_bin_rows"][11] > 0                      # the rows of bound 8000
     assert_matches_oracle(C, A, B, sorted_output)
