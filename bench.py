@@ -272,10 +272,10 @@ def run_batch(args) -> int:
             p.destroy()
         return launches
 
-    def batch_pass():
+    def batch_pass(tuning=None):
         launches = 0
         for w in waves:
-            b = sg.Batch([dm[i] for i in w], [dm[i] for i in w], True, stream=stream)
+            b = sg.Batch([dm[i] for i in w], [dm[i] for i in w], True, stream=stream, tuning=tuning)
             b.symbolic()
             b.numeric()
             launches += b.plan_stats()["kernel_launches"] + 2     # + pack, unpack
@@ -296,8 +296,15 @@ def run_batch(args) -> int:
             ts.append(e0.elapsed_time(e1) / 1e3)
         return sum(ts) / len(ts), launches
 
+    # autotuning (bin threshold, lanes per a_ik) on a sample: every 10th product
+    from paper_1804_01698_gb300.tune import autotune_batch
+    sample = [dm[i] for i in range(0, count, 10)]
+    t0 = time.time()
+    tuning, tune_table = autotune_batch(sample, sample, True, steps=2, stream=stream)
+    tune_s = time.time() - t0
     with ClockSampler(0) as clocks:
-        t_batch, l_batch = timed(batch_pass, args.steps, max(1, args.warmup))
+        t_batch, l_batch = timed(lambda: batch_pass(tuning), args.steps, max(1, args.warmup))
+        t_default, _ = timed(batch_pass, args.steps, max(1, args.warmup))
         t_plain, l_plain = timed(plain_pass, args.steps, max(1, args.warmup))
     flop = sum(flops)
     line = {
@@ -305,11 +312,14 @@ def run_batch(args) -> int:
         "n_gpus": 1, "steps": args.steps, "warmup": max(1, args.warmup), "ms_per_step": t_batch * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"{count} Erdos-Renyi products A_i*A_i, n_i log-uniform in [256,65536], "
-                               "k_i uniform in {2..32} per row, FP64, sorted output",
+                               "k_i uniform in {2..32} per row, FP64, sorted output, autotuned plan",
                    "products": count, "flop": flop, "nnz_a": sum(m.nnz for m in mats), "waves": len(waves),
                    "generation_s": gen_s, "l2": "inputs larger than L2"},
         "batched": {"solves_per_s": count / t_batch, "gflops": 2 * flop / t_batch / 1e9, "s_per_pass": t_batch,
-                    "kernel_launches": l_batch},
+                    "kernel_launches": l_batch, "tuning": tuning},
+        "batched_default_tuning": {"solves_per_s": count / t_default, "s_per_pass": t_default},
+        "autotune": {"sample": f"every 10th product ({len(sample)} products, one packed batch)",
+                     "seconds": tune_s, "candidates_ms": [[t, ms] for t, ms in tune_table]},
         "one_call_per_product": {"solves_per_s": count / t_plain, "gflops": 2 * flop / t_plain / 1e9,
                                  "s_per_pass": t_plain, "kernel_launches": l_plain},
         "speedup": t_plain / t_batch,

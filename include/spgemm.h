@@ -139,6 +139,30 @@ SPGEMM_API int spgemm_plan_create(spgemm_plan_t *out, const spgemm_csr *A, const
                        int dtype, unsigned flags, void *stream);
 
 /*
+ * Tuning of a plan's two main decisions (all zeros: the defaults).  The
+ * result does not depend on them; only the time does.  The paper tunes its
+ * recipe per input class (Sec. 4.2.4, Sec. 5.7); this is the GPU form.
+ *   lanes_per_entry   G, the lanes that share one stored a_ik in the row
+ *                     loop of the block kernels: 0 = chosen from the mean
+ *                     B-row length flop/nnz(A) (>= 24: 32, >= 12: 16,
+ *                     >= 6: 8, else 4); otherwise 4, 8, 16 or 32.
+ *   bitmap_min_bound  rows whose symbolic bound min(flop_i, k) exceeds it
+ *                     take the column-bitmap path (B with at most 2^18
+ *                     columns): 0 = max(512, k/64); -1 = no bitmap rows;
+ *                     otherwise a positive bound.
+ */
+typedef struct {
+    int32_t lanes_per_entry;
+    int32_t reserved; /* must be 0 */
+    int64_t bitmap_min_bound;
+} spgemm_tuning;
+
+/* spgemm_plan_create with a tuning (NULL: the defaults).  Out-of-range
+ * tuning values give SPGEMM_ERR_INVALID_ARGUMENT. */
+SPGEMM_API int spgemm_plan_create_tuned(spgemm_plan_t *out, const spgemm_csr *A, const spgemm_csr *B, int dtype,
+                                        unsigned flags, void *stream, const spgemm_tuning *tuning);
+
+/*
  * Symbolic phase (Sec. 4.2.1: "it is enough to insert keys to the hash
  * table"): counts the distinct columns of every output row, writes the
  * exclusive prefix sum to c_row_ptr (device, m+1 int32, caller-owned) and
@@ -229,6 +253,10 @@ SPGEMM_API int spgemm(const spgemm_csr *A, const spgemm_csr *B, int dtype, unsig
 typedef struct spgemm_batch_s *spgemm_batch_t;
 SPGEMM_API int spgemm_batch_create(spgemm_batch_t *out, int64_t nprod, const spgemm_csr *A, const spgemm_csr *B,
                                    int dtype, unsigned flags, void *stream);
+/* spgemm_batch_create with a tuning for the batch's plan (NULL: defaults). */
+SPGEMM_API int spgemm_batch_create_tuned(spgemm_batch_t *out, int64_t nprod, const spgemm_csr *A,
+                                         const spgemm_csr *B, int dtype, unsigned flags, void *stream,
+                                         const spgemm_tuning *tuning);
 SPGEMM_API int spgemm_batch_symbolic(spgemm_batch_t batch, int32_t *c_row_ptr, int64_t *nnz_c, int64_t *row_off);
 SPGEMM_API int spgemm_batch_numeric(spgemm_batch_t batch, const int32_t *c_row_ptr, int32_t *c_col_idx, void *c_vals);
 SPGEMM_API spgemm_plan_t spgemm_batch_plan(spgemm_batch_t batch);

@@ -58,6 +58,20 @@ class Stats(ctypes.Structure):
                 ("sym_bin_flop", ctypes.c_int64 * MAX_BINS), ("num_bin_flop", ctypes.c_int64 * MAX_BINS)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("lanes_per_entry", ctypes.c_int32), ("reserved", ctypes.c_int32), ("bitmap_min_bound", ctypes.c_int64)]
+
+
+def _tuning(t):
+    """A spgemm_tuning from a dict {lanes_per_entry, bitmap_min_bound} (None: defaults)."""
+    if t is None:
+        return None
+    unknown = set(t) - {"lanes_per_entry", "bitmap_min_bound"}
+    if unknown:
+        raise ValueError(f"unknown tuning keys {sorted(unknown)}")
+    return Tuning(int(t.get("lanes_per_entry", 0)), 0, int(t.get("bitmap_min_bound", 0)))
+
+
 class KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 40), ("ms", ctypes.c_float), ("launches", ctypes.c_int32)]
 
@@ -68,7 +82,7 @@ EXPORTED = ("spgemm_plan_create", "spgemm_symbolic", "spgemm_numeric", "spgemm_p
             "spgemm_plan_workspace_bytes", "spgemm_plan_stats", "spgemm_plan_row_flop", "spgemm_plan_sym_bins",
             "spgemm_plan_row_nnz", "spgemm_plan_kernel_times", "spgemm", "spgemm_status_string",
             "spgemm_last_error", "spgemm_symbolic_noalloc", "spgemm_batch_create", "spgemm_batch_symbolic",
-            "spgemm_batch_numeric", "spgemm_batch_destroy")
+            "spgemm_batch_numeric", "spgemm_batch_destroy", "spgemm_plan_create_tuned", "spgemm_batch_create_tuned")
 
 
 def library_path() -> str:
@@ -88,6 +102,8 @@ def library():
     P, I64, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
     lib.spgemm_plan_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(CsrDesc), ctypes.POINTER(CsrDesc), I32,
                                        ctypes.c_uint, P]
+    lib.spgemm_plan_create_tuned.argtypes = [ctypes.POINTER(P), ctypes.POINTER(CsrDesc), ctypes.POINTER(CsrDesc),
+                                             I32, ctypes.c_uint, P, ctypes.POINTER(Tuning)]
     lib.spgemm_symbolic.argtypes = [P, P, ctypes.POINTER(I64)]
     lib.spgemm_numeric.argtypes = [P, P, P, P]
     lib.spgemm_plan_destroy.argtypes = [P]
@@ -99,6 +115,8 @@ def library():
     lib.spgemm_plan_kernel_times.argtypes = [P, ctypes.POINTER(KernelTime), I32, ctypes.POINTER(I32)]
     lib.spgemm_batch_create.argtypes = [ctypes.POINTER(P), I64, ctypes.POINTER(CsrDesc), ctypes.POINTER(CsrDesc), I32,
                                         ctypes.c_uint, P]
+    lib.spgemm_batch_create_tuned.argtypes = [ctypes.POINTER(P), I64, ctypes.POINTER(CsrDesc),
+                                              ctypes.POINTER(CsrDesc), I32, ctypes.c_uint, P, ctypes.POINTER(Tuning)]
     lib.spgemm_batch_symbolic.argtypes = [P, P, ctypes.POINTER(I64), P]
     lib.spgemm_batch_numeric.argtypes = [P, P, P, P]
     lib.spgemm_batch_destroy.argtypes = [P]
@@ -166,7 +184,7 @@ class Plan:
     """A plan for C = A*B; methods mirror spgemm_symbolic / spgemm_numeric."""
 
     def __init__(self, A: DeviceCSR, B: DeviceCSR, sorted_output: bool = True, stream=None, timing: bool = False,
-                 serial: bool = False, probe: str = "linear"):
+                 serial: bool = False, probe: str = "linear", tuning: dict | None = None):
         self.lib = library()
         if A.vals.dtype != B.vals.dtype or A.vals.dtype not in _DTYPES:
             raise TypeError("A and B must share a value dtype among int64, float32, float64")
@@ -179,9 +197,11 @@ class Plan:
         self._a, self._b = A.desc(), B.desc()
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
-            _check(self.lib.spgemm_plan_create(ctypes.byref(h), ctypes.byref(self._a), ctypes.byref(self._b),
-                                               _DTYPES[self.dtype], flags, _stream_ptr(self.stream)),
-                   "spgemm_plan_create")
+            self._tuning = _tuning(tuning)
+            _check(self.lib.spgemm_plan_create_tuned(ctypes.byref(h), ctypes.byref(self._a), ctypes.byref(self._b),
+                                                     _DTYPES[self.dtype], flags, _stream_ptr(self.stream),
+                                                     ctypes.byref(self._tuning) if self._tuning else None),
+                   "spgemm_plan_create_tuned")
         self.handle = h
         self.c_row_ptr = None
         self.nnz_c = None
@@ -363,7 +383,7 @@ class Batch:
     packing on the device); mirrors spgemm_batch_create / _symbolic / _numeric."""
 
     def __init__(self, As, Bs, sorted_output: bool = True, stream=None, timing: bool = False, serial: bool = False,
-                 probe: str = "linear"):
+                 probe: str = "linear", tuning: dict | None = None):
         self.lib = library()
         if len(As) != len(Bs) or not As:
             raise ValueError("need the same positive number of A and B operands")
@@ -380,8 +400,11 @@ class Batch:
         self._b = (CsrDesc * n)(*[m.desc() for m in Bs])
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
-            _check(self.lib.spgemm_batch_create(ctypes.byref(h), n, self._a, self._b, _DTYPES[self.dtype], flags,
-                                                _stream_ptr(self.stream)), "spgemm_batch_create")
+            self._tuning = _tuning(tuning)
+            _check(self.lib.spgemm_batch_create_tuned(ctypes.byref(h), n, self._a, self._b, _DTYPES[self.dtype], flags,
+                                                      _stream_ptr(self.stream),
+                                                      ctypes.byref(self._tuning) if self._tuning else None),
+                   "spgemm_batch_create_tuned")
         self.handle = h
         self.nprod = n
         self.m = sum(a.nrows for a in As)

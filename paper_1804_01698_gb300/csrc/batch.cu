@@ -165,6 +165,11 @@ extern "C" {
 
 int spgemm_batch_create(spgemm_batch_t *out, int64_t nprod, const spgemm_csr *A, const spgemm_csr *B, int dtype,
                         unsigned flags, void *stream) {
+  return spgemm_batch_create_tuned(out, nprod, A, B, dtype, flags, stream, nullptr);
+}
+
+int spgemm_batch_create_tuned(spgemm_batch_t *out, int64_t nprod, const spgemm_csr *A, const spgemm_csr *B,
+                              int dtype, unsigned flags, void *stream, const spgemm_tuning *tuning) {
   if (!out) return SPGEMM_ERR_INVALID_ARGUMENT;
   *out = nullptr;
   set_last_error("");
@@ -276,7 +281,7 @@ int spgemm_batch_create(spgemm_batch_t *out, int64_t nprod, const spgemm_csr *A,
   }
   spgemm_csr pa{am, bm, an, b->arp, b->aci, b->av};
   spgemm_csr pb{bm, bk, bn, b->brp, b->bci, b->bv};
-  int rc = spgemm_plan_create(&b->plan, &pa, &pb, dtype, flags, stream);
+  int rc = spgemm_plan_create_tuned(&b->plan, &pa, &pb, dtype, flags, stream, tuning);
   if (rc != SPGEMM_OK) {
     cudaFreeAsync(b->ws, b->stream);
     delete b;

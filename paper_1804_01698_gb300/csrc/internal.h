@@ -140,6 +140,8 @@ struct spgemm_plan_s {
   int device;
   int state;  // 0 planned, 1 symbolic done, 2 numeric done
   int G;
+  int tune_G;            // spgemm_tuning::lanes_per_entry (0: chosen from the flop pass)
+  int64_t tune_bm_min;   // spgemm_tuning::bitmap_min_bound (0: default rule, -1: no bitmaps)
   bool bitmap_ok;
   int bm_words;
 

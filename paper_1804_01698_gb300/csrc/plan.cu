@@ -547,9 +547,22 @@ const char *spgemm_last_error(void) { return g_last_error.c_str(); }
 
 int spgemm_plan_create(spgemm_plan_t *out, const spgemm_csr *A, const spgemm_csr *B, int dtype, unsigned flags,
                        void *stream) {
+  return spgemm_plan_create_tuned(out, A, B, dtype, flags, stream, nullptr);
+}
+
+int spgemm_plan_create_tuned(spgemm_plan_t *out, const spgemm_csr *A, const spgemm_csr *B, int dtype,
+                             unsigned flags, void *stream, const spgemm_tuning *tuning) {
   if (!out) return SPGEMM_ERR_INVALID_ARGUMENT;
   *out = nullptr;
   g_last_error.clear();
+  if (tuning) {
+    const int g = tuning->lanes_per_entry;
+    if ((g != 0 && g != 4 && g != 8 && g != 16 && g != 32) || tuning->reserved != 0 ||
+        tuning->bitmap_min_bound < -1) {
+      set_last_error("tuning: lanes_per_entry must be 0, 4, 8, 16 or 32 and bitmap_min_bound >= -1");
+      return SPGEMM_ERR_INVALID_ARGUMENT;
+    }
+  }
   if (!valid_csr_desc(A) || !valid_csr_desc(B) || A->ncols != B->nrows) return SPGEMM_ERR_INVALID_ARGUMENT;
   if (dtype != SPGEMM_I64 && dtype != SPGEMM_F32 && dtype != SPGEMM_F64) return SPGEMM_ERR_INVALID_ARGUMENT;
   if (flags & ~(SPGEMM_SORTED | SPGEMM_VALIDATE | SPGEMM_TIMING | SPGEMM_SERIAL | SPGEMM_PROBE_CHUNK4))
@@ -583,6 +596,8 @@ int spgemm_plan_create(spgemm_plan_t *out, const spgemm_csr *A, const spgemm_csr
   p->stream = (cudaStream_t)stream;
   p->device = dev;
   p->G = 32;  // set from the flop pass below
+  p->tune_G = tuning ? tuning->lanes_per_entry : 0;
+  p->tune_bm_min = tuning ? tuning->bitmap_min_bound : 0;
   p->bitmap_ok = p->k <= kBitmapMaxCols;
   p->bm_words = (int)((p->k + 31) / 32);
   // bitmap classes: 3, 2 and 1 blocks per SM (228 KB per SM, 1 KB per block kept by the system)
@@ -639,8 +654,10 @@ int spgemm_plan_create(spgemm_plan_t *out, const spgemm_csr *A, const spgemm_csr
     Args a{p->m, p->n, p->k, p->arp, p->aci, p->brp, p->bci, p->av, p->bv, p->G, &p->dc->err};
     {
       KernelScope ks(p, "row_flop");
-      k_row_flop<<<(unsigned)((m + 7) / 8), 256, 0, p->stream>>>(a, p->nnz_a, p->nnz_b,
-                                                                  p->bitmap_ok ? bitmap_min_bound(p->k) : 0,
+      const int64_t bm_min = !p->bitmap_ok || p->tune_bm_min < 0 ? 0
+                             : p->tune_bm_min > 0                 ? p->tune_bm_min
+                                                                  : bitmap_min_bound(p->k);
+      k_row_flop<<<(unsigned)((m + 7) / 8), 256, 0, p->stream>>>(a, p->nnz_a, p->nnz_b, bm_min,
                                                                     p->flop, p->rbin, p->nnz_row, p->dc);
     }
     e = cudaGetLastError();
@@ -654,6 +671,7 @@ int spgemm_plan_create(spgemm_plan_t *out, const spgemm_csr *A, const spgemm_csr
     // from (flop / nnz(A)), so that long rows get whole warps
     const double per_entry = p->nnz_a > 0 ? (double)p->total_flop / (double)p->nnz_a : 0.0;
     p->G = per_entry >= 24 ? 32 : per_entry >= 12 ? 16 : per_entry >= 6 ? 8 : 4;
+    if (p->tune_G) p->G = p->tune_G;
     p->sym_off[0] = 0;
     for (int b = 0; b < kNumSymBins; ++b) {
       p->sym_flop[b] = (int64_t)p->hc->sym_flop[b];

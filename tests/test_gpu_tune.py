@@ -1,0 +1,59 @@
+"""Tuned plans (spgemm_tuning) and the autotuner on the GPU: every tuning
+gives the oracle's product (the tuning moves rows between kernels, never
+changes the result), out-of-range tunings are rejected, and the autotuner
+returns one of its candidates."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1804_01698_gb300 import inputs
+from gpu_helpers import assert_matches_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("tuning", [
+    {"lanes_per_entry": 4}, {"lanes_per_entry": 32}, {"bitmap_min_bound": 256}, {"bitmap_min_bound": 2048},
+    {"bitmap_min_bound": -1}, {"lanes_per_entry": 8, "bitmap_min_bound": 100000}])
+@pytest.mark.parametrize("sorted_output", [True, False])
+def test_every_tuning_gives_the_same_product(tuning, sorted_output):
+    from paper_1804_01698_gb300 import binding as sg
+    A = inputs.rmat(12, 16, seed=111)
+    dA = sg.to_device(A)
+    with sg.Plan(dA, dA, sorted_output, tuning=tuning) as p:
+        p.symbolic()
+        C = p.numeric()
+        st = p.stats()
+    torch.cuda.synchronize()
+    assert st["status"] == 0
+    if tuning.get("bitmap_min_bound") == -1:
+        assert st["sym_bin_rows"][10] == 0 and st["sym_bin_rows"][11] == 0
+    if tuning.get("bitmap_min_bound") == 256:
+        assert st["sym_bin_rows"][11] > 0
+    assert_matches_oracle(C, A, A, sorted_output)
+
+
+@pytest.mark.parametrize("bad", [{"lanes_per_entry": 5}, {"lanes_per_entry": 64}, {"bitmap_min_bound": -2}])
+def test_out_of_range_tuning_is_rejected(bad):
+    from paper_1804_01698_gb300 import binding as sg
+    dA = sg.to_device(inputs.er_exact(100, 4, seed=112))
+    with pytest.raises(sg.SpgemmError) as ei:
+        sg.Plan(dA, dA, True, tuning=bad)
+    assert ei.value.status == -1
+    with pytest.raises(ValueError):
+        sg.Plan(dA, dA, True, tuning={"no_such_knob": 1})
+
+
+def test_autotune_returns_a_candidate():
+    from paper_1804_01698_gb300 import binding as sg
+    from paper_1804_01698_gb300.tune import autotune, autotune_batch
+    dA = sg.to_device(inputs.rmat(11, 16, seed=113))
+    cands = [{"lanes_per_entry": 0, "bitmap_min_bound": 0}, {"lanes_per_entry": 16, "bitmap_min_bound": 2048},
+             {"lanes_per_entry": 32, "bitmap_min_bound": -1}]
+    best, table = autotune(dA, dA, True, candidates=cands, steps=2)
+    assert best in cands and len(table) == 3 and all(ms > 0 for _, ms in table)
+    mats = [sg.to_device(m) for m in inputs.er_batch(6, seed=114, n_hi=3000)]
+    best, table = autotune_batch(mats, mats, True, candidates=cands[:2], steps=2)
+    assert best in cands[:2] and len(table) == 2
