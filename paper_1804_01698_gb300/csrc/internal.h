@@ -216,6 +216,13 @@ struct KernelScope {
 // plan's stream wait for every side stream.  Without side streams all bins
 // run on the plan's stream.
 cudaError_t fork(spgemm_plan_s *p);
+// Bins run on side streams unless SPGEMM_SERIAL is set or the product is
+// small (total flop below kSideStreamMinFlop), where the fork and join cost
+// more than the overlap gains.
+constexpr int64_t kSideStreamMinFlop = 1 << 20;
+inline bool use_side_streams(const spgemm_plan_s *p) {
+  return !(p->flags & SPGEMM_SERIAL) && p->total_flop >= kSideStreamMinFlop;
+}
 cudaStream_t bin_stream(spgemm_plan_s *p, int i);
 cudaError_t join(spgemm_plan_s *p);
 

@@ -769,7 +769,7 @@ cudaError_t launch_numeric_t(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_c
   // heavy bins first, each bin on the next side stream
   static const int order[kNumNumBins] = {kNumBitmapBin, kNumBitmapMBin, kNumBitmapSBin, kNumGlobalBin, 8, 7, 6, 5,
                                          4, 3, 2, 1, 0};
-  const bool concurrent = !(p->flags & SPGEMM_SERIAL);
+  const bool concurrent = use_side_streams(p);
   cudaError_t e = cudaSuccess;
   const int64_t nbm = p->sym_count[kSymBitmapBin] + p->sym_count[kSymBitmapMidBin];
   if (nbm > 0 && p->bm_item_off[3] > 0) {

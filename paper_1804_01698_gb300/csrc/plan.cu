@@ -20,6 +20,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -362,14 +363,69 @@ static int sm_count() {
   return cached[dev];
 }
 
+// Side streams and their fork/join events come from a per-device pool: a
+// plan takes a set at its first fork and returns it when destroyed, so
+// repeated plans do not pay for creating streams.  A returned set may still
+// hold the old plan's work; the next plan's kernels queue behind it.
+struct SideSet {
+  cudaStream_t s[4];
+  cudaEvent_t fork_ev, join_ev[4];
+};
+static std::mutex g_side_mu;
+static std::vector<SideSet> g_side_free[64];
+
+static cudaError_t acquire_side(spgemm_plan_s *p) {
+  SideSet set{};
+  bool have = false;
+  if (p->device >= 0 && p->device < 64) {
+    std::lock_guard<std::mutex> g(g_side_mu);
+    if (!g_side_free[p->device].empty()) {
+      set = g_side_free[p->device].back();
+      g_side_free[p->device].pop_back();
+      have = true;
+    }
+  }
+  if (!have) {
+    bool ok = true;
+    for (int i = 0; i < 4 && ok; ++i) ok = cudaStreamCreateWithFlags(&set.s[i], cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&set.fork_ev, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; i < 4 && ok; ++i) ok = cudaEventCreateWithFlags(&set.join_ev[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) return cudaGetLastError() == cudaSuccess ? cudaErrorUnknown : cudaGetLastError();
+  }
+  for (int i = 0; i < 4; ++i) {
+    p->side[i] = set.s[i];
+    p->join_ev[i] = set.join_ev[i];
+  }
+  p->fork_ev = set.fork_ev;
+  p->side_ready = true;
+  return cudaSuccess;
+}
+
+static void release_side(spgemm_plan_s *p) {
+  if (!p->side_ready) return;
+  SideSet set{};
+  for (int i = 0; i < 4; ++i) {
+    set.s[i] = p->side[i];
+    set.join_ev[i] = p->join_ev[i];
+  }
+  set.fork_ev = p->fork_ev;
+  p->side_ready = false;
+  if (p->device >= 0 && p->device < 64) {
+    std::lock_guard<std::mutex> g(g_side_mu);
+    g_side_free[p->device].push_back(set);
+    return;
+  }
+  for (int i = 0; i < 4; ++i) {
+    cudaStreamDestroy(set.s[i]);
+    cudaEventDestroy(set.join_ev[i]);
+  }
+  cudaEventDestroy(set.fork_ev);
+}
+
 cudaError_t fork(spgemm_plan_s *p) {
   if (!p->side_ready) {
-    bool ok = true;
-    for (int i = 0; i < 4 && ok; ++i) ok = cudaStreamCreateWithFlags(&p->side[i], cudaStreamNonBlocking) == cudaSuccess;
-    ok = ok && cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming) == cudaSuccess;
-    for (int i = 0; i < 4 && ok; ++i) ok = cudaEventCreateWithFlags(&p->join_ev[i], cudaEventDisableTiming) == cudaSuccess;
-    if (!ok) return cudaGetLastError() == cudaSuccess ? cudaErrorUnknown : cudaGetLastError();
-    p->side_ready = true;
+    const cudaError_t ea = acquire_side(p);
+    if (ea != cudaSuccess) return ea;
   }
   cudaError_t e = cudaEventRecord(p->fork_ev, p->stream);
   for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(p->side[i], p->fork_ev, 0);
@@ -481,14 +537,7 @@ void free_events(spgemm_plan_s *p) {
 
 void free_ws(spgemm_plan_s *p) {
   free_events(p);
-  if (p->side_ready) {
-    for (int i = 0; i < 4; ++i) {
-      cudaStreamDestroy(p->side[i]);
-      cudaEventDestroy(p->join_ev[i]);
-    }
-    cudaEventDestroy(p->fork_ev);
-    p->side_ready = false;
-  }
+  release_side(p);
   if (p->ws_fixed) cudaFreeAsync(p->ws_fixed, p->stream);
   if (p->bitmaps) cudaFreeAsync(p->bitmaps, p->stream);
   if (p->bm_items) cudaFreeAsync(p->bm_items, p->stream);

@@ -186,7 +186,7 @@ cudaError_t launch_symbolic(spgemm_plan_s *p) {
          (p->flags & SPGEMM_PROBE_CHUNK4) ? 1 : 0};
   // heavy bins first, each bin on the next side stream
   static const int order[kNumSymBins] = {kSymBitmapBin, kSymBitmapMidBin, kSymGlobalBin, 9, 8, 7, 6, 5, 4, 3, 2, 1, 0};
-  const bool concurrent = !(p->flags & SPGEMM_SERIAL);
+  const bool concurrent = use_side_streams(p);
   cudaError_t e = concurrent ? fork(p) : cudaSuccess;
   int launched = 0;
   for (int o = 0; o < kNumSymBins && e == cudaSuccess; ++o) {
