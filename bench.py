@@ -272,10 +272,11 @@ def run_batch(args) -> int:
             p.destroy()
         return launches
 
-    def batch_pass(tuning=None):
+    def batch_pass(candidate=None):
+        kw, tuning = _split(candidate) if candidate else ({}, None)
         launches = 0
         for w in waves:
-            b = sg.Batch([dm[i] for i in w], [dm[i] for i in w], True, stream=stream, tuning=tuning)
+            b = sg.Batch([dm[i] for i in w], [dm[i] for i in w], True, stream=stream, tuning=tuning, **kw)
             b.symbolic()
             b.numeric()
             launches += b.plan_stats()["kernel_launches"] + 2     # + pack, unpack
@@ -297,7 +298,7 @@ def run_batch(args) -> int:
         return sum(ts) / len(ts), launches
 
     # autotuning (bin threshold, lanes per a_ik) on a sample: every 10th product
-    from paper_1804_01698_gb300.tune import autotune_batch
+    from paper_1804_01698_gb300.tune import _split, autotune_batch
     sample = [dm[i] for i in range(0, count, 10)]
     t0 = time.time()
     tuning, tune_table = autotune_batch(sample, sample, True, steps=2, stream=stream)
@@ -492,13 +493,14 @@ def run_sweep(args) -> int:
     return 0
 
 
-def collision_factor(A, B, row_nnz, rows, chunk: bool) -> float:
+def collision_factor(A, B, row_nnz, rows, chunk: bool, high: bool = False) -> float:
     """Probes per insertion (the collision factor c of Eq. 2) of the numeric
     hash tables, simulated sequentially on the given rows: each row's table
     has the size its bin gives it (warp tables of S = 64..1024 slots hold
     up to S/2 keys, block tables of 2048..16384 slots up to 3S/4), keys
-    arrive in product order, slot = (col * 2654435761) mod S.  Linear
-    probing reads one slot per probe; chunked probing reads 4 (one probe)."""
+    arrive in product order, slot = (col * 2654435761) mod S (or, `high`,
+    its top log2(S) bits of 32).  Linear probing reads one slot per probe;
+    chunked probing reads 4 (one probe)."""
     caps = [(s, s // 2) for s in (64, 128, 256, 512, 1024)] + [(s, 3 * s // 4) for s in (2048, 4096, 8192, 16384)]
     probes = inserts = 0
     for i in rows:
@@ -512,7 +514,8 @@ def collision_factor(A, B, row_nnz, rows, chunk: bool) -> float:
             k = A.col_idx[j]
             for q in range(B.row_ptr[k], B.row_ptr[k + 1]):
                 col = int(B.col_idx[q])
-                h = (col * 2654435761) & 0xFFFFFFFF & mask
+                x = (col * 2654435761) & 0xFFFFFFFF
+                h = (x >> (32 - size.bit_length() + 1)) if high else (x & mask)
                 inserts += 1
                 if chunk:
                     h &= ~3
@@ -542,7 +545,9 @@ def run_ablate_probe(args) -> int:
     the chunked probing of HashVector, Sec. 4.2.2 (4 slots per 16-byte load,
     SPGEMM_PROBE_CHUNK4): whole products (concurrent bins, L2 flushed) and
     the hash-table kernels alone (bins serialised, an event pair per
-    kernel), plus the collision factor c of Eq. 2 of each scheme."""
+    kernel), plus the collision factor c of Eq. 2 of each scheme: counted on
+    the device (SPGEMM_COUNT_PROBES, every hash insert of both phases) and
+    simulated sequentially on a sample of rows."""
     import torch
 
     import __graft_entry__
@@ -565,14 +570,16 @@ def run_ablate_probe(args) -> int:
             dA = sg.to_device(A, dev)
             dB = dA if B is A else sg.to_device(B, dev)
             row = {"workload": name, "flop": None}
-            for probe in ("linear", "chunk4"):
+            for probe, hsh in (("linear", "low"), ("chunk4", "low"), ("linear", "high"), ("chunk4", "high")):
+                tag = probe if hsh == "low" else f"{probe}_high"   # plain names: the paper's low-bits hash
                 for timing in (False, True):
                     ts, kt = [], {}
                     for it in range(steps + 1):
                         flush.fill_(it & 0xFF)
                         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                         e0.record(stream)
-                        plan = sg.Plan(dA, dB, True, stream=stream, timing=timing, serial=timing, probe=probe)
+                        plan = sg.Plan(dA, dB, True, stream=stream, timing=timing, serial=timing, probe=probe,
+                                       hash=hsh)
                         plan.symbolic()
                         C = plan.numeric()
                         e1.record(stream)
@@ -586,7 +593,7 @@ def run_ablate_probe(args) -> int:
                             if timing:
                                 for k, (ms, _) in plan.kernel_times().items():
                                     kt[k] = kt.get(k, 0.0) + ms / steps
-                        if probe == "linear" and not timing and it == 0:
+                        if tag == "linear" and not timing and it == 0:
                             row_nnz = plan.row_nnz().cpu().numpy()
                         plan.destroy()
                         del C
@@ -594,14 +601,25 @@ def run_ablate_probe(args) -> int:
                         hash_ms = sum(v for k, v in kt.items() if k.startswith(("sym_warp", "sym_block", "num_warp",
                                                                                    "num_block", "sym_global",
                                                                                    "num_global")))
-                        row[probe + "_hash_kernels_ms"] = hash_ms
+                        row[tag + "_hash_kernels_ms"] = hash_ms
                     else:
-                        row[probe + "_step_ms"] = statistics.median(ts)
+                        row[tag + "_step_ms"] = statistics.median(ts)
                 row["flop"] = st["total_flop"]
+                # the collision factor measured on the device (SPGEMM_COUNT_PROBES, an untimed run)
+                with sg.Plan(dA, dB, True, stream=stream, probe=probe, hash=hsh, count_probes=True) as cp:
+                    cp.symbolic()
+                    cp.numeric()
+                    cs = cp.stats()
+                row[f"c_gpu_{tag}"] = {
+                    "symbolic": cs["sym_probes"] / cs["sym_inserts"] if cs["sym_inserts"] else None,
+                    "numeric": cs["num_probes"] / cs["num_inserts"] if cs["num_inserts"] else None,
+                    "hash_inserts": cs["sym_inserts"] + cs["num_inserts"]}
             hash_rows = np.nonzero((row_nnz > 0) & (row_nnz <= 12288))[0]
             sample = rng.choice(hash_rows, size=min(300, len(hash_rows)), replace=False) if len(hash_rows) else []
             row["c_linear"] = collision_factor(A, B, row_nnz, sample, False)
             row["c_chunk4"] = collision_factor(A, B, row_nnz, sample, True)
+            row["c_linear_high"] = collision_factor(A, B, row_nnz, sample, False, True)
+            row["c_chunk4_high"] = collision_factor(A, B, row_nnz, sample, True, True)
             row["c_sample_rows"] = len(sample)
             rows_out.append(row)
             print(json.dumps(row), file=sys.stderr, flush=True)
@@ -611,7 +629,8 @@ def run_ablate_probe(args) -> int:
         "metric": "SpGEMM GFLOP/s (2*flop per second)", "value": 2 * head["flop"] / (head["linear_step_ms"] * 1e-3) / 1e9,
         "unit": "GFLOP/s", "n_gpus": 1, "steps": steps, "warmup": 1, "ms_per_step": head["linear_step_ms"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "probing ablation: linear (Sec. 4.2.1) vs 4-slot chunks (Sec. 4.2.2) on R-MAT16 A*A, "
+        "config": {"workload": "probing ablation: linear (Sec. 4.2.1) vs 4-slot chunks (Sec. 4.2.2), each with the "
+                               "low-bits and the high-bits hash, on R-MAT16 A*A, "
                                "ER (R-MAT .25) scale 16 EF 16 A*A and triangle L*U of R-MAT16; FP64, sorted",
                    "l2": "256 MiB flush between steps", "timing": "median over steps"},
         "ablation": rows_out,
@@ -761,8 +780,45 @@ def main() -> int:
                     "frac": path_gbs / hbm_peak, "frac_of_8tbs": path_gbs / 8000.0, "peak_source": hbm_src}
 
     phases = {name: round(ms / args.steps, 4) for name, (ms, n) in sorted(kt.items(), key=lambda kv: -kv[1][0])}
+
+    def phase_of(name):
+        if name.startswith(("row_flop", "bin_rows_sym")):
+            return "plan: flop pass and binning (Sec. 4.1)"
+        if name.startswith(("sym_", "scan_", "num_classify", "bm_items_count")):
+            return "symbolic: counts, row_ptr scan (Sec. 4.2.1)"
+        return "numeric: accumulation and sort (Sec. 4.2.1)"
+    phase_totals = {}
+    for name, (ms, _) in kt.items():
+        phase_totals[phase_of(name)] = phase_totals.get(phase_of(name), 0.0) + ms / args.steps
+    phase_totals = {k: round(v, 4) for k, v in phase_totals.items()}
     kt_total = sum(ms for ms, _ in kt.values())
     shares = {name: round(ms / kt_total, 4) for name, (ms, n) in sorted(kt.items(), key=lambda kv: -kv[1][0])}
+
+    # the autotuner's pick for this product (tuning runs untimed), then the
+    # same K steps with it; the headline value stays the default plan's
+    tuned = None
+    if not args.no_variant:
+        from paper_1804_01698_gb300.tune import _split, autotune
+        t0 = time.perf_counter()
+        best, table = autotune(dA, dB, sorted_output, steps=2, stream=stream)
+        tune_s = time.perf_counter() - t0
+        kw, tuning = _split(best)
+        tt = []
+        for it in range(args.steps + 1):
+            flush.fill_(it & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            with sg.Plan(dA, dB, sorted_output, stream=stream, tuning=tuning, **kw) as tp:
+                tp.symbolic()
+                tC = tp.numeric()
+            e1.record(stream)
+            e1.synchronize()
+            del tC
+            if it > 0:
+                tt.append(e0.elapsed_time(e1))
+        tms = sum(tt) / len(tt)
+        tuned = {"candidate": best, "ms_per_step": tms, "value": 2 * flop / (tms * 1e-3) / 1e9,
+                 "autotune_seconds": tune_s, "candidates": len(table)}
 
     variant = None
     if not args.no_variant:
@@ -822,6 +878,25 @@ def main() -> int:
         cpu = {"value": 2 * flop / dt / 1e9, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
                "sample": "the whole product once (dense-SPA Gustavson, rows split by RowsToThreads)",
                "seconds": dt}
+        # the same oracle on one thread, and scipy's CSR product as a library
+        # reference point (not the oracle; timed once each)
+        t0 = time.perf_counter()
+        oracle.spgemm(A, B, nthreads=1)
+        dt1 = time.perf_counter() - t0
+        cpu["single_thread"] = {"value": 2 * flop / dt1 / 1e9, "unit": "GFLOP/s", "cores": 1, "seconds": dt1}
+        try:
+            import scipy.sparse as sp
+            sa = sp.csr_matrix((A.vals, A.col_idx, A.row_ptr), shape=(A.nrows, A.ncols))
+            sb = sa if same else sp.csr_matrix((B.vals, B.col_idx, B.row_ptr), shape=(B.nrows, B.ncols))
+            t0 = time.perf_counter()
+            sc = sa @ sb
+            if sorted_output:
+                sc.sort_indices()
+            dts = time.perf_counter() - t0
+            cpu["scipy"] = {"value": 2 * flop / dts / 1e9, "unit": "GFLOP/s", "cores": 1, "seconds": dts,
+                            "note": "scipy.sparse CSR product, a library reference point"}
+        except ImportError:
+            cpu["scipy"] = None
 
     if rank == 0:
         line = {
@@ -840,8 +915,11 @@ def main() -> int:
             "gpu_launches": launches * world,
             "clocks": clock_summary,
             "phases_ms": phases,
+            "phase_totals_ms": phase_totals,
+            "ms_per_step_median": round(statistics.median(times), 4),
             "kernel_share": shares,
             "variant": variant,
+            "tuned": tuned,
             "wall_s_timed_region": wall,
         }
         print(json.dumps(line), flush=True)

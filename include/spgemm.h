@@ -87,6 +87,15 @@ typedef enum { SPGEMM_I64 = 0, SPGEMM_F32 = 1, SPGEMM_F64 = 2 } spgemm_dtype;
 #define SPGEMM_TIMING 4u   /* record CUDA events around every kernel (spgemm_plan_kernel_times) */
 #define SPGEMM_SERIAL 8u   /* run the bins of a phase one after another on the plan's stream
                               (default: concurrently on side streams joined back to it) */
+#define SPGEMM_HASH_LOW_BITS 64u /* hash slot = the low log2(size) bits of col * 2654435761, the remainder
+                                    modulo the table size that Sec. 4.2.1 describes.  The default takes the
+                                    top log2(size) bits instead (Fibonacci hashing): the low bits depend only
+                                    on the column's low bits, which skewed (R-MAT) inputs share, and measured
+                                    R-MAT A*A probes 2.75 slots per insert with them against 1.25.  The
+                                    result is the same either way. */
+#define SPGEMM_COUNT_PROBES 32u /* count hash-table probes and inserts (spgemm_stats::sym_probes etc.):
+                                   the collision factor c of Eq. 2 is probes / inserts.  Adds global
+                                   atomics to every hash insert: for measurement, not for timing. */
 #define SPGEMM_PROBE_CHUNK4 16u /* hash tables probed 4 slots at a time: one 16-byte load reads the
                                    chunk holding the key's slot, a key is claimed in the chunk's first
                                    empty slot and the next chunk is tried only when this one is full
@@ -122,6 +131,9 @@ typedef struct {
     int32_t state;             /* 0 planned, 1 symbolic done, 2 numeric done */
     int64_t sym_bin_flop[SPGEMM_MAX_BINS]; /* sum of flop[i] over the rows of each symbolic bin */
     int64_t num_bin_flop[SPGEMM_MAX_BINS]; /* same for numeric bins (bitmap bin: its rows, once) */
+    int64_t sym_probes, sym_inserts;       /* hash-table slot reads (chunk reads under SPGEMM_PROBE_CHUNK4) and
+                                              key insertions of the symbolic phase (SPGEMM_COUNT_PROBES only) */
+    int64_t num_probes, num_inserts;       /* the same for the numeric phase */
 } spgemm_stats;
 
 typedef struct spgemm_plan_s *spgemm_plan_t;
@@ -150,11 +162,17 @@ SPGEMM_API int spgemm_plan_create(spgemm_plan_t *out, const spgemm_csr *A, const
  *                     take the column-bitmap path (B with at most 2^18
  *                     columns): 0 = max(512, k/64); -1 = no bitmap rows;
  *                     otherwise a positive bound.
+ *   max_nnz_c         the largest nnz(C) the plan accepts before
+ *                     spgemm_symbolic returns SPGEMM_ERR_INDEX_OVERFLOW:
+ *                     0 = 2^31-1 (int32 indexing); a smaller limit caps the
+ *                     output memory of a product (and lets tests reach the
+ *                     overflow path on small inputs).
  */
 typedef struct {
     int32_t lanes_per_entry;
     int32_t reserved; /* must be 0 */
     int64_t bitmap_min_bound;
+    int64_t max_nnz_c;
 } spgemm_tuning;
 
 /* spgemm_plan_create with a tuning (NULL: the defaults).  Out-of-range

@@ -27,6 +27,9 @@ _LIB = None
 SPGEMM_I64, SPGEMM_F32, SPGEMM_F64 = 0, 1, 2
 SPGEMM_UNSORTED, SPGEMM_SORTED, SPGEMM_VALIDATE, SPGEMM_TIMING, SPGEMM_SERIAL = 0, 1, 2, 4, 8
 SPGEMM_PROBE_CHUNK4 = 16
+SPGEMM_COUNT_PROBES = 32
+SPGEMM_HASH_LOW_BITS = 64
+_HASHES = {"high": 0, "low": SPGEMM_HASH_LOW_BITS}
 _PROBES = {"linear": 0, "chunk4": SPGEMM_PROBE_CHUNK4}
 MAX_BINS = 24
 
@@ -55,21 +58,24 @@ class Stats(ctypes.Structure):
                 ("sym_bin_rows", ctypes.c_int64 * MAX_BINS), ("num_bin_rows", ctypes.c_int64 * MAX_BINS),
                 ("sym_bin_table", ctypes.c_int32 * MAX_BINS), ("num_bin_table", ctypes.c_int32 * MAX_BINS),
                 ("workspace_bytes", ctypes.c_int64), ("kernel_launches", ctypes.c_int32), ("state", ctypes.c_int32),
-                ("sym_bin_flop", ctypes.c_int64 * MAX_BINS), ("num_bin_flop", ctypes.c_int64 * MAX_BINS)]
+                ("sym_bin_flop", ctypes.c_int64 * MAX_BINS), ("num_bin_flop", ctypes.c_int64 * MAX_BINS),
+                ("sym_probes", ctypes.c_int64), ("sym_inserts", ctypes.c_int64),
+                ("num_probes", ctypes.c_int64), ("num_inserts", ctypes.c_int64)]
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("lanes_per_entry", ctypes.c_int32), ("reserved", ctypes.c_int32), ("bitmap_min_bound", ctypes.c_int64)]
+    _fields_ = [("lanes_per_entry", ctypes.c_int32), ("reserved", ctypes.c_int32), ("bitmap_min_bound", ctypes.c_int64),
+                ("max_nnz_c", ctypes.c_int64)]
 
 
 def _tuning(t):
-    """A spgemm_tuning from a dict {lanes_per_entry, bitmap_min_bound} (None: defaults)."""
+    """A spgemm_tuning from a dict {lanes_per_entry, bitmap_min_bound, max_nnz_c} (None: defaults)."""
     if t is None:
         return None
-    unknown = set(t) - {"lanes_per_entry", "bitmap_min_bound"}
+    unknown = set(t) - {"lanes_per_entry", "bitmap_min_bound", "max_nnz_c"}
     if unknown:
         raise ValueError(f"unknown tuning keys {sorted(unknown)}")
-    return Tuning(int(t.get("lanes_per_entry", 0)), 0, int(t.get("bitmap_min_bound", 0)))
+    return Tuning(int(t.get("lanes_per_entry", 0)), 0, int(t.get("bitmap_min_bound", 0)), int(t.get("max_nnz_c", 0)))
 
 
 class KernelTime(ctypes.Structure):
@@ -184,7 +190,8 @@ class Plan:
     """A plan for C = A*B; methods mirror spgemm_symbolic / spgemm_numeric."""
 
     def __init__(self, A: DeviceCSR, B: DeviceCSR, sorted_output: bool = True, stream=None, timing: bool = False,
-                 serial: bool = False, probe: str = "linear", tuning: dict | None = None):
+                 serial: bool = False, probe: str = "linear", tuning: dict | None = None, count_probes: bool = False,
+                 hash: str = "high"):
         self.lib = library()
         if A.vals.dtype != B.vals.dtype or A.vals.dtype not in _DTYPES:
             raise TypeError("A and B must share a value dtype among int64, float32, float64")
@@ -193,7 +200,8 @@ class Plan:
         self.device = A.row_ptr.device
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         flags = (SPGEMM_SORTED if sorted_output else SPGEMM_UNSORTED) | (SPGEMM_TIMING if timing else 0) | \
-            (SPGEMM_SERIAL if serial else 0) | _PROBES[probe]
+            (SPGEMM_SERIAL if serial else 0) | _PROBES[probe] | _HASHES[hash] | \
+            (SPGEMM_COUNT_PROBES if count_probes else 0)
         self._a, self._b = A.desc(), B.desc()
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
@@ -383,7 +391,7 @@ class Batch:
     packing on the device); mirrors spgemm_batch_create / _symbolic / _numeric."""
 
     def __init__(self, As, Bs, sorted_output: bool = True, stream=None, timing: bool = False, serial: bool = False,
-                 probe: str = "linear", tuning: dict | None = None):
+                 probe: str = "linear", tuning: dict | None = None, hash: str = "high"):
         self.lib = library()
         if len(As) != len(Bs) or not As:
             raise ValueError("need the same positive number of A and B operands")
@@ -394,7 +402,7 @@ class Batch:
         self.device = As[0].row_ptr.device
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         flags = (SPGEMM_SORTED if sorted_output else SPGEMM_UNSORTED) | (SPGEMM_TIMING if timing else 0) | \
-            (SPGEMM_SERIAL if serial else 0) | _PROBES[probe]
+            (SPGEMM_SERIAL if serial else 0) | _PROBES[probe] | _HASHES[hash]
         n = len(As)
         self._a = (CsrDesc * n)(*[m.desc() for m in As])
         self._b = (CsrDesc * n)(*[m.desc() for m in Bs])

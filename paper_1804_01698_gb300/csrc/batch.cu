@@ -170,6 +170,7 @@ int spgemm_batch_create(spgemm_batch_t *out, int64_t nprod, const spgemm_csr *A,
 
 int spgemm_batch_create_tuned(spgemm_batch_t *out, int64_t nprod, const spgemm_csr *A, const spgemm_csr *B,
                               int dtype, unsigned flags, void *stream, const spgemm_tuning *tuning) {
+  NvtxRange nvtx("spgemm_batch_create");
   if (!out) return SPGEMM_ERR_INVALID_ARGUMENT;
   *out = nullptr;
   set_last_error("");

@@ -16,8 +16,13 @@ namespace sg {
 constexpr uint32_t kHashScale = 2654435761u;
 constexpr int32_t kEmpty = -1;  // Sec. 4.2.1: tables are initialised with -1
 
-__device__ __forceinline__ uint32_t hash_slot(int32_t col, uint32_t mask) {
-  return ((uint32_t)col * kHashScale) & mask;
+// The slot of a key in a table of mask+1 (a power of two) slots: with `hi`
+// (the default) the top log2(size) bits of col * kHashScale (Fibonacci
+// hashing), which depend on every bit of the column; otherwise its low bits,
+// the remainder modulo the table size of Sec. 4.2.1 (SPGEMM_HASH_LOW_BITS).
+__device__ __forceinline__ uint32_t hash_slot(int32_t col, uint32_t mask, int hi = 0) {
+  const uint32_t x = (uint32_t)col * kHashScale;
+  return hi ? x >> (32 - __popc(mask)) : x & mask;
 }
 
 // Bits of the device error word (DevCounters::err).
@@ -62,12 +67,24 @@ __device__ __forceinline__ int4 load_chunk(const int32_t *tab, uint32_t h) {
 // chunk and never freed, so a key is absent from the table when its chunk
 // has an empty slot and no match.  Returns the key's slot and sets *fresh
 // when this call claimed it; -1 after a failed bound (err raised).
+constexpr int kProbeSlots = 32;  // counters per phase for SPGEMM_COUNT_PROBES
+
+// SPGEMM_COUNT_PROBES: adds one insertion of `probes` probes to the phase's
+// counters (spread over kProbeSlots addresses).
+__device__ __forceinline__ void count_probes(unsigned long long *ctr, unsigned probes) {
+  if (!ctr) return;
+  const unsigned slot = (blockIdx.x * 7u + threadIdx.x) % kProbeSlots;
+  atomicAdd(ctr + slot, (unsigned long long)probes);
+  atomicAdd(ctr + kProbeSlots + slot, 1ull);
+}
+
 template <bool GLOBAL_MEM>
 __device__ __forceinline__ int chunk_find_or_claim(int32_t *tab, uint32_t mask, int32_t c, bool *fresh,
-                                                   uint32_t *err) {
-  uint32_t h = hash_slot(c, mask) & ~3u;
+                                                   uint32_t *err, unsigned *probes, int hi) {
+  uint32_t h = hash_slot(c, mask, hi) & ~3u;
   int retries = 0;
   for (uint32_t chunk = 0; chunk <= (mask >> 2);) {
+    ++*probes;
     const int4 k4 = load_chunk<GLOBAL_MEM>(tab, h);
     const int32_t kk[4] = {k4.x, k4.y, k4.z, k4.w};
     int e = -1;

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/spgemm.h"
 
@@ -114,9 +115,19 @@ struct DevCounters {
   unsigned long long bm_items[3];       // numeric bitmap work items per class (small, medium, large)
   unsigned long long bm_cursor[3];
   unsigned long long bm_flop[3];        // flop of the rows of each class
+  // SPGEMM_COUNT_PROBES: rows 0/1 symbolic probes/inserts, 2/3 numeric,
+  // each spread over kProbeSlots counters to limit atomic contention
+  unsigned long long probe_stats[4][kProbeSlots];
   unsigned int err;
   unsigned int pad;
 };
+
+// Hash-table variants of a plan (Args::probe bits).
+constexpr int kProbeChunk = 1;   // chunks of 4 slots per probe
+constexpr int kProbeHashHi = 2;  // slot from the top bits of col * kHashScale (default)
+inline int probe_mode(unsigned flags) {
+  return ((flags & SPGEMM_PROBE_CHUNK4) ? kProbeChunk : 0) | ((flags & SPGEMM_HASH_LOW_BITS) ? 0 : kProbeHashHi);
+}
 
 // Kernel arguments common to all phases.
 struct Args {
@@ -125,9 +136,22 @@ struct Args {
   const void *av, *bv;
   int G;  // lanes per stored a_ik
   uint32_t *err;
-  int probe = 0;  // hash probing: 0 linear, 1 chunks of 4 slots (SPGEMM_PROBE_CHUNK4)
+  int probe = 0;  // hash tables: kProbeChunk (SPGEMM_PROBE_CHUNK4) | kProbeHashHi (unless SPGEMM_HASH_LOW_BITS)
+  // SPGEMM_COUNT_PROBES: this phase's probe counters (inserts at +kProbeSlots), else null
+  unsigned long long *probe_ctr = nullptr;
 };
 
+}  // namespace sg
+
+namespace sg {
+// An NVTX range for the lifetime of a scope (shown by profilers; no cost
+// without one attached).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 }  // namespace sg
 
 struct spgemm_plan_s {
@@ -142,6 +166,7 @@ struct spgemm_plan_s {
   int G;
   int tune_G;            // spgemm_tuning::lanes_per_entry (0: chosen from the flop pass)
   int64_t tune_bm_min;   // spgemm_tuning::bitmap_min_bound (0: default rule, -1: no bitmaps)
+  int64_t max_nnz_c;     // largest nnz(C) accepted (spgemm_tuning::max_nnz_c, default 2^31-1)
   bool bitmap_ok;
   int bm_words;
 

@@ -26,13 +26,15 @@ namespace sg {
 
 constexpr int kUN = 4;  // B entries (column + value) loaded ahead per lane
 
-// Finds or claims the slot of key c and accumulates a*b there.
+// Every variant of the insert (see insert_key_any).
 template <typename T, bool GLOBAL_MEM>
-__device__ __forceinline__ void insert_acc(int32_t *keys, T *vals, uint32_t mask, int32_t c, T a, T b,
-                                           uint32_t *err, int probe) {
-  if (probe) {
+__device__ __forceinline__ void insert_acc_any(int32_t *keys, T *vals, uint32_t mask, int32_t c, T a, T b,
+                                            uint32_t *err, int probe, unsigned long long *ctr) {
+  if (probe & kProbeChunk) {
     bool fresh = false;
-    const int h = chunk_find_or_claim<GLOBAL_MEM>(keys, mask, c, &fresh, err);
+    unsigned probes = 0;
+    const int h = chunk_find_or_claim<GLOBAL_MEM>(keys, mask, c, &fresh, err, &probes, probe & kProbeHashHi);
+    count_probes(ctr, probes);
     if (h < 0) return;
     if (GLOBAL_MEM) {
       Val<T>::acc_global(vals + h, a, b);
@@ -41,8 +43,34 @@ __device__ __forceinline__ void insert_acc(int32_t *keys, T *vals, uint32_t mask
     }
     return;
   }
-  uint32_t h = hash_slot(c, mask);
+  uint32_t h = hash_slot(c, mask, probe & kProbeHashHi);
   for (uint32_t probe = 0; probe <= mask; ++probe) {
+    const int32_t old = atomicCAS(keys + h, kEmpty, c);
+    if (old == kEmpty || old == c) {
+      count_probes(ctr, probe + 1);
+      if (GLOBAL_MEM) {
+        Val<T>::acc_global(vals + h, a, b);
+      } else if (!Val<T>::acc_shared(vals + h, a, b)) {
+        raise_err(err, kErrRetry);
+      }
+      return;
+    }
+    h = (h + 1) & mask;
+  }
+  raise_err(err, kErrProbe);
+}
+
+// Finds or claims the slot of key c and accumulates a*b there.  The default
+// plan (linear probing, top-bits hash, no counting) runs the loop inline.
+template <typename T, bool GLOBAL_MEM>
+__device__ __forceinline__ void insert_acc(int32_t *keys, T *vals, uint32_t mask, int32_t c, T a, T b,
+                                           uint32_t *err, int probe, unsigned long long *ctr) {
+  if (probe != kProbeHashHi || ctr) {
+    insert_acc_any<T, GLOBAL_MEM>(keys, vals, mask, c, a, b, err, probe, ctr);
+    return;
+  }
+  uint32_t h = hash_slot(c, mask, 1);
+  for (uint32_t q = 0; q <= mask; ++q) {
     const int32_t old = atomicCAS(keys + h, kEmpty, c);
     if (old == kEmpty || old == c) {
       if (GLOBAL_MEM) {
@@ -259,7 +287,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 8)
   const int G = a.G;
   warp_row_products<kUN, true, T>(a.arp[i], a.arp[i + 1], G, a.aci, (const T *)a.av, a.brp, a.bci, (const T *)a.bv,
                                   (int32_t)a.k, a.err, Stage<T>{s_ent[warp], &s_next[warp], nullptr},
-                                 [&](int32_t c, T av, T bv) { insert_acc<T, false>(keys, vals, S - 1, c, av, bv, a.err, a.probe); });
+                                 [&](int32_t c, T av, T bv) { insert_acc<T, false>(keys, vals, S - 1, c, av, bv, a.err, a.probe, a.probe_ctr); });
   __syncwarp();
   const int32_t rp = c_rp[i];
   const int32_t nnz = c_rp[i + 1] - rp;
@@ -350,7 +378,7 @@ __global__ void __launch_bounds__(num_block_threads<S>(), num_block_min_blocks<S
   const int G = a.G;
   block_row_products<kUN, true, T>(a.arp[i], a.arp[i + 1], G, a.aci, (const T *)a.av, a.brp, a.bci,
                                    (const T *)a.bv, (int32_t)a.k, a.err, Stage<T>{s_ent, &s_next, s_wsum},
-                                 [&](int32_t c, T av, T bv) { insert_acc<T, false>(keys, vals, S - 1, c, av, bv, a.err, a.probe); });
+                                 [&](int32_t c, T av, T bv) { insert_acc<T, false>(keys, vals, S - 1, c, av, bv, a.err, a.probe, a.probe_ctr); });
   __syncthreads();
   const int32_t rp = c_rp[i];
   const int32_t nnz = c_rp[i + 1] - rp;
@@ -645,7 +673,7 @@ __global__ void __launch_bounds__(1024, 1)
     const int32_t i = rows[r];
     block_row_products<kUN, true, T>(a.arp[i], a.arp[i + 1], G, a.aci, (const T *)a.av, a.brp, a.bci,
                                    (const T *)a.bv, (int32_t)a.k, a.err, Stage<T>{s_ent, &s_next, s_wsum},
-                                   [&](int32_t c, T av, T bv) { insert_acc<T, true>(keys, vals, mask, c, av, bv, a.err, a.probe); });
+                                   [&](int32_t c, T av, T bv) { insert_acc<T, true>(keys, vals, mask, c, av, bv, a.err, a.probe, a.probe_ctr); });
     __syncthreads();
     const int32_t rp = c_rp[i];
     const int32_t nnz = c_rp[i + 1] - rp;
@@ -765,7 +793,7 @@ static cudaError_t num_block(spgemm_plan_s *p, cudaStream_t st, const Args &a, c
 template <typename T>
 cudaError_t launch_numeric_t(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_ci, T *c_v) {
   Args a{p->m, p->n, p->k, p->arp, p->aci, p->brp, p->bci, p->av, p->bv, p->G, &p->dc->err,
-         (p->flags & SPGEMM_PROBE_CHUNK4) ? 1 : 0};
+         probe_mode(p->flags), (p->flags & SPGEMM_COUNT_PROBES) ? &p->dc->probe_stats[2][0] : nullptr};
   // heavy bins first, each bin on the next side stream
   static const int order[kNumNumBins] = {kNumBitmapBin, kNumBitmapMBin, kNumBitmapSBin, kNumGlobalBin, 8, 7, 6, 5,
                                          4, 3, 2, 1, 0};

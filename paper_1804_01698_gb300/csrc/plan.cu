@@ -189,7 +189,8 @@ __global__ void __launch_bounds__(kScanThreads)
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_spine(long long *partial, int64_t nblk, DevCounters *dc) {
+__global__ void __launch_bounds__(kScanThreads)
+    k_scan_spine(long long *partial, int64_t nblk, long long max_nnz, DevCounters *dc) {
   __shared__ long long red[33];
   long long carry = 0;
   for (int64_t c0 = 0; c0 < nblk; c0 += kScanThreads) {
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_spine(long long *partial,
   }
   if (threadIdx.x == 0) {
     dc->nnz_c = (unsigned long long)carry;
-    if (carry > 2147483647LL) raise_err(&dc->err, kErrOverflow);
+    if (carry > max_nnz) raise_err(&dc->err, kErrOverflow);
   }
 }
 
@@ -601,20 +602,23 @@ int spgemm_plan_create(spgemm_plan_t *out, const spgemm_csr *A, const spgemm_csr
 
 int spgemm_plan_create_tuned(spgemm_plan_t *out, const spgemm_csr *A, const spgemm_csr *B, int dtype,
                              unsigned flags, void *stream, const spgemm_tuning *tuning) {
+  NvtxRange nvtx("spgemm_plan_create");
   if (!out) return SPGEMM_ERR_INVALID_ARGUMENT;
   *out = nullptr;
   g_last_error.clear();
   if (tuning) {
     const int g = tuning->lanes_per_entry;
     if ((g != 0 && g != 4 && g != 8 && g != 16 && g != 32) || tuning->reserved != 0 ||
-        tuning->bitmap_min_bound < -1) {
-      set_last_error("tuning: lanes_per_entry must be 0, 4, 8, 16 or 32 and bitmap_min_bound >= -1");
+        tuning->bitmap_min_bound < -1 || tuning->max_nnz_c < 0 || tuning->max_nnz_c > INT32_MAX) {
+      set_last_error("tuning: lanes_per_entry must be 0, 4, 8, 16 or 32, bitmap_min_bound >= -1 and "
+                     "0 <= max_nnz_c <= 2^31-1");
       return SPGEMM_ERR_INVALID_ARGUMENT;
     }
   }
   if (!valid_csr_desc(A) || !valid_csr_desc(B) || A->ncols != B->nrows) return SPGEMM_ERR_INVALID_ARGUMENT;
   if (dtype != SPGEMM_I64 && dtype != SPGEMM_F32 && dtype != SPGEMM_F64) return SPGEMM_ERR_INVALID_ARGUMENT;
-  if (flags & ~(SPGEMM_SORTED | SPGEMM_VALIDATE | SPGEMM_TIMING | SPGEMM_SERIAL | SPGEMM_PROBE_CHUNK4))
+  if (flags & ~(SPGEMM_SORTED | SPGEMM_VALIDATE | SPGEMM_TIMING | SPGEMM_SERIAL | SPGEMM_PROBE_CHUNK4 |
+                SPGEMM_COUNT_PROBES | SPGEMM_HASH_LOW_BITS))
     return SPGEMM_ERR_INVALID_ARGUMENT;
 
   int dev = 0;
@@ -647,6 +651,7 @@ int spgemm_plan_create_tuned(spgemm_plan_t *out, const spgemm_csr *A, const spge
   p->G = 32;  // set from the flop pass below
   p->tune_G = tuning ? tuning->lanes_per_entry : 0;
   p->tune_bm_min = tuning ? tuning->bitmap_min_bound : 0;
+  p->max_nnz_c = tuning && tuning->max_nnz_c > 0 ? tuning->max_nnz_c : INT32_MAX;
   p->bitmap_ok = p->k <= kBitmapMaxCols;
   p->bm_words = (int)((p->k + 31) / 32);
   // bitmap classes: 3, 2 and 1 blocks per SM (228 KB per SM, 1 KB per block kept by the system)
@@ -764,6 +769,7 @@ int spgemm_plan_create_tuned(spgemm_plan_t *out, const spgemm_csr *A, const spge
 }
 
 int spgemm_symbolic(spgemm_plan_t p, int32_t *c_row_ptr, int64_t *nnz_c) {
+  NvtxRange nvtx("spgemm_symbolic");
   if (!p || !c_row_ptr || !nnz_c) return SPGEMM_ERR_INVALID_ARGUMENT;
   if (p->state != 0) return SPGEMM_ERR_BAD_STATE;
   g_last_error.clear();
@@ -783,7 +789,7 @@ int spgemm_symbolic(spgemm_plan_t p, int32_t *c_row_ptr, int64_t *nnz_c) {
     }
     {
       KernelScope ks(p, "scan_spine");
-      k_scan_spine<<<1, kScanThreads, 0, p->stream>>>(partial, nblk, p->dc);
+      k_scan_spine<<<1, kScanThreads, 0, p->stream>>>(partial, nblk, p->max_nnz_c, p->dc);
     }
     {
       KernelScope ks(p, "scan_apply");
@@ -828,6 +834,7 @@ int spgemm_symbolic(spgemm_plan_t p, int32_t *c_row_ptr, int64_t *nnz_c) {
 }
 
 int spgemm_numeric(spgemm_plan_t p, const int32_t *c_row_ptr, int32_t *c_col_idx, void *c_vals) {
+  NvtxRange nvtx("spgemm_numeric");
   if (!p || !c_row_ptr) return SPGEMM_ERR_INVALID_ARGUMENT;
   if (p->state != 1) return SPGEMM_ERR_BAD_STATE;
   if (p->nnz_c > 0 && (!c_col_idx || !c_vals)) return SPGEMM_ERR_INVALID_ARGUMENT;
@@ -930,6 +937,15 @@ int spgemm_plan_stats(spgemm_plan_t p, spgemm_stats *s) {
   s->total_flop = p->total_flop;
   s->max_row_flop = p->max_flop;
   s->nnz_c = p->nnz_c;
+  {
+    long long acc[4] = {0, 0, 0, 0};
+    for (int r = 0; r < 4; ++r)
+      for (int j = 0; j < kProbeSlots; ++j) acc[r] += (long long)p->hc->probe_stats[r][j];
+    s->sym_probes = acc[0];
+    s->sym_inserts = acc[1];
+    s->num_probes = acc[2];
+    s->num_inserts = acc[3];
+  }
   s->n_sym_bins = kNumSymBins;
   s->n_num_bins = kNumNumBins;
   for (int b = 0; b < kNumSymBins; ++b) {

@@ -23,15 +23,41 @@ namespace sg {
 constexpr int kU = 4;  // B entries loaded ahead per lane
 
 // Inserts key c into an S-slot table; returns 1 when c was new.
+// Every variant of the insert: chunked or linear probing, either hash,
+// optional probe counting.  Only ablations and measurement runs take it.
+// (Measured: an out-of-line call here, never taken, still slowed the default
+// path of the warp bins by 5%, so it stays inline.)
 template <bool GLOBAL_MEM>
-__device__ __forceinline__ int insert_key(int32_t *tab, uint32_t mask, int32_t c, uint32_t *err, int probe) {
-  if (probe) {
+__device__ __forceinline__ int insert_key_any(int32_t *tab, uint32_t mask, int32_t c, uint32_t *err, int probe,
+                                           unsigned long long *ctr) {
+  if (probe & kProbeChunk) {
     bool fresh = false;
-    chunk_find_or_claim<GLOBAL_MEM>(tab, mask, c, &fresh, err);
+    unsigned probes = 0;
+    chunk_find_or_claim<GLOBAL_MEM>(tab, mask, c, &fresh, err, &probes, probe & kProbeHashHi);
+    count_probes(ctr, probes);
     return fresh ? 1 : 0;
   }
-  uint32_t h = hash_slot(c, mask);
+  uint32_t h = hash_slot(c, mask, probe & kProbeHashHi);
   for (uint32_t probe = 0; probe <= mask; ++probe) {
+    const int32_t old = atomicCAS(tab + h, kEmpty, c);
+    if (old == kEmpty || old == c) {
+      count_probes(ctr, probe + 1);
+      return old == kEmpty ? 1 : 0;
+    }
+    h = (h + 1) & mask;
+  }
+  raise_err(err, kErrProbe);
+  return 0;
+}
+
+// Inserts key c; returns 1 when c was new.  The default plan (linear
+// probing, top-bits hash, no counting) runs the loop inline.
+template <bool GLOBAL_MEM>
+__device__ __forceinline__ int insert_key(int32_t *tab, uint32_t mask, int32_t c, uint32_t *err, int probe,
+                                          unsigned long long *ctr) {
+  if (probe != kProbeHashHi || ctr) return insert_key_any<GLOBAL_MEM>(tab, mask, c, err, probe, ctr);
+  uint32_t h = hash_slot(c, mask, 1);
+  for (uint32_t q = 0; q <= mask; ++q) {
     const int32_t old = atomicCAS(tab + h, kEmpty, c);
     if (old == kEmpty) return 1;
     if (old == c) return 0;
@@ -59,7 +85,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 8)
   Stage<int32_t> st{s_ent[warp], &s_next[warp], nullptr};
   warp_row_products<kU, false, int32_t>(a.arp[i], a.arp[i + 1], G, a.aci, (const int32_t *)nullptr, a.brp, a.bci,
                                         (const int32_t *)nullptr, (int32_t)a.k, a.err, st,
-                                        [&](int32_t c, int32_t, int32_t) { cnt += insert_key<false>(tab, S - 1, c, a.err, a.probe); });
+                                        [&](int32_t c, int32_t, int32_t) { cnt += insert_key<false>(tab, S - 1, c, a.err, a.probe, a.probe_ctr); });
   cnt = warp_sum(cnt);
   if (lane == 0) nnz_row[i] = cnt;
 }
@@ -86,7 +112,7 @@ __global__ void __launch_bounds__(sym_block_threads<S>(), sym_block_min_blocks<S
   block_row_products<kU, false, int32_t>(a.arp[i], a.arp[i + 1], G, a.aci, (const int32_t *)nullptr,
                                          a.brp, a.bci, (const int32_t *)nullptr, (int32_t)a.k, a.err,
                                          Stage<int32_t>{s_ent, &s_next, s_wsum},
-                                       [&](int32_t c, int32_t, int32_t) { cnt += insert_key<false>(tab, S - 1, c, a.err, a.probe); });
+                                       [&](int32_t c, int32_t, int32_t) { cnt += insert_key<false>(tab, S - 1, c, a.err, a.probe, a.probe_ctr); });
   cnt = block_sum(cnt, red);
   if (threadIdx.x == 0) nnz_row[i] = cnt;
 }
@@ -141,7 +167,7 @@ __global__ void __launch_bounds__(1024, 1)
     block_row_products<kU, false, int32_t>(a.arp[i], a.arp[i + 1], G, a.aci, (const int32_t *)nullptr,
                                          a.brp, a.bci, (const int32_t *)nullptr, (int32_t)a.k, a.err,
                                          Stage<int32_t>{s_ent, &s_next, s_wsum},
-                                         [&](int32_t c, int32_t, int32_t) { cnt += insert_key<true>(tab, mask, c, a.err, a.probe); });
+                                         [&](int32_t c, int32_t, int32_t) { cnt += insert_key<true>(tab, mask, c, a.err, a.probe, a.probe_ctr); });
     cnt = block_sum(cnt, red);
     if (threadIdx.x == 0) nnz_row[i] = cnt;
   }
@@ -183,7 +209,7 @@ static cudaError_t sym_block(spgemm_plan_s *p, cudaStream_t st, const Args &a, c
 
 cudaError_t launch_symbolic(spgemm_plan_s *p) {
   Args a{p->m, p->n, p->k, p->arp, p->aci, p->brp, p->bci, p->av, p->bv, p->G, &p->dc->err,
-         (p->flags & SPGEMM_PROBE_CHUNK4) ? 1 : 0};
+         probe_mode(p->flags), (p->flags & SPGEMM_COUNT_PROBES) ? &p->dc->probe_stats[0][0] : nullptr};
   // heavy bins first, each bin on the next side stream
   static const int order[kNumSymBins] = {kSymBitmapBin, kSymBitmapMidBin, kSymGlobalBin, 9, 8, 7, 6, 5, 4, 3, 2, 1, 0};
   const bool concurrent = use_side_streams(p);

@@ -1,8 +1,10 @@
 """Autotuner: picks a plan's tuning (spgemm_tuning) by timing candidates.
 
-The two decisions a plan exposes are the lanes that share one stored a_ik
-in the block kernels' row loop (G) and the symbolic bound above which rows
-take the column-bitmap path.  Defaults come from rules measured on R-MAT
+The decisions a plan exposes are the lanes that share one stored a_ik in
+the block kernels' row loop (G), the symbolic bound above which rows take
+the column-bitmap path, the hash probing (one slot or chunks of four per
+probe) and the hash (low or high bits of the product); the better choices
+depend on the input's collision factor.  Defaults come from rules measured on R-MAT
 and ER products; `autotune` times a grid of candidates on the caller's own
 product (or a sample batch) with CUDA events and returns the fastest.  The
 result of a product does not depend on the tuning, only its time.
@@ -15,8 +17,14 @@ import torch
 
 from . import binding as sg
 
-DEFAULT_GRID = [{"lanes_per_entry": g, "bitmap_min_bound": b}
-                for g in (0, 8, 16, 32) for b in (0, 512, 2048, 8192, -1)]
+DEFAULT_GRID = [{"lanes_per_entry": g, "bitmap_min_bound": b, "probe": pr, "hash": h}
+                for g in (0, 32) for b in (0, 512, 2048, -1) for pr in ("linear", "chunk4") for h in ("low", "high")]
+
+
+def _split(candidate):
+    """(plan keyword arguments: probe and hash schemes, spgemm_tuning dict) of a candidate."""
+    t = dict(candidate)
+    return {"probe": t.pop("probe", "linear"), "hash": t.pop("hash", "high")}, t
 
 
 def _time(run, steps: int, stream) -> float:
@@ -38,8 +46,10 @@ def autotune(A, B, sorted_output: bool = True, candidates=None, steps: int = 3, 
     stream = stream if stream is not None else torch.cuda.current_stream(A.row_ptr.device)
 
     def run_with(t):
+        kw, tuning = _split(t)
+
         def run():
-            with sg.Plan(A, B, sorted_output, stream=stream, tuning=t) as p:
+            with sg.Plan(A, B, sorted_output, stream=stream, tuning=tuning, **kw) as p:
                 p.symbolic()
                 p.numeric()
         return run
@@ -54,8 +64,10 @@ def autotune_batch(As, Bs, sorted_output: bool = True, candidates=None, steps: i
     stream = stream if stream is not None else torch.cuda.current_stream(As[0].row_ptr.device)
 
     def run_with(t):
+        kw, tuning = _split(t)
+
         def run():
-            with sg.Batch(As, Bs, sorted_output, stream=stream, tuning=t) as b:
+            with sg.Batch(As, Bs, sorted_output, stream=stream, tuning=tuning, **kw) as b:
                 b.symbolic()
                 b.numeric()
         return run

@@ -18,7 +18,8 @@ from paper_1804_01698_gb300.inputs import CSR
 TOL = {torch.float64: 1e-12, torch.float32: 1e-5}
 
 
-def gpu_product(A: CSR, B: CSR, dtype, sorted_output: bool, one_shot: bool = False, probe: str = "linear"):
+def gpu_product(A: CSR, B: CSR, dtype, sorted_output: bool, one_shot: bool = False, probe: str = "linear",
+                hash: str = "high"):
     from paper_1804_01698_gb300 import binding as sg
     dA = sg.to_device(A, "cuda", dtype)
     dB = sg.to_device(B, "cuda", dtype)
@@ -26,7 +27,7 @@ def gpu_product(A: CSR, B: CSR, dtype, sorted_output: bool, one_shot: bool = Fal
         C = sg.spgemm(dA, dB, sorted_output)
         torch.cuda.synchronize()
         return C, None
-    with sg.Plan(dA, dB, sorted_output, probe=probe) as plan:
+    with sg.Plan(dA, dB, sorted_output, probe=probe, hash=hash) as plan:
         plan.symbolic()
         C = plan.numeric()
         stats = plan.stats()

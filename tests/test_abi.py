@@ -72,7 +72,7 @@ def test_argument_validation_before_any_cuda_call(lib):
     assert h.value is None
     b_ok = binding.CsrDesc(3, 3, 0, 16, None, None)
     assert lib.spgemm_plan_create(ctypes.byref(h), ctypes.byref(a), ctypes.byref(b_ok), 7, 1, None) == -1  # dtype
-    assert lib.spgemm_plan_create(ctypes.byref(h), ctypes.byref(a), ctypes.byref(b_ok), 2, 64, None) == -1  # flags
+    assert lib.spgemm_plan_create(ctypes.byref(h), ctypes.byref(a), ctypes.byref(b_ok), 2, 1 << 12, None) == -1  # flags
     neg = binding.CsrDesc(-1, 3, 0, 16, None, None)
     assert lib.spgemm_plan_create(ctypes.byref(h), ctypes.byref(neg), ctypes.byref(b_ok), 2, 1, None) == -1
     nnz_no_ptr = binding.CsrDesc(2, 3, 5, 16, None, None)

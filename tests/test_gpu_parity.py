@@ -381,13 +381,14 @@ def test_heavy_bitmap_row_split_over_blocks(dt, sorted_output):
     assert_matches_oracle(C, A, B, sorted_output)
 
 
+@pytest.mark.parametrize("scheme", [("chunk4", "low"), ("linear", "low"), ("chunk4", "high")])
 @pytest.mark.parametrize("sorted_output", [True, False])
 @pytest.mark.parametrize("dt", ["f64", "i64"])
 @pytest.mark.parametrize("shape", ["rmat12", "er", "global"])
-def test_chunked_probing_gives_the_same_product(shape, dt, sorted_output):
-    """SPGEMM_PROBE_CHUNK4 (4-slot chunks, Sec. 4.2.2) in every kind of hash
-    table: warp and block tables in shared memory (R-MAT, ER) and global
-    tables (B with 2^20 columns)."""
+def test_chunked_probing_gives_the_same_product(shape, dt, sorted_output, scheme):
+    """SPGEMM_PROBE_CHUNK4 (4-slot chunks, Sec. 4.2.2) and SPGEMM_HASH_LOW_BITS
+    (the remainder form of Sec. 4.2.1) in every kind of hash table: warp and block tables in shared memory
+    (R-MAT, ER) and global tables (B with 2^20 columns)."""
     dtype = DT[dt]
     if shape == "rmat12":
         A = B = inputs.rmat(12, 16, seed=81)
@@ -399,7 +400,7 @@ def test_chunked_probing_gives_the_same_product(shape, dt, sorted_output):
     if dt != "f64":
         A, B = int_valued(A, 85), int_valued(B, 86)
     A, B = host_vals(A, dtype), host_vals(B, dtype)
-    C, st = gpu_product(A, B, dtype, sorted_output, probe="chunk4")
+    C, st = gpu_product(A, B, dtype, sorted_output, probe=scheme[0], hash=scheme[1])
     assert st["status"] == 0
     if shape == "global":
         assert st["sym_bin_rows"][12] == 5 and st["num_bin_rows"][10] >= 5

@@ -51,7 +51,7 @@ def test_autotune_returns_a_candidate():
     from paper_1804_01698_gb300.tune import autotune, autotune_batch
     dA = sg.to_device(inputs.rmat(11, 16, seed=113))
     cands = [{"lanes_per_entry": 0, "bitmap_min_bound": 0}, {"lanes_per_entry": 16, "bitmap_min_bound": 2048},
-             {"lanes_per_entry": 32, "bitmap_min_bound": -1}]
+             {"lanes_per_entry": 32, "bitmap_min_bound": -1, "probe": "chunk4", "hash": "low"}]
     best, table = autotune(dA, dA, True, candidates=cands, steps=2)
     assert best in cands and len(table) == 3 and all(ms > 0 for _, ms in table)
     mats = [sg.to_device(m) for m in inputs.er_batch(6, seed=114, n_hi=3000)]
