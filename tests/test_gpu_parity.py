@@ -430,3 +430,44 @@ def test_block_bins_below_the_bitmap_threshold(dt, sorted_output):
     assert all(st["num_bin_rows"][b] > 0 for b in (5, 6, 7))
     assert st["sym_bin_rows"][11] > 0                      # the rows of bound 8000
     assert_matches_oracle(C, A, B, sorted_output)
+
+
+@pytest.mark.parametrize("sorted_output", [True, False])
+@pytest.mark.parametrize("dt", ["f64", "i64"])
+def test_duplicate_columns_in_input_rows_are_summed(dt, sorted_output):
+    """Duplicate columns inside an input row break the CSR precondition; both
+    the oracle and the GPU sum them (a repeated a_ik repeats its products, a
+    repeated b_kj adds twice into one output column).  Light rows (hash
+    tables) and heavy rows (bitmaps) both see duplicates."""
+    rng = np.random.default_rng(131)
+    n, k = 400, 3000
+
+    def with_dups(m, ncols, seed):
+        r = np.random.default_rng(seed)
+        rows, cols = [], []
+        for i in range(m.nrows):
+            cs = m.col_idx[m.row_ptr[i]:m.row_ptr[i + 1]].tolist()
+            if cs and i % 3 == 0:
+                cs = cs + r.choice(cs, size=max(1, len(cs) // 4)).tolist()   # repeat some columns
+            rows += [i] * len(cs)
+            cols += cs
+        order = np.lexsort((np.array(cols), np.array(rows)))
+        rp = np.zeros(m.nrows + 1, np.int32)
+        np.add.at(rp, np.array(rows)[order] + 1, 1)
+        return CSR(m.nrows, ncols, np.cumsum(rp).astype(np.int32), np.array(cols, np.int32)[order],
+                   r.uniform(-1, 1, len(cols)))
+
+    A = with_dups(inputs.er_exact(n, 6, seed=132, ncols=n), n, 133)
+    heavy = np.zeros(n, bool)
+    heavy[:5] = True                                  # five rows of A reach every row of B
+    rp = np.concatenate([[0], np.cumsum(np.where(heavy, n, np.diff(A.row_ptr)))]).astype(np.int32)
+    ci = np.concatenate([np.arange(n) if heavy[i] else A.col_idx[A.row_ptr[i]:A.row_ptr[i + 1]] for i in range(n)])
+    A = CSR(n, n, rp, ci.astype(np.int32), rng.uniform(-1, 1, len(ci)))
+    B = with_dups(inputs.er_exact(n, 30, seed=134, ncols=k), k, 135)
+    if dt != "f64":
+        A, B = int_valued(A, 136), int_valued(B, 137)
+    A, B = host_vals(A, DT[dt]), host_vals(B, DT[dt])
+    C, st = gpu_product(A, B, DT[dt], sorted_output)
+    assert st["status"] == 0
+    assert st["sym_bin_rows"][10] + st["sym_bin_rows"][11] >= 5     # the heavy rows took bitmaps
+    assert_matches_oracle(C, A, B, sorted_output)

@@ -415,3 +415,37 @@ def test_degree_order_and_split():
     lt = sorted(zip(L.col_idx.tolist(), np.repeat(np.arange(L.nrows), np.diff(L.row_ptr)).tolist()))
     ut = list(zip(np.repeat(np.arange(U.nrows), np.diff(U.row_ptr)).tolist(), U.col_idx.tolist()))
     assert lt == ut
+
+
+def test_duplicate_columns_are_summed_like_the_dense_product():
+    """Duplicate columns inside input rows (a precondition violation) are
+    summed: the result equals the dense product of the duplicate-summed
+    matrices, and each output column appears once."""
+    rng = np.random.default_rng(141)
+    for _ in range(20):
+        m, n, k = rng.integers(1, 12, 3)
+        rows = rng.integers(0, m, 40)
+        A = CSR(int(m), int(n), *_coo_to_csr(int(m), rows, rng.integers(0, n, 40)), rng.integers(-3, 4, 40).astype(np.int64))
+        rows = rng.integers(0, n, 40)
+        B = CSR(int(n), int(k), *_coo_to_csr(int(n), rows, rng.integers(0, k, 40)), rng.integers(-3, 4, 40).astype(np.int64))
+        C, _ = oracle.spgemm(A, B)
+        assert np.array_equal(_dense(C), _dense(A) @ _dense(B))
+        for i in range(C.nrows):
+            cs = C.col_idx[C.row_ptr[i]:C.row_ptr[i + 1]]
+            assert len(set(cs.tolist())) == len(cs)
+
+
+def _coo_to_csr(m, rows, cols):
+    """Row pointers and columns of (row, col) pairs kept with repeats, rows in order."""
+    order = np.argsort(rows, kind="stable")
+    rp = np.zeros(m + 1, np.int32)
+    np.add.at(rp, rows + 1, 1)
+    return np.cumsum(rp).astype(np.int32), cols[order].astype(np.int32)
+
+
+def _dense(M):
+    d = np.zeros((M.nrows, M.ncols), dtype=np.int64)
+    for i in range(M.nrows):
+        for j in range(M.row_ptr[i], M.row_ptr[i + 1]):
+            d[i, M.col_idx[j]] += M.vals[j]
+    return d
