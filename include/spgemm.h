@@ -5,7 +5,7 @@
  * Gustavson's row-wise algorithm (paper Sec. 2, Fig. "RowWise_SpGEMM"):
  * row i of C accumulates a_ik * b_k* over the stored a_ik of row i of A,
  * in a hash table keyed by column index (Sec. 4.2.1).  The work runs in two
- * phases (Sec. 2, "two-phase method"; Sec. 4.2.1, Fig. "Hash_SpGEMM"):
+ * phases (the two-phase approach of Sec. 2; Sec. 4.2.1, Fig. "Hash_SpGEMM"):
  * a symbolic phase counts the entries of every output row so that C can be
  * allocated exactly, then a numeric phase computes the values.
  *
@@ -32,11 +32,11 @@
  *
  * Layout: CSR, 0-based, int32 row_ptr (nrows+1 entries) and col_idx.
  * Column indices inside an input row may be in any order (Table
- * "Summary of SpGEMM codes": Hash accepts any input order) but must be
- * distinct.  Values are int64, float or double (spgemm_dtype); A, B and C
+ * "Summary of SpGEMM codes": Hash accepts any input order) and should be
+ * distinct; a column repeated within a row is summed like separate entries.  Values are int64, float or double (spgemm_dtype); A, B and C
  * share one value type.  Output rows are column-sorted when flags has
- * SPGEMM_SORTED, otherwise their order is unspecified (Sec. 4.2.1: the
- * results are sorted "if necessary").
+ * SPGEMM_SORTED, otherwise their order is unspecified (Sec. 4.2.1 makes the
+ * sort an optional last step of the numeric phase).
  *
  * Arithmetic: plus-times.  int64 wraps modulo 2^64.  Floating-point sums
  * are taken in an unspecified order (atomic accumulation), so results may
@@ -181,8 +181,8 @@ SPGEMM_API int spgemm_plan_create_tuned(spgemm_plan_t *out, const spgemm_csr *A,
                                         unsigned flags, void *stream, const spgemm_tuning *tuning);
 
 /*
- * Symbolic phase (Sec. 4.2.1: "it is enough to insert keys to the hash
- * table"): counts the distinct columns of every output row, writes the
+ * Symbolic phase (Sec. 4.2.1: only keys, no values, go into the hash
+ * table): counts the distinct columns of every output row, writes the
  * exclusive prefix sum to c_row_ptr (device, m+1 int32, caller-owned) and
  * returns nnz(C) in *nnz_c (host).  Synchronises the stream once.  Returns
  * SPGEMM_ERR_INDEX_OVERFLOW if nnz(C) > 2^31-1.

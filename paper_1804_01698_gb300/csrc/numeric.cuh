@@ -1,6 +1,6 @@
 // Numeric phase (paper Sec. 4.2.1; Fig. "Hash_SpGEMM", step Numeric): the
 // keys are inserted again and a_ik*b_kj is added to the value of the key's
-// slot; the finished row is then stored, sorted by column "if necessary".
+// slot; the finished row is then stored, sorted by column when requested.
 //
 //   k_num_warp<T,S>   one warp per row, S-slot table (keys + values) in smem
 //   k_num_block<T,S>  one block per row, S-slot table in smem

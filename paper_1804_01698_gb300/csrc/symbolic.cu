@@ -1,5 +1,5 @@
-// Symbolic phase (paper Sec. 4.2.1: "it is enough to insert keys to the
-// hash table"): nnz(c_i*) = number of distinct keys inserted for row i.
+// Symbolic phase (paper Sec. 4.2.1: only keys, no values, go into the hash
+// table): nnz(c_i*) = number of distinct keys inserted for row i.
 //
 //   k_sym_warp<S>    one warp per row, S-slot table in shared memory
 //   k_sym_block<S>   one block per row, S-slot table in shared memory
