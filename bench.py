@@ -136,11 +136,18 @@ class ClockSampler:
 
 
 def source_digest() -> str:
+    """Digest of the kernel sources with comments and blank space removed, so
+    that edits to comments do not mark committed counters as stale."""
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1804_01698_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, name), "rb") as f:
-            h.update(name.encode() + f.read())
+        with open(os.path.join(csrc, name), encoding="utf-8") as f:
+            code = f.read()
+        code = re.sub(r"/\*.*?\*/", " ", code, flags=re.S)
+        code = re.sub(r"//[^\n]*", " ", code)
+        code = " ".join(code.split())
+        h.update(name.encode() + code.encode())
     return h.hexdigest()[:16]
 
 
