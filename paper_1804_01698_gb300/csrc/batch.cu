@@ -288,6 +288,11 @@ int spgemm_batch_create_tuned(spgemm_batch_t *out, int64_t nprod, const spgemm_c
     delete b;
     return rc;
   }
+  // a row of the packed C spans at most its own product's columns: the block
+  // bins' sort window is sized from the widest product, not the packed k
+  int64_t widest = 0;
+  for (int64_t q = 0; q < nprod; ++q) widest = B[q].ncols > widest ? B[q].ncols : widest;
+  b->plan->span_cols = widest;
   b->state = 0;
   *out = b;
   return SPGEMM_OK;

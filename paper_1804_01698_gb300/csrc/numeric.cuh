@@ -771,7 +771,7 @@ static cudaError_t num_block(spgemm_plan_s *p, cudaStream_t st, const Args &a, c
   int mode = 0;
   // sorted output: rank by a bitmap over each row's column window of up to
   // kSortWindowWords x 32 columns (the whole of B's columns when they fit)
-  const int words = (int)std::min<int64_t>(p->bm_words, kSortWindowWords);
+  const int words = (int)std::min<int64_t>((p->span_cols + 31) / 32, kSortWindowWords);
   if (p->flags & SPGEMM_SORTED) {
     const size_t extra = (size_t)words * 8;
     if (smem + extra + kStaticSmemReserve <= (size_t)max_smem_per_block()) {

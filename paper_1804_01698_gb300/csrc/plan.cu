@@ -652,6 +652,7 @@ int spgemm_plan_create_tuned(spgemm_plan_t *out, const spgemm_csr *A, const spge
   p->tune_G = tuning ? tuning->lanes_per_entry : 0;
   p->tune_bm_min = tuning ? tuning->bitmap_min_bound : 0;
   p->max_nnz_c = tuning && tuning->max_nnz_c > 0 ? tuning->max_nnz_c : INT32_MAX;
+  p->span_cols = p->k;
   p->bitmap_ok = p->k <= kBitmapMaxCols;
   p->bm_words = (int)((p->k + 31) / 32);
   // bitmap classes: 3, 2 and 1 blocks per SM (228 KB per SM, 1 KB per block kept by the system)

@@ -315,7 +315,7 @@ def test_out_of_range_column_is_an_error_not_a_fault(where):
 def test_block_rows_wider_than_the_sort_window(sorted_output):
     # ~1200 products per row: block bins.  B has 2^20 columns and half of each
     # row's entries spread over all of them, so every row of C spans far more
-    # than the 65536-column window of the bitmap sort: the bitonic fallback.
+    # than the 131072-column window of the bitmap sort: the bitonic fallback.
     A = inputs.er_exact(300, 30, seed=121, ncols=400)
     B1 = inputs.er_exact(400, 40, seed=122, ncols=1 << 20)
     narrow = inputs.er_exact(400, 40, seed=123, ncols=3000)
