@@ -59,11 +59,11 @@ extern const BinCfg kSymBins[kNumSymBins];
 // Numeric bins 0..8: tables 64 .. 16384 slots, same load factors.
 extern const BinCfg kNumBins[kNumNumBins];
 
-// Rows whose symbolic bound exceeds kBitmapMinBound use a column bitmap
-// when B has at most kBitmapMaxCols columns: the symbolic phase builds and
-// saves the bitmap, the numeric phase turns it into output positions.
-// Without bitmaps, rows above the largest shared-memory table (3/4 of 32768
-// keys) use global-memory hash tables.
+// Rows whose symbolic bound exceeds bitmap_min_bound(k) (at least
+// kBitmapMinBound) use a column bitmap when B has at most kBitmapMaxCols
+// columns: the symbolic phase builds and saves the bitmap, the numeric phase
+// turns it into output positions.  Without bitmaps, rows above the largest
+// shared-memory table (3/4 of 32768 keys) use global-memory hash tables.
 constexpr int64_t kBitmapMinBound = 512;
 
 constexpr int64_t kBitmapMidMax = 24576;

@@ -4,12 +4,15 @@
 //
 //   k_num_warp<T,S>   one warp per row, S-slot table (keys + values) in smem
 //   k_num_block<T,S>  one block per row, S-slot table in smem
-//   k_num_bitmap<T>   heavy rows with a column bitmap saved by the symbolic
-//                     phase: the rank of column j among the row's columns is
-//                     its output position, so values accumulate in a dense
-//                     array indexed by rank and come out sorted.  A row with
-//                     more entries than fit in shared memory is split into
-//                     windows of consecutive ranks (one block each).
+//   k_num_bitmap<T,NT,MINB>  heavy rows with a column bitmap saved by the
+//                     symbolic phase: the rank of column j among the row's
+//                     columns is its output position, so values accumulate in
+//                     a dense array indexed by rank and come out sorted.  A
+//                     row with more entries than fit in shared memory is
+//                     split into windows of consecutive ranks, and a row
+//                     with much more flop than output into parts of its
+//                     stored a_ik (one block per window and part); three
+//                     size classes, each with its own launch shape.
 //   k_num_global<T>   heavy rows without bitmaps: hash table in global memory.
 //
 // Tables are sized from the exact row count found by the symbolic phase,

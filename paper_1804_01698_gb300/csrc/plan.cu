@@ -11,7 +11,7 @@
 //                   (Fig. "Hash_SpGEMM": rpts_C is allocated and filled
 //                   between the symbolic and the numeric phase)
 //   k_num_classify  numeric bins from the exact row counts
-//   k_bm_items_*    work items (row, rank window) of heavy bitmap rows
+//   k_bm_items_*    work items (row, rank window, part) of heavy bitmap rows
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
