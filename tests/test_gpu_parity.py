@@ -471,3 +471,37 @@ def test_duplicate_columns_in_input_rows_are_summed(dt, sorted_output):
     assert st["status"] == 0
     assert st["sym_bin_rows"][10] + st["sym_bin_rows"][11] >= 5     # the heavy rows took bitmaps
     assert_matches_oracle(C, A, B, sorted_output)
+
+
+def test_product_with_more_than_2_31_flop():
+    """R-MAT scale 18 A*A: total flop 2.9e9 (beyond int32), about 1e9 output
+    entries, B at the bitmap column limit (2^18).  Every row count is
+    compared with the oracle's symbolic phase, and 300 sampled rows (the
+    heaviest among them) entry by entry."""
+    from paper_1804_01698_gb300 import binding as sg
+    A = inputs.rmat(18, 16, seed=141)
+    flop = oracle.row_flop(A, A)
+    assert int(flop.sum()) > 2**31
+    dA = sg.to_device(A)
+    with sg.Plan(dA, dA, True) as plan:
+        nnz = plan.symbolic()
+        C = plan.numeric()
+        st = plan.stats()
+    torch.cuda.synchronize()
+    assert st["status"] == 0
+    assert st["total_flop"] == int(flop.sum())
+    expect_rows = oracle.symbolic(A, A, nthreads=os.cpu_count() or 8)
+    rp = C.row_ptr.cpu().numpy()
+    assert np.array_equal(np.diff(rp), expect_rows)
+    assert nnz == int(expect_rows.sum())
+    rng = np.random.default_rng(142)
+    sample = np.unique(np.concatenate([np.argsort(flop)[-20:], rng.choice(A.nrows, 280, replace=False)]))
+    ref, absb = oracle.spgemm_rows(A, A, sample, nthreads=os.cpu_count() or 8)
+    for t, i in enumerate(sample):
+        lo, hi = int(rp[i]), int(rp[i + 1])
+        r0, r1 = int(ref.row_ptr[t]), int(ref.row_ptr[t + 1])
+        assert hi - lo == r1 - r0
+        ci = C.col_idx[lo:hi].cpu().numpy()
+        cv = C.vals[lo:hi].cpu().numpy()
+        assert np.array_equal(ci, ref.col_idx[r0:r1])
+        assert np.all(np.abs(cv - ref.vals[r0:r1]) <= 1e-12 * absb[r0:r1])
