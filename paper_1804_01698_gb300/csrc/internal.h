@@ -90,6 +90,18 @@ constexpr long long kSplitMinFlop = 65536;
 constexpr long long kSplitFlopPerEntry = 8;
 constexpr long long kSplitMaxParts = 64;
 
+// The symbolic phase of a heavy bitmap row (bin kSymBitmapBin) is split the
+// same way when its flop reaches kSymSplitFlop: one part per kSymSplitFlop
+// products, each ORing its partial bitmap into the row's saved bitmap; the
+// last part to finish counts it.
+constexpr long long kSymSplitFlop = 131072;
+__host__ __device__ inline int sym_split_parts(long long flop) {
+  long long parts = flop / kSymSplitFlop;
+  if (parts < 1) parts = 1;
+  if (parts > kSplitMaxParts) parts = kSplitMaxParts;
+  return (int)parts;
+}
+
 __host__ __device__ inline int bm_split_parts(long long flop, long long nnz) {
   const long long unit = kSplitMinFlop > kSplitFlopPerEntry * nnz ? kSplitMinFlop : kSplitFlopPerEntry * nnz;
   long long parts = flop / unit;
@@ -119,6 +131,8 @@ struct DevCounters {
   unsigned long long bm_items[3];       // numeric bitmap work items per class (small, medium, large)
   unsigned long long bm_cursor[3];
   unsigned long long bm_flop[3];        // flop of the rows of each class
+  unsigned long long sym_split_extra;   // heavy symbolic bitmap rows: parts beyond one per row
+  unsigned long long sym_item_cursor;
   // SPGEMM_COUNT_PROBES: rows 0/1 symbolic probes/inserts, 2/3 numeric,
   // each spread over kProbeSlots counters to limit atomic contention
   unsigned long long probe_stats[4][kProbeSlots];
@@ -188,6 +202,9 @@ struct spgemm_plan_s {
   uint32_t *bitmaps;  // one bitmap per row of the symbolic bitmap bin
   size_t bitmaps_bytes;
   int4 *bm_items;     // numeric bitmap work items (bitmap index, window, part, parts)
+  int4 *sym_items;    // split heavy symbolic rows: work items (index in the bin, part, parts)
+  unsigned *sym_tickets;  // per heavy symbolic row: parts finished
+  int64_t n_sym_items;
   size_t bm_items_bytes;
   void *gtab;         // global hash tables (heavy rows without bitmaps)
   size_t gtab_bytes;

@@ -85,12 +85,12 @@ __global__ void __launch_bounds__(256)
                uint8_t *__restrict__ rbin, int32_t *__restrict__ nnz_row, DevCounters *dc) {
   __shared__ unsigned int hist[kNumSymBins];
   __shared__ unsigned long long hflop[kNumSymBins];
-  __shared__ unsigned long long s_tot, s_max, s_maxg;
+  __shared__ unsigned long long s_tot, s_max, s_maxg, s_extra;
   if (threadIdx.x < kNumSymBins) {
     hist[threadIdx.x] = 0;
     hflop[threadIdx.x] = 0;
   }
-  if (threadIdx.x == 0) s_tot = s_max = s_maxg = 0;
+  if (threadIdx.x == 0) s_tot = s_max = s_maxg = s_extra = 0;
   __syncthreads();
   const int sub = threadIdx.x & 31;
   const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -136,6 +136,7 @@ __global__ void __launch_bounds__(256)
       atomicAdd(&hflop[bin], (unsigned long long)f);
     }
     if (bin == kSymGlobalBin) atomicMax(&s_maxg, (unsigned long long)bound);
+    if (bin == kSymBitmapBin && sym_split_parts(f) > 1) atomicAdd(&s_extra, (unsigned long long)(sym_split_parts(f) - 1));
     atomicAdd(&s_tot, (unsigned long long)f);
     atomicMax(&s_max, (unsigned long long)f);
   }
@@ -146,6 +147,7 @@ __global__ void __launch_bounds__(256)
   }
   if (threadIdx.x == 0) {
     if (s_tot) atomicAdd(&dc->total_flop, s_tot);
+    if (s_extra) atomicAdd(&dc->sym_split_extra, s_extra);
     atomicMax(&dc->max_flop, s_max);
     atomicMax(&dc->max_bound_global, s_maxg);
   }
@@ -542,10 +544,13 @@ void free_ws(spgemm_plan_s *p) {
   if (p->ws_fixed) cudaFreeAsync(p->ws_fixed, p->stream);
   if (p->bitmaps) cudaFreeAsync(p->bitmaps, p->stream);
   if (p->bm_items) cudaFreeAsync(p->bm_items, p->stream);
+  if (p->sym_items) cudaFreeAsync(p->sym_items, p->stream);
   if (p->gtab) cudaFreeAsync(p->gtab, p->stream);
   p->ws_fixed = nullptr;
   p->bitmaps = nullptr;
   p->bm_items = nullptr;
+  p->sym_items = nullptr;
+  p->sym_tickets = nullptr;
   p->gtab = nullptr;
 }
 

@@ -17,6 +17,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "rowsplit.cuh"
 
 namespace sg {
 
@@ -120,31 +121,76 @@ __global__ void __launch_bounds__(sym_block_threads<S>(), sym_block_min_blocks<S
 // Heavy rows with a bitmap over the columns of B.  words = ceil(k / 32).
 template <int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
-    k_sym_bitmap(Args a, const int32_t *__restrict__ rows, int32_t *__restrict__ nnz_row,
-                 uint32_t *__restrict__ bitmaps, int words) {
+    k_sym_bitmap(Args a, const int32_t *__restrict__ rows, const int4 *__restrict__ items,
+                 int32_t *__restrict__ nnz_row, uint32_t *__restrict__ bitmaps, int words,
+                 unsigned *__restrict__ tickets) {
   extern __shared__ uint32_t sm_bm[];
   __shared__ int red[33];
   __shared__ Entry<int32_t> s_ent[kStageN];
   __shared__ long long s_wsum[8];
   __shared__ int s_next;
+  __shared__ int s_last;
+  // block b is row b of the bin, or, for split rows, work item b (row t of
+  // the bin, part `part` of `parts`)
+  int t = blockIdx.x, part = 0, parts = 1;
+  if (items) {
+    const int4 it = items[blockIdx.x];
+    t = it.x;
+    part = it.y;
+    parts = it.z;
+  }
   for (int w = threadIdx.x; w < words; w += blockDim.x) sm_bm[w] = 0u;
+  const int32_t i = rows[t];
+  int32_t j_lo = a.arp[i], j_hi = a.arp[i + 1];
+  if (parts > 1) part_range(a, i, part, parts, &j_lo, &j_hi);
   __syncthreads();
-  const int32_t i = rows[blockIdx.x];
   const int G = a.G;
-  block_row_products<kU, false, int32_t>(a.arp[i], a.arp[i + 1], G, a.aci, (const int32_t *)nullptr,
+  block_row_products<kU, false, int32_t>(j_lo, j_hi, G, a.aci, (const int32_t *)nullptr,
                                          a.brp, a.bci, (const int32_t *)nullptr, (int32_t)a.k, a.err,
                                          Stage<int32_t>{s_ent, &s_next, s_wsum},
                                        [&](int32_t c, int32_t, int32_t) { atomicOr(sm_bm + (c >> 5), 1u << (c & 31)); });
   __syncthreads();
-  int cnt = 0;
-  uint32_t *out = bitmaps + (size_t)blockIdx.x * words;
+  uint32_t *out = bitmaps + (size_t)t * words;
+  if (parts == 1) {
+    int cnt = 0;
+    for (int w = threadIdx.x; w < words; w += blockDim.x) {
+      const uint32_t b = sm_bm[w];
+      out[w] = b;
+      cnt += __popc(b);
+    }
+    cnt = block_sum(cnt, red);
+    if (threadIdx.x == 0) nnz_row[i] = cnt;
+    return;
+  }
+  // a part ORs its bits into the row's bitmap (zeroed before the launch);
+  // the last part to finish counts the union
   for (int w = threadIdx.x; w < words; w += blockDim.x) {
     const uint32_t b = sm_bm[w];
-    out[w] = b;
-    cnt += __popc(b);
+    if (b) atomicOr(out + w, b);
   }
-  cnt = block_sum(cnt, red);
-  if (threadIdx.x == 0) nnz_row[i] = cnt;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(tickets + t, 1u) == (unsigned)(parts - 1);
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    int cnt = 0;
+    for (int w = threadIdx.x; w < words; w += blockDim.x) cnt += __popc(__ldcg(out + w));
+    cnt = block_sum(cnt, red);
+    if (threadIdx.x == 0) nnz_row[i] = cnt;
+  }
+}
+
+// Work items of the split heavy bitmap rows: row t of the bin (rows[t]) gets
+// sym_split_parts(flop) items (t, part, parts).
+__global__ void __launch_bounds__(256)
+    k_sym_items_fill(const int32_t *__restrict__ rows, int64_t n, const int64_t *__restrict__ flop, DevCounters *dc,
+                     int4 *__restrict__ items) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int parts = sym_split_parts(flop[rows[t]]);
+  const unsigned long long base = atomicAdd(&dc->sym_item_cursor, (unsigned long long)parts);
+  for (int q = 0; q < parts; ++q) items[base + q] = make_int4((int)t, q, parts, 0);
 }
 
 // Heavy rows, hash table in global memory: block b owns tables[b*S .. b*S+S)
@@ -213,7 +259,33 @@ cudaError_t launch_symbolic(spgemm_plan_s *p) {
   // heavy bins first, each bin on the next side stream
   static const int order[kNumSymBins] = {kSymBitmapBin, kSymBitmapMidBin, kSymGlobalBin, 9, 8, 7, 6, 5, 4, 3, 2, 1, 0};
   const bool concurrent = use_side_streams(p);
-  cudaError_t e = concurrent ? fork(p) : cudaSuccess;
+  cudaError_t e = cudaSuccess;
+  // split heavy bitmap rows: work items, zeroed tickets and bitmaps (on the
+  // plan's stream, before the side streams fork from it)
+  const int64_t nheavy = p->sym_count[kSymBitmapBin];
+  const int64_t extra = (int64_t)p->hc->sym_split_extra;
+  p->n_sym_items = 0;
+  if (nheavy > 0 && extra > 0) {
+    const int64_t n_items = nheavy + extra;
+    const size_t items_bytes = ((size_t)n_items * sizeof(int4) + 255) / 256 * 256;
+    e = cudaMallocAsync((void **)&p->sym_items, items_bytes + (size_t)nheavy * sizeof(unsigned), p->stream);
+    if (e != cudaSuccess) {
+      p->sym_items = nullptr;
+      return e;
+    }
+    p->sym_tickets = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(p->sym_items) + items_bytes);
+    e = cudaMemsetAsync(p->sym_tickets, 0, (size_t)nheavy * sizeof(unsigned), p->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->bitmaps, 0, (size_t)nheavy * p->bm_words * sizeof(uint32_t), p->stream);
+    if (e == cudaSuccess) {
+      KernelScope ks(p, "sym_items_fill");
+      k_sym_items_fill<<<(unsigned)((nheavy + 255) / 256), 256, 0, p->stream>>>(p->perm + p->sym_off[kSymBitmapBin],
+                                                                                nheavy, p->flop, p->dc, p->sym_items);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return e;
+    p->n_sym_items = n_items;
+  }
+  if (concurrent) e = fork(p);
   int launched = 0;
   for (int o = 0; o < kNumSymBins && e == cudaSuccess; ++o) {
     const int b = order[o];
@@ -246,7 +318,9 @@ cudaError_t launch_symbolic(spgemm_plan_s *p) {
         {
           KernelScope ks(p, b == kSymBitmapBin ? "sym_bitmap_heavy" : "sym_bitmap_mid", st);
           uint32_t *bm = p->bitmaps + (size_t)(p->sym_off[b] - p->sym_off[kSymBitmapBin]) * p->bm_words;
-          kern<<<(unsigned)n, c.threads, smem, st>>>(a, rows, p->nnz_row, bm, p->bm_words);
+          const bool split = b == kSymBitmapBin && p->n_sym_items > 0;
+          kern<<<(unsigned)(split ? p->n_sym_items : n), c.threads, smem, st>>>(
+              a, rows, split ? p->sym_items : nullptr, p->nnz_row, bm, p->bm_words, split ? p->sym_tickets : nullptr);
         }
         e = cudaGetLastError();
         break;

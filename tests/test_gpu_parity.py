@@ -505,3 +505,26 @@ def test_product_with_more_than_2_31_flop():
         cv = C.vals[lo:hi].cpu().numpy()
         assert np.array_equal(ci, ref.col_idx[r0:r1])
         assert np.all(np.abs(cv - ref.vals[r0:r1]) <= 1e-12 * absb[r0:r1])
+
+
+@pytest.mark.parametrize("sorted_output", [True, False])
+@pytest.mark.parametrize("dt", ["f64", "i64"])
+def test_heavy_symbolic_row_split_over_blocks(dt, sorted_output):
+    """A heavy bitmap row (bound 65536) with 600,000 products takes four
+    symbolic blocks: each ORs its part of the row's columns into the saved
+    bitmap and the last one counts them.  Its output (about 65,000 entries)
+    then spans several numeric rank windows."""
+    rng = np.random.default_rng(151)
+    nb, kb = 20000, 1 << 16
+    B = inputs.er_exact(nb, 30, seed=152, ncols=kb)
+    rows = [np.zeros(nb, np.int64)] + [np.full(40 * r, r) for r in range(1, 6)]
+    cols = [np.arange(nb)] + [rng.choice(nb, size=40 * r, replace=False) for r in range(1, 6)]
+    rp, ci = inputs.from_coo(6, nb, np.concatenate(rows), np.concatenate(cols))
+    A = CSR(6, nb, rp, ci, rng.uniform(-1, 1, len(ci)))
+    if dt != "f64":
+        A, B = int_valued(A, 153), int_valued(B, 154)
+    A, B = host_vals(A, DT[dt]), host_vals(B, DT[dt])
+    C, st = gpu_product(A, B, DT[dt], sorted_output)
+    assert st["status"] == 0
+    assert st["sym_bin_rows"][10] == 1 and st["max_row_flop"] == 600000
+    assert_matches_oracle(C, A, B, sorted_output)
