@@ -17,8 +17,9 @@ Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
 Workloads: the named single products of inputs.WORKLOADS (default
 rmat16_ef16_f64; also er4096_k8_f64, rmat18_frontier1024_f32,
 tc_rmat16_lu_f64), batch_er2000 (batched products), serve_mix (serving
-loop), sweep_rmat (density and size sweeps) and ablate_probe (linear vs
-chunked hash probing).
+loop), sweep_rmat (density and size sweeps), ablate_probe (linear vs
+chunked hash probing) and numeric_repeat (repeated numeric phases of one
+structure, plain and as a CUDA graph).
 For N > 1 launch under torch.distributed.run: each rank runs an
 independent replica on its own GPU (weak scaling); timing takes the maximum
 over ranks.
@@ -649,6 +650,88 @@ def run_ablate_probe(args) -> int:
     return 0
 
 
+def run_numeric_repeat(args) -> int:
+    """Repeated products of one structure with new values (as in multigrid
+    setup): the whole product (plan, symbolic, numeric) against the numeric
+    phase alone re-run on the same plan, and replayed as a CUDA graph
+    (spgemm_numeric_graph).  FP64, sorted; values change between steps."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1804_01698_gb300 import binding as sg
+    from paper_1804_01698_gb300 import inputs
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    cases = [("er4096_k8_f64", *inputs.workload("er4096_k8_f64")[:2]),
+             ("amg_poisson7_g48_times_aggregation", inputs.poisson7(48), inputs.aggregation(48)),
+             ("rmat16_ef16_f64", *inputs.workload("rmat16_ef16_f64")[:2])]
+    steps = max(3, args.steps)
+    rows, launches = [], 0
+
+    def timed(fn):
+        fn()
+        ts = []
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    with ClockSampler(0) as clocks:
+        for name, A, B in cases:
+            dA = sg.to_device(A, dev)
+            dB = dA if B is A else sg.to_device(B, dev)
+            gen = torch.Generator(device=dev)
+            gen.manual_seed(7)
+
+            def new_values():
+                dA.vals.uniform_(-1.0, 1.0, generator=gen)
+
+            def whole():
+                new_values()
+                with sg.Plan(dA, dB, True, stream=stream) as p:
+                    p.symbolic()
+                    p.numeric()
+            plan = sg.Plan(dA, dB, True, stream=stream)
+            plan.symbolic()
+            C = plan.numeric()
+
+            def again():
+                new_values()
+                plan.numeric(C.col_idx, C.vals)
+
+            def graph():
+                new_values()
+                plan.numeric_graph(C)
+            t_whole, t_again, t_graph = timed(whole), timed(again), timed(graph)
+            st = plan.stats()
+            launches += st["kernel_launches"]
+            flop = st["total_flop"]
+            plan.destroy()
+            rows.append({"workload": name, "flop": flop, "whole_product_ms": t_whole, "numeric_again_ms": t_again,
+                         "numeric_graph_ms": t_graph, "graph_gflops": 2 * flop / (t_graph * 1e-3) / 1e9})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    head = rows[-1]
+    line = {
+        "metric": "SpGEMM GFLOP/s (2*flop per second)", "value": head["graph_gflops"], "unit": "GFLOP/s",
+        "n_gpus": 1, "steps": steps, "warmup": 1, "ms_per_step": head["numeric_graph_ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "repeated numeric phases of one structure with new A values: ER n=4096 k=8, AMG A*P "
+                               "g=48, R-MAT16 A*A; FP64 sorted; whole product vs numeric re-run vs CUDA-graph replay",
+                   "headline_point": "R-MAT16 graph replay", "l2": "inputs of R-MAT16 larger than L2",
+                   "timing": "median over steps; each step includes drawing new values of A on the device"},
+        "repeat": rows, "e2e": None, "gpu_launches": launches, "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------------------- GPU arm
 
 def main() -> int:
@@ -663,6 +746,8 @@ def main() -> int:
         return run_sweep(args)
     if args.workload == "ablate_probe":
         return run_ablate_probe(args)
+    if args.workload == "numeric_repeat":
+        return run_numeric_repeat(args)
 
     import torch
     import torch.distributed as dist

@@ -196,8 +196,26 @@ SPGEMM_API int spgemm_symbolic(spgemm_plan_t plan, int32_t *c_row_ptr, int64_t *
  * c_vals (device, nnz(C) values), column-sorted when the plan has
  * SPGEMM_SORTED.  c_row_ptr must be the array filled by spgemm_symbolic.
  * Asynchronous: results are ready when the plan's stream reaches this point.
+ * May be called again on the same plan, with the same or new output
+ * buffers, after the VALUES of A and B changed: the row structure (row_ptr
+ * and col_idx of A and B) must be unchanged, as in the repeated products of
+ * multigrid setup.  The first call also prepares the structure-only work
+ * (row grouping, heavy-row work items); later calls run only the kernels.
  */
 SPGEMM_API int spgemm_numeric(spgemm_plan_t plan, const int32_t *c_row_ptr, int32_t *c_col_idx, void *c_vals);
+
+/*
+ * The numeric phase as a CUDA graph.  The first call after a spgemm_numeric
+ * on this plan captures the plan's numeric kernels (all bins, their side
+ * streams and joins) for these output buffers and launches the graph; later
+ * calls with the same buffers only launch it again, with one API call
+ * instead of one per kernel.  New buffers capture a new graph.  Same rules
+ * as a repeated spgemm_numeric: only the values of A and B may change.
+ * Returns SPGEMM_ERR_BAD_STATE before the first spgemm_numeric, and
+ * SPGEMM_ERR_INVALID_ARGUMENT for plans created with SPGEMM_TIMING (whose
+ * per-kernel events cannot be timed inside a graph).
+ */
+SPGEMM_API int spgemm_numeric_graph(spgemm_plan_t plan, const int32_t *c_row_ptr, int32_t *c_col_idx, void *c_vals);
 
 /* Release the plan and its workspace (stream-ordered).  NULL is accepted. */
 SPGEMM_API int spgemm_plan_destroy(spgemm_plan_t plan);

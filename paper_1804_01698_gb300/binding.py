@@ -88,7 +88,8 @@ EXPORTED = ("spgemm_plan_create", "spgemm_symbolic", "spgemm_numeric", "spgemm_p
             "spgemm_plan_workspace_bytes", "spgemm_plan_stats", "spgemm_plan_row_flop", "spgemm_plan_sym_bins",
             "spgemm_plan_row_nnz", "spgemm_plan_kernel_times", "spgemm", "spgemm_status_string",
             "spgemm_last_error", "spgemm_symbolic_noalloc", "spgemm_batch_create", "spgemm_batch_symbolic",
-            "spgemm_batch_numeric", "spgemm_batch_destroy", "spgemm_plan_create_tuned", "spgemm_batch_create_tuned")
+            "spgemm_batch_numeric", "spgemm_batch_destroy", "spgemm_plan_create_tuned", "spgemm_batch_create_tuned",
+            "spgemm_numeric_graph")
 
 
 def library_path() -> str:
@@ -112,6 +113,7 @@ def library():
                                              I32, ctypes.c_uint, P, ctypes.POINTER(Tuning)]
     lib.spgemm_symbolic.argtypes = [P, P, ctypes.POINTER(I64)]
     lib.spgemm_numeric.argtypes = [P, P, P, P]
+    lib.spgemm_numeric_graph.argtypes = [P, P, P, P]
     lib.spgemm_plan_destroy.argtypes = [P]
     lib.spgemm_plan_workspace_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
     lib.spgemm_plan_stats.argtypes = [P, ctypes.POINTER(Stats)]
@@ -233,6 +235,16 @@ class Plan:
                                            c_col_idx.data_ptr() if self.nnz_c else None,
                                            c_vals.data_ptr() if self.nnz_c else None), "spgemm_numeric")
         return DeviceCSR(self.A.nrows, self.B.ncols, self.c_row_ptr, c_col_idx, c_vals)
+
+    def numeric_graph(self, C: DeviceCSR) -> DeviceCSR:
+        """Numeric phase again into C's buffers through a CUDA graph (captured
+        on the first call for these buffers, replayed afterwards).  Only the
+        values of A and B may have changed since the first numeric()."""
+        with torch.cuda.device(self.device):
+            _check(self.lib.spgemm_numeric_graph(self.handle, self.c_row_ptr.data_ptr(),
+                                                 C.col_idx.data_ptr() if self.nnz_c else None,
+                                                 C.vals.data_ptr() if self.nnz_c else None), "spgemm_numeric_graph")
+        return C
 
     def stats(self) -> dict:
         s = Stats()

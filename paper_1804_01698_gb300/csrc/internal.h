@@ -186,6 +186,9 @@ struct spgemm_plan_s {
   int64_t tune_bm_min;   // spgemm_tuning::bitmap_min_bound (0: default rule, -1: no bitmaps)
   int64_t max_nnz_c;     // largest nnz(C) accepted (spgemm_tuning::max_nnz_c, default 2^31-1)
   int64_t span_cols;     // bound on the column span of any row of C: k, or a batch's widest product
+  // spgemm_numeric_graph: the captured numeric launches and the output buffers baked into them
+  cudaGraphExec_t graph_exec;
+  const void *graph_rp, *graph_ci, *graph_cv;
   bool bitmap_ok;
   int bm_words;
 

@@ -539,6 +539,8 @@ void free_events(spgemm_plan_s *p) {
 }
 
 void free_ws(spgemm_plan_s *p) {
+  if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+  p->graph_exec = nullptr;
   free_events(p);
   release_side(p);
   if (p->ws_fixed) cudaFreeAsync(p->ws_fixed, p->stream);
@@ -839,52 +841,122 @@ int spgemm_symbolic(spgemm_plan_t p, int32_t *c_row_ptr, int64_t *nnz_c) {
   return SPGEMM_OK;
 }
 
+// Structure-only part of the numeric phase (bitmap work items, global
+// tables, rows grouped by numeric bin): run by the first numeric call.
+static int numeric_prepare(spgemm_plan_t p) {
+  const int64_t m = p->m;
+  cudaError_t e = cudaSuccess;
+  const int64_t nitems = p->bm_item_off[3];
+  if (nitems > 0) {
+    p->bm_items_bytes = (size_t)nitems * sizeof(int4);
+    e = cudaMallocAsync((void **)&p->bm_items, p->bm_items_bytes, p->stream);
+    if (e != cudaSuccess) {
+      p->bm_items = nullptr;
+      return fail_cuda(e, "allocating bitmap work items");
+    }
+    const int64_t nbm = p->sym_count[kSymBitmapBin] + p->sym_count[kSymBitmapMidBin];
+    KernelScope ks(p, "bm_items_fill");
+    BmCaps caps{{p->bm_cap[0], p->bm_cap[1], p->bm_cap[2]}, {p->bm_item_off[0], p->bm_item_off[1], p->bm_item_off[2]}};
+    k_bm_items_fill<<<(unsigned)((nbm + 255) / 256), 256, 0, p->stream>>>(
+        p->perm + p->sym_off[kSymBitmapBin], nbm, p->nnz_row, p->flop, caps, p->dc, p->bm_items);
+  }
+  if (p->num_count[kNumGlobalBin] > 0) {
+    const int64_t slots = std::max<int64_t>(64, pow2_above((int64_t)p->hc->max_nnz_global * 4 / 3));
+    const int rc = alloc_gtab(p, slots, 4 + value_size(p->dtype), p->num_count[kNumGlobalBin]);
+    if (rc != SPGEMM_OK) return rc;
+  }
+  Offsets o{};
+  for (int b = 0; b < kNumNumBins; ++b) o.v[b] = p->num_off[b];
+  {
+    KernelScope ks(p, "bin_rows_num");
+    k_bin_scatter<<<(unsigned)((m + 255) / 256), 256, 0, p->stream>>>(p->rbin2, m, o, p->dc->num_cursor, p->perm2,
+                                                                      kNumNumBins);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail_cuda(e, "numeric binning");
+  return SPGEMM_OK;
+}
+
+// Value-dependent part: the numeric kernels of every bin.
+static cudaError_t numeric_launch(spgemm_plan_t p, const int32_t *c_row_ptr, int32_t *c_col_idx, void *c_vals) {
+  switch (p->dtype) {
+    case SPGEMM_F64: return launch_numeric_f64(p, c_row_ptr, c_col_idx, c_vals);
+    case SPGEMM_F32: return launch_numeric_f32(p, c_row_ptr, c_col_idx, c_vals);
+    default: return launch_numeric_i64(p, c_row_ptr, c_col_idx, c_vals);
+  }
+}
+
 int spgemm_numeric(spgemm_plan_t p, const int32_t *c_row_ptr, int32_t *c_col_idx, void *c_vals) {
   NvtxRange nvtx("spgemm_numeric");
   if (!p || !c_row_ptr) return SPGEMM_ERR_INVALID_ARGUMENT;
-  if (p->state != 1) return SPGEMM_ERR_BAD_STATE;
+  if (p->state != 1 && p->state != 2) return SPGEMM_ERR_BAD_STATE;
   if (p->nnz_c > 0 && (!c_col_idx || !c_vals)) return SPGEMM_ERR_INVALID_ARGUMENT;
   g_last_error.clear();
-  const int64_t m = p->m;
-  cudaError_t e = cudaSuccess;
-  int rc = SPGEMM_OK;
   if (p->nnz_c > 0) {
-    const int64_t nitems = p->bm_item_off[3];
-    if (nitems > 0) {
-      p->bm_items_bytes = (size_t)nitems * sizeof(int4);
-      e = cudaMallocAsync((void **)&p->bm_items, p->bm_items_bytes, p->stream);
-      if (e != cudaSuccess) {
-        p->bm_items = nullptr;
-        return fail_cuda(e, "allocating bitmap work items");
-      }
-      const int64_t nbm = p->sym_count[kSymBitmapBin] + p->sym_count[kSymBitmapMidBin];
-      KernelScope ks(p, "bm_items_fill");
-      BmCaps caps{{p->bm_cap[0], p->bm_cap[1], p->bm_cap[2]}, {p->bm_item_off[0], p->bm_item_off[1], p->bm_item_off[2]}};
-      k_bm_items_fill<<<(unsigned)((nbm + 255) / 256), 256, 0, p->stream>>>(
-          p->perm + p->sym_off[kSymBitmapBin], nbm, p->nnz_row, p->flop, caps, p->dc, p->bm_items);
-    }
-    if (p->num_count[kNumGlobalBin] > 0) {
-      const int64_t slots = std::max<int64_t>(64, pow2_above((int64_t)p->hc->max_nnz_global * 4 / 3));
-      rc = alloc_gtab(p, slots, 4 + value_size(p->dtype), p->num_count[kNumGlobalBin]);
+    if (p->state == 1) {
+      const int rc = numeric_prepare(p);
       if (rc != SPGEMM_OK) return rc;
     }
-    Offsets o{};
-    for (int b = 0; b < kNumNumBins; ++b) o.v[b] = p->num_off[b];
-    {
-      KernelScope ks(p, "bin_rows_num");
-      k_bin_scatter<<<(unsigned)((m + 255) / 256), 256, 0, p->stream>>>(p->rbin2, m, o, p->dc->num_cursor, p->perm2,
-                                                                        kNumNumBins);
-    }
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return fail_cuda(e, "numeric binning");
-    switch (p->dtype) {
-      case SPGEMM_F64: e = launch_numeric_f64(p, c_row_ptr, c_col_idx, c_vals); break;
-      case SPGEMM_F32: e = launch_numeric_f32(p, c_row_ptr, c_col_idx, c_vals); break;
-      default: e = launch_numeric_i64(p, c_row_ptr, c_col_idx, c_vals); break;
-    }
+    const cudaError_t e = numeric_launch(p, c_row_ptr, c_col_idx, c_vals);
     if (e != cudaSuccess) return fail_cuda(e, "numeric kernels");
   }
   p->state = 2;
+  return SPGEMM_OK;
+}
+
+int spgemm_numeric_graph(spgemm_plan_t p, const int32_t *c_row_ptr, int32_t *c_col_idx, void *c_vals) {
+  NvtxRange nvtx("spgemm_numeric_graph");
+  if (!p || !c_row_ptr) return SPGEMM_ERR_INVALID_ARGUMENT;
+  if (p->state != 2) return SPGEMM_ERR_BAD_STATE;
+  if (p->flags & SPGEMM_TIMING) {
+    set_last_error("spgemm_numeric_graph: plans created with SPGEMM_TIMING time every kernel; use spgemm_numeric");
+    return SPGEMM_ERR_INVALID_ARGUMENT;
+  }
+  if (p->nnz_c > 0 && (!c_col_idx || !c_vals)) return SPGEMM_ERR_INVALID_ARGUMENT;
+  g_last_error.clear();
+  if (p->nnz_c == 0) return SPGEMM_OK;
+  cudaError_t e = cudaSuccess;
+  const bool same = p->graph_exec && p->graph_rp == c_row_ptr && p->graph_ci == c_col_idx && p->graph_cv == c_vals;
+  if (!same) {
+    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+    p->graph_exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    // the default streams cannot be captured: capture on a private stream
+    // (the graph does not depend on the stream that recorded it) and launch
+    // the graph into the plan's stream
+    cudaStream_t cap = p->stream;
+    const bool private_stream = p->stream == nullptr || p->stream == cudaStreamLegacy ||
+                                p->stream == cudaStreamPerThread;
+    if (private_stream) {
+      e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return fail_cuda(e, "numeric graph capture stream");
+    }
+    const cudaStream_t saved = p->stream;
+    p->stream = cap;
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    cudaError_t el = cudaSuccess;
+    if (e == cudaSuccess) {
+      el = numeric_launch(p, c_row_ptr, c_col_idx, c_vals);
+      e = cudaStreamEndCapture(cap, &graph);
+    }
+    p->stream = saved;
+    if (private_stream) cudaStreamDestroy(cap);
+    if (el != cudaSuccess || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return fail_cuda(el != cudaSuccess ? el : e, "numeric graph capture");
+    }
+    e = cudaGraphInstantiate(&p->graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      p->graph_exec = nullptr;
+      return fail_cuda(e, "numeric graph instantiation");
+    }
+    p->graph_rp = c_row_ptr;
+    p->graph_ci = c_col_idx;
+    p->graph_cv = c_vals;
+  }
+  e = cudaGraphLaunch(p->graph_exec, p->stream);
+  if (e != cudaSuccess) return fail_cuda(e, "numeric graph launch");
   return SPGEMM_OK;
 }
 
