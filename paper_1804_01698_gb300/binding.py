@@ -172,6 +172,21 @@ class DeviceCSR:
                    self.vals.cpu().numpy())
 
 
+def hand_over(stream, *tensors) -> None:
+    """Results written on `stream` and used on the caller's current stream:
+    the current stream waits for `stream`, and the tensors' memory (allocated
+    on `stream`) is not reused there before the current stream's work on
+    them has finished (torch's caching allocator only tracks the allocating
+    stream otherwise)."""
+    cur = torch.cuda.current_stream(stream.device)
+    if cur == stream:
+        return
+    cur.wait_stream(stream)
+    for t in tensors:
+        if t is not None and t.numel() > 0:
+            t.record_stream(cur)
+
+
 def to_device(m, device="cuda", dtype=None, non_blocking=False) -> DeviceCSR:
     """Copy a host CSR (paper_1804_01698_gb300.inputs.CSR) to the device."""
     vals = torch.from_numpy(np.ascontiguousarray(m.vals))
@@ -217,33 +232,43 @@ class Plan:
         self.nnz_c = None
 
     def symbolic(self) -> int:
-        self.c_row_ptr = torch.empty(self.A.nrows + 1, dtype=torch.int32, device=self.device)
+        with torch.cuda.stream(self.stream):
+            self.c_row_ptr = torch.empty(self.A.nrows + 1, dtype=torch.int32, device=self.device)
         nnz = ctypes.c_int64()
         with torch.cuda.device(self.device):
             _check(self.lib.spgemm_symbolic(self.handle, self.c_row_ptr.data_ptr(), ctypes.byref(nnz)),
                    "spgemm_symbolic")
         self.nnz_c = int(nnz.value)
+        hand_over(self.stream, self.c_row_ptr)
         return self.nnz_c
 
     def numeric(self, c_col_idx: torch.Tensor | None = None, c_vals: torch.Tensor | None = None) -> DeviceCSR:
-        if c_col_idx is None:
-            c_col_idx = torch.empty(max(self.nnz_c, 0), dtype=torch.int32, device=self.device)
-        if c_vals is None:
-            c_vals = torch.empty(max(self.nnz_c, 0), dtype=self.dtype, device=self.device)
+        with torch.cuda.stream(self.stream):
+            if c_col_idx is None:
+                c_col_idx = torch.empty(max(self.nnz_c, 0), dtype=torch.int32, device=self.device)
+            if c_vals is None:
+                c_vals = torch.empty(max(self.nnz_c, 0), dtype=self.dtype, device=self.device)
+        # the plan's stream must not run ahead of work the caller queued on these buffers
+        if torch.cuda.current_stream(self.device) != self.stream:
+            self.stream.wait_stream(torch.cuda.current_stream(self.device))
         with torch.cuda.device(self.device):
             _check(self.lib.spgemm_numeric(self.handle, self.c_row_ptr.data_ptr(),
                                            c_col_idx.data_ptr() if self.nnz_c else None,
                                            c_vals.data_ptr() if self.nnz_c else None), "spgemm_numeric")
+        hand_over(self.stream, self.c_row_ptr, c_col_idx, c_vals)
         return DeviceCSR(self.A.nrows, self.B.ncols, self.c_row_ptr, c_col_idx, c_vals)
 
     def numeric_graph(self, C: DeviceCSR) -> DeviceCSR:
         """Numeric phase again into C's buffers through a CUDA graph (captured
         on the first call for these buffers, replayed afterwards).  Only the
         values of A and B may have changed since the first numeric()."""
+        if torch.cuda.current_stream(self.device) != self.stream:
+            self.stream.wait_stream(torch.cuda.current_stream(self.device))
         with torch.cuda.device(self.device):
             _check(self.lib.spgemm_numeric_graph(self.handle, self.c_row_ptr.data_ptr(),
                                                  C.col_idx.data_ptr() if self.nnz_c else None,
                                                  C.vals.data_ptr() if self.nnz_c else None), "spgemm_numeric_graph")
+        hand_over(self.stream, C.col_idx, C.vals)
         return C
 
     def stats(self) -> dict:
@@ -270,22 +295,28 @@ class Plan:
         return int(v.value)
 
     def row_flop(self) -> torch.Tensor:
-        out = torch.empty(self.A.nrows, dtype=torch.int64, device=self.device)
+        with torch.cuda.stream(self.stream):
+            out = torch.empty(self.A.nrows, dtype=torch.int64, device=self.device)
         _check(self.lib.spgemm_plan_row_flop(self.handle, out.data_ptr()), "spgemm_plan_row_flop")
+        hand_over(self.stream, out)
         return out
 
     def sym_bins(self):
         s = Stats()
         self.lib.spgemm_plan_stats(self.handle, ctypes.byref(s))
         offs = (ctypes.c_int64 * (s.n_sym_bins + 1))()
-        perm = torch.empty(max(self.A.nrows, 1), dtype=torch.int32, device=self.device)
+        with torch.cuda.stream(self.stream):
+            perm = torch.empty(max(self.A.nrows, 1), dtype=torch.int32, device=self.device)
         _check(self.lib.spgemm_plan_sym_bins(self.handle, perm.data_ptr(), offs), "spgemm_plan_sym_bins")
+        hand_over(self.stream, perm)
         offsets = list(offs)
         return perm[: offsets[-1]], offsets
 
     def row_nnz(self) -> torch.Tensor:
-        out = torch.empty(self.A.nrows, dtype=torch.int32, device=self.device)
+        with torch.cuda.stream(self.stream):
+            out = torch.empty(self.A.nrows, dtype=torch.int32, device=self.device)
         _check(self.lib.spgemm_plan_row_nnz(self.handle, out.data_ptr()), "spgemm_plan_row_nnz")
+        hand_over(self.stream, out)
         return out
 
     def destroy(self):
@@ -375,8 +406,11 @@ def spgemm(A: DeviceCSR, B: DeviceCSR, sorted_output: bool = True, stream=None) 
     device = A.row_ptr.device
     keep: dict[int, torch.Tensor] = {}
 
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+
     def _alloc(nbytes, _ctx):
-        t = torch.empty(max(int(nbytes), 16), dtype=torch.uint8, device=device)
+        with torch.cuda.stream(s):
+            t = torch.empty(max(int(nbytes), 16), dtype=torch.uint8, device=device)
         keep[t.data_ptr()] = t
         return t.data_ptr()
 
@@ -384,7 +418,6 @@ def spgemm(A: DeviceCSR, B: DeviceCSR, sorted_output: bool = True, stream=None) 
     a, b = A.desc(), B.desc()
     rp, ci, cv = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
     nnz = ctypes.c_int64()
-    s = stream if stream is not None else torch.cuda.current_stream(device)
     with torch.cuda.device(device):
         status = lib.spgemm(ctypes.byref(a), ctypes.byref(b), _DTYPES[A.vals.dtype],
                             SPGEMM_SORTED if sorted_output else SPGEMM_UNSORTED, _stream_ptr(s), cb, None,
@@ -395,6 +428,7 @@ def spgemm(A: DeviceCSR, B: DeviceCSR, sorted_output: bool = True, stream=None) 
     cit = keep[ci.value][: n * 4].view(torch.int32)
     esz = torch.empty(0, dtype=A.vals.dtype).element_size()
     cvt = keep[cv.value][: n * esz].view(A.vals.dtype)
+    hand_over(s, rpt, cit, cvt)
     return DeviceCSR(A.nrows, B.ncols, rpt, cit, cvt)
 
 
@@ -433,29 +467,35 @@ class Batch:
         self.row_off = None
 
     def symbolic(self) -> int:
-        self.c_row_ptr = torch.empty(self.m + 1, dtype=torch.int32, device=self.device)
+        with torch.cuda.stream(self.stream):
+            self.c_row_ptr = torch.empty(self.m + 1, dtype=torch.int32, device=self.device)
         nnz = ctypes.c_int64()
         off = (ctypes.c_int64 * (self.nprod + 1))()
         with torch.cuda.device(self.device):
             _check(self.lib.spgemm_batch_symbolic(self.handle, self.c_row_ptr.data_ptr(), ctypes.byref(nnz), off),
                    "spgemm_batch_symbolic")
+        hand_over(self.stream, self.c_row_ptr)
         self.nnz_c = int(nnz.value)
         self.row_off = list(off)
         return self.nnz_c
 
     def numeric(self):
         """Returns (c_row_ptr, c_col_idx, c_vals) of the packed C; columns are local to each product."""
-        ci = torch.empty(max(self.nnz_c, 0), dtype=torch.int32, device=self.device)
-        cv = torch.empty(max(self.nnz_c, 0), dtype=self.dtype, device=self.device)
+        with torch.cuda.stream(self.stream):
+            ci = torch.empty(max(self.nnz_c, 0), dtype=torch.int32, device=self.device)
+            cv = torch.empty(max(self.nnz_c, 0), dtype=self.dtype, device=self.device)
         with torch.cuda.device(self.device):
             _check(self.lib.spgemm_batch_numeric(self.handle, self.c_row_ptr.data_ptr(),
                                                  ci.data_ptr() if self.nnz_c else None,
                                                  cv.data_ptr() if self.nnz_c else None), "spgemm_batch_numeric")
         self.c_col_idx, self.c_vals = ci, cv
+        hand_over(self.stream, self.c_row_ptr, ci, cv)
         return self.c_row_ptr, ci, cv
 
     def product(self, p: int, row_ptr_host=None) -> DeviceCSR:
-        """Product p of the batch as a DeviceCSR view (row_ptr rebased to 0)."""
+        """Product p of the batch as a DeviceCSR view (row_ptr rebased to 0),
+        for use on the current stream (which may differ from the batch's)."""
+        hand_over(self.stream, self.c_row_ptr, self.c_col_idx, self.c_vals)
         r0, r1 = self.row_off[p], self.row_off[p + 1]
         rp = self.c_row_ptr[r0:r1 + 1]
         if row_ptr_host is not None:

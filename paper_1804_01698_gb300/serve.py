@@ -247,9 +247,14 @@ class GpuBackend:
         h["event"].synchronize()
 
     def results(self, h):
+        """The batch's products, for use on the caller's current stream (the
+        batch ran on its own stream, whose memory pool must not reuse the
+        results while the caller still works on them)."""
         w = h["work"]
         if h["n"] == 1:
-            return [h["out"]]
+            C = h["out"]
+            self.sg.hand_over(h["stream"], C.row_ptr, C.col_idx, C.vals)
+            return [C]
         rp = w.c_row_ptr.cpu().numpy()
         return [w.product(p, rp) for p in range(h["n"])]
 
