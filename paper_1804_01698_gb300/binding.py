@@ -187,6 +187,14 @@ def hand_over(stream, *tensors) -> None:
             t.record_stream(cur)
 
 
+def _after_caller(stream) -> None:
+    """Work queued on `stream` starts after what the caller's current stream
+    has queued so far (the operands may still be in flight there)."""
+    cur = torch.cuda.current_stream(stream.device)
+    if cur != stream:
+        stream.wait_stream(cur)
+
+
 def to_device(m, device="cuda", dtype=None, non_blocking=False) -> DeviceCSR:
     """Copy a host CSR (paper_1804_01698_gb300.inputs.CSR) to the device."""
     vals = torch.from_numpy(np.ascontiguousarray(m.vals))
@@ -216,6 +224,7 @@ class Plan:
         self.dtype = A.vals.dtype
         self.device = A.row_ptr.device
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        _after_caller(self.stream)
         flags = (SPGEMM_SORTED if sorted_output else SPGEMM_UNSORTED) | (SPGEMM_TIMING if timing else 0) | \
             (SPGEMM_SERIAL if serial else 0) | _PROBES[probe] | _HASHES[hash] | \
             (SPGEMM_COUNT_PROBES if count_probes else 0)
@@ -248,9 +257,9 @@ class Plan:
                 c_col_idx = torch.empty(max(self.nnz_c, 0), dtype=torch.int32, device=self.device)
             if c_vals is None:
                 c_vals = torch.empty(max(self.nnz_c, 0), dtype=self.dtype, device=self.device)
-        # the plan's stream must not run ahead of work the caller queued on these buffers
-        if torch.cuda.current_stream(self.device) != self.stream:
-            self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        # the plan's stream must not run ahead of work the caller queued on the
+        # operands (new values) or on these buffers
+        _after_caller(self.stream)
         with torch.cuda.device(self.device):
             _check(self.lib.spgemm_numeric(self.handle, self.c_row_ptr.data_ptr(),
                                            c_col_idx.data_ptr() if self.nnz_c else None,
@@ -262,8 +271,7 @@ class Plan:
         """Numeric phase again into C's buffers through a CUDA graph (captured
         on the first call for these buffers, replayed afterwards).  Only the
         values of A and B may have changed since the first numeric()."""
-        if torch.cuda.current_stream(self.device) != self.stream:
-            self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        _after_caller(self.stream)
         with torch.cuda.device(self.device):
             _check(self.lib.spgemm_numeric_graph(self.handle, self.c_row_ptr.data_ptr(),
                                                  C.col_idx.data_ptr() if self.nnz_c else None,
@@ -391,6 +399,7 @@ def spgemm_symbolic_noalloc(A: DeviceCSR, B: DeviceCSR, c_row_ptr: torch.Tensor,
     a, b = A.desc(), B.desc()
     nnz = ctypes.c_int64()
     s = stream if stream is not None else torch.cuda.current_stream(A.row_ptr.device)
+    _after_caller(s)
     with torch.cuda.device(A.row_ptr.device):
         _check(lib.spgemm_symbolic_noalloc(ctypes.byref(a), ctypes.byref(b), c_row_ptr.data_ptr(), ctypes.byref(nnz),
                                            _stream_ptr(s)), "spgemm_symbolic_noalloc")
@@ -418,6 +427,7 @@ def spgemm(A: DeviceCSR, B: DeviceCSR, sorted_output: bool = True, stream=None) 
     a, b = A.desc(), B.desc()
     rp, ci, cv = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
     nnz = ctypes.c_int64()
+    _after_caller(s)
     with torch.cuda.device(device):
         status = lib.spgemm(ctypes.byref(a), ctypes.byref(b), _DTYPES[A.vals.dtype],
                             SPGEMM_SORTED if sorted_output else SPGEMM_UNSORTED, _stream_ptr(s), cb, None,
@@ -447,6 +457,7 @@ class Batch:
         self.As, self.Bs = list(As), list(Bs)
         self.device = As[0].row_ptr.device
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        _after_caller(self.stream)
         flags = (SPGEMM_SORTED if sorted_output else SPGEMM_UNSORTED) | (SPGEMM_TIMING if timing else 0) | \
             (SPGEMM_SERIAL if serial else 0) | _PROBES[probe] | _HASHES[hash]
         n = len(As)
