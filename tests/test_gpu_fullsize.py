@@ -79,3 +79,28 @@ def test_serving_stream_full_size_ranges_sampled():
     for i in sorted(set(rng.choice(200, 20, replace=False).tolist()) | {big_amg}):
         A, B = mix[i]
         assert_matches_oracle(by_rid[i], A, B, True, nthreads=os.cpu_count() or 8)
+
+
+def test_serving_stream_poisson_arrivals_sampled():
+    """The same stream arriving as a Poisson process near the server's
+    capacity: batches of varying sizes overlap on several streams while
+    new ones are prepared and finished ones retired."""
+    from paper_1804_01698_gb300 import binding as sg
+    from paper_1804_01698_gb300.serve import GpuBackend, Request, Server
+    mix = inputs.serving_mix(200, seed=inputs.SEED_BASE + 9)
+    arrivals = inputs.poisson_arrivals(200, 3000.0, inputs.SEED_BASE + 9)
+    reqs = []
+    for i, (A, B) in enumerate(mix):
+        dA = sg.to_device(A)
+        dB = dA if B is A else sg.to_device(B)
+        reqs.append(Request(i, dA, dB, float(arrivals[i]), int(np.diff(B.row_ptr)[A.col_idx].sum())))
+    st = Server(GpuBackend(sorted_output=False), mem_cap=40 << 30, max_batch=16, max_inflight=3).run(
+        reqs, keep_results=True)
+    torch.cuda.synchronize()
+    assert sorted(c.rid for c in st.completions) == list(range(200))
+    assert st.batches > 10
+    by_rid = {c.rid: c.result for c in st.completions}
+    rng = np.random.default_rng(173)
+    for i in sorted(rng.choice(200, 25, replace=False).tolist()):
+        A, B = mix[i]
+        assert_matches_oracle(by_rid[i], A, B, False, nthreads=os.cpu_count() or 8)
