@@ -15,10 +15,12 @@
  *     (caller allocates C col_idx and vals for nnz(C) entries)
  *     spgemm_numeric       -> C col_idx and vals, rows sorted if requested
  *     spgemm_plan_destroy
- * or the one-shot spgemm(), which takes a caller allocator.
+ * or the one-shot spgemm(), which takes a caller allocator, or spgemm_host()
+ * for operands and result in host memory.
  *
  * Memory and ownership:
- *   - Every matrix pointer is a DEVICE pointer on the current CUDA device.
+ *   - Every matrix pointer is a DEVICE pointer on the current CUDA device,
+ *     except in spgemm_host(), whose operands and result are in host memory.
  *   - The caller owns A, B and all C buffers.  A plan borrows A and B: they
  *     must stay valid and unmodified until spgemm_numeric has completed on
  *     the plan's stream.
@@ -297,6 +299,44 @@ SPGEMM_API int spgemm_batch_symbolic(spgemm_batch_t batch, int32_t *c_row_ptr, i
 SPGEMM_API int spgemm_batch_numeric(spgemm_batch_t batch, const int32_t *c_row_ptr, int32_t *c_col_idx, void *c_vals);
 SPGEMM_API spgemm_plan_t spgemm_batch_plan(spgemm_batch_t batch);
 SPGEMM_API int spgemm_batch_destroy(spgemm_batch_t batch);
+
+/*
+ * C = A*B with A, B and C in HOST memory, the copy of C to the host
+ * overlapped with the computation.  The paper's products run on one
+ * machine's memory and have no transfer step; this entry point serves
+ * callers whose operands live in host memory.
+ *
+ * A and B describe host arrays (the same CSR layout as spgemm_csr; if the
+ * descriptors point to the same arrays, B is copied once).  The memory
+ * `host_alloc` returns for C must be host memory; page-locked memory
+ * (cudaHostAlloc, cudaHostRegister) is needed for the copies to overlap,
+ * and so it is for A and B.  `host_alloc` is called three times, after the
+ * symbolic phase: row_ptr ((m+1)*4 bytes), col_idx (nnz*4) and vals
+ * (nnz*sizeof(value)); the caller owns what it returns, also on error.
+ *
+ * The call copies A and B to the device, runs the flop pass and splits A's
+ * rows into `row_blocks` contiguous blocks by flop (the partition of
+ * Sec. 4.1, Fig. "RowsToThreads", steps 1-2), block r taking a share of the
+ * flop proportional to 2^min(r, 6): the first block, whose numeric phase
+ * no copy hides, is small, and each later block's numeric phase fits under
+ * the copy of the block before it.  Every block is
+ * a product of its own (one plan each).  The symbolic phases of all blocks
+ * give nnz(C); C is then allocated through `host_alloc`, and the numeric
+ * phases run block after block on `stream` while a second stream copies
+ * each finished block's columns and values to the host, so the copy of
+ * block b overlaps the numeric phase of block b+1.  The result is the same
+ * for every row_blocks.  row_blocks <= 0 picks a default (3 blocks from
+ * 2^26 flop, else 1: every block is a product of its own and costs a plan
+ * and a symbolic phase); it is capped at m.  flags as for
+ * spgemm_plan_create, without SPGEMM_TIMING.
+ *
+ * Returns when C is complete in host memory.  The device memory it used is
+ * released (stream-ordered on `stream`).  Errors as for spgemm(); on error
+ * the pointers already allocated are returned and the rest are NULL.
+ */
+SPGEMM_API int spgemm_host(const spgemm_csr *A, const spgemm_csr *B, int dtype, unsigned flags, void *stream,
+                           int row_blocks, spgemm_alloc_fn host_alloc, void *alloc_ctx, int32_t **c_row_ptr,
+                           int32_t **c_col_idx, void **c_vals, int64_t *nnz_c);
 
 /*
  * Symbolic phase for callers that cannot allocate device memory.  The paper

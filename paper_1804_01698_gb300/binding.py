@@ -89,7 +89,7 @@ EXPORTED = ("spgemm_plan_create", "spgemm_symbolic", "spgemm_numeric", "spgemm_p
             "spgemm_plan_row_nnz", "spgemm_plan_kernel_times", "spgemm", "spgemm_status_string",
             "spgemm_last_error", "spgemm_symbolic_noalloc", "spgemm_batch_create", "spgemm_batch_symbolic",
             "spgemm_batch_numeric", "spgemm_batch_destroy", "spgemm_plan_create_tuned", "spgemm_batch_create_tuned",
-            "spgemm_numeric_graph")
+            "spgemm_numeric_graph", "spgemm_host")
 
 
 def library_path() -> str:
@@ -133,6 +133,8 @@ def library():
     lib.spgemm_symbolic_noalloc.argtypes = [ctypes.POINTER(CsrDesc), ctypes.POINTER(CsrDesc), P, ctypes.POINTER(I64), P]
     lib.spgemm.argtypes = [ctypes.POINTER(CsrDesc), ctypes.POINTER(CsrDesc), I32, ctypes.c_uint, P, ALLOC_FN, P,
                            ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(I64)]
+    lib.spgemm_host.argtypes = [ctypes.POINTER(CsrDesc), ctypes.POINTER(CsrDesc), I32, ctypes.c_uint, P, I32, ALLOC_FN,
+                                P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(I64)]
     for name in EXPORTED:
         getattr(lib, name).restype = ctypes.c_int
     lib.spgemm_status_string.argtypes = [I32]
@@ -440,6 +442,96 @@ def spgemm(A: DeviceCSR, B: DeviceCSR, sorted_output: bool = True, stream=None) 
     cvt = keep[cv.value][: n * esz].view(A.vals.dtype)
     hand_over(s, rpt, cit, cvt)
     return DeviceCSR(A.nrows, B.ncols, rpt, cit, cvt)
+
+
+class HostArena:
+    """Page-locked host memory for spgemm_host's results: one pinned buffer,
+    allocated once, handed out in 256-byte aligned pieces.  Pinning memory
+    costs far more than the product, so a caller that runs many products
+    keeps one arena and calls reset() before each call (the previous
+    results are overwritten then)."""
+
+    def __init__(self, nbytes: int):
+        self.buf = torch.empty(int(nbytes), dtype=torch.uint8).pin_memory()
+        self.off = 0
+
+    @staticmethod
+    def bytes_for(nrows: int, nnz: int, value_size: int) -> int:
+        """Arena size that holds one result of nrows rows and nnz entries."""
+        return 3 * 256 + (nrows + 1) * 4 + max(nnz * 4, 16) + max(nnz * value_size, 16)
+
+    def alloc(self, nbytes: int):
+        start = (self.off + 255) // 256 * 256
+        if start + nbytes > self.buf.numel():
+            return None
+        self.off = start + nbytes
+        return self.buf[start:start + nbytes]
+
+    def reset(self) -> None:
+        self.off = 0
+
+
+def _host_array(x, dtype=None):
+    """A CPU torch tensor over a host array (numpy arrays are wrapped, not copied)."""
+    t = x if isinstance(x, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(x))
+    if t.device.type != "cpu" or not t.is_contiguous():
+        raise ValueError("spgemm_host takes contiguous host arrays")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    return t
+
+
+def spgemm_host(A, B, sorted_output: bool = True, row_blocks: int = 0, arena: HostArena | None = None,
+                stream=None, device=None):
+    """C = A*B with A, B and C in host memory, through the C entry point
+    spgemm_host(): the copy of C to the host overlaps the numeric phase,
+    block of rows by block of rows.
+
+    A and B are host CSR matrices (paper_1804_01698_gb300.inputs.CSR or
+    anything with nrows, ncols and row_ptr/col_idx/vals as numpy arrays or
+    CPU tensors; pinned tensors let the copies overlap).  C is returned as
+    an inputs.CSR whose arrays live in `arena` (or in freshly pinned
+    buffers when no arena is given).  row_blocks=0 lets the library choose."""
+    lib = library()
+    from .inputs import CSR
+    arp, aci = _host_array(A.row_ptr, torch.int32), _host_array(A.col_idx, torch.int32)
+    brp, bci = _host_array(B.row_ptr, torch.int32), _host_array(B.col_idx, torch.int32)
+    av, bv = _host_array(A.vals), _host_array(B.vals)
+    if av.dtype != bv.dtype or av.dtype not in _DTYPES:
+        raise TypeError("A and B must share a value dtype among int64, float32, float64")
+    same = A is B
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    keep: dict[int, torch.Tensor] = {}
+
+    def _alloc(nbytes, _ctx):
+        n = max(int(nbytes), 16)
+        t = arena.alloc(n) if arena is not None else torch.empty(n, dtype=torch.uint8).pin_memory()
+        if t is None:
+            return None
+        keep[t.data_ptr()] = t
+        return t.data_ptr()
+
+    def desc(m, rp, ci, v):
+        nnz = int(ci.numel())
+        return CsrDesc(m.nrows, m.ncols, nnz, rp.data_ptr(), ci.data_ptr() if nnz else None,
+                       v.data_ptr() if nnz else None)
+
+    a = desc(A, arp, aci, av)
+    b = a if same else desc(B, brp, bci, bv)
+    cb = ALLOC_FN(_alloc)
+    rp, ci, cv = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    nnz = ctypes.c_int64()
+    with torch.cuda.device(dev):
+        status = lib.spgemm_host(ctypes.byref(a), ctypes.byref(b), _DTYPES[av.dtype],
+                                 SPGEMM_SORTED if sorted_output else SPGEMM_UNSORTED, _stream_ptr(s), int(row_blocks),
+                                 cb, None, ctypes.byref(rp), ctypes.byref(ci), ctypes.byref(cv), ctypes.byref(nnz))
+    _check(status, "spgemm_host")
+    n = int(nnz.value)
+    rpt = keep[rp.value][: (A.nrows + 1) * 4].view(torch.int32)
+    cit = keep[ci.value][: n * 4].view(torch.int32)
+    cvt = keep[cv.value][: n * av.element_size()].view(av.dtype)
+    return CSR(A.nrows, B.ncols, rpt.numpy(), cit.numpy(), cvt.numpy())
 
 
 class Batch:
