@@ -565,47 +565,32 @@ __global__ void __launch_bounds__(NT, MINB)
                                    }
                                  });
   __syncthreads();
-  // Store ranks [lo, hi) in rank order with coalesced writes: a warp takes
-  // 32 consecutive bitmap words, and its lanes walk the words' entries 32 at
-  // a time; the lane of entry j finds the word holding it by binary search
-  // over the words' prefix counts (shuffles) and its column with __fns.
-  {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int w0 = warp * 32; w0 < words; w0 += nw * 32) {
-      const int w = w0 + lane;
-      const bool valid = w < words;
-      const uint2 mine = valid ? rk[w] : make_uint2(0u, 0u);
-      const int pre0 = __shfl_sync(0xffffffffu, (int)mine.y, 0);
-      // entries before this lane's word, within the 32 words (lanes past the
-      // last word sort after every entry)
-      const int first = valid ? (int)mine.y - pre0 : 0x3fffffff;
-      const int last = min(31, words - 1 - w0);
-      const int total = __shfl_sync(0xffffffffu, first + (valid ? __popc(mine.x) : 0), last);
-      if (pre0 >= hi || pre0 + total <= lo) continue;
-      for (int j0 = 0; j0 < total; j0 += 32) {
-        const int j = j0 + lane;
-        int l = 0;  // last lane whose word starts at or before entry j
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-          const int f = __shfl_sync(0xffffffffu, first, l + step);
-          if (f <= j) l += step;
-        }
-        const unsigned bits = __shfl_sync(0xffffffffu, mine.x, l);
-        const int fl = __shfl_sync(0xffffffffu, first, l);
-        const int r = pre0 + j;
-        if (j < total && r >= lo && r < hi) {
-          const int col = (w0 + l) * 32 + (int)__fns(bits, 0, j - fl + 1);
-          if (part == 0) c_ci[rp + r] = col;
-          if (parts == 1) c_v[rp + r] = vals[r - lo];
-        }
-      }
-    }
-  }
-  if (parts > 1) {
+  // Store ranks [lo, hi).  vals[] is already in rank order, so the block
+  // copies it out with coalesced writes (a split row's parts add theirs).
+  // Columns are then staged in the same shared array: thread t takes bitmap
+  // words t, t + blockDim.x, ...; the set bits of word w, in order, are the
+  // entries of ranks prefix[w], prefix[w] + 1, ..., so no entry needs a
+  // search for its word; the staged columns go out with coalesced writes.
+  if (parts == 1) {
+    for (int r = threadIdx.x; r < hi - lo; r += blockDim.x) c_v[rp + lo + r] = vals[r];
+  } else {
     for (int r = threadIdx.x; r < hi - lo; r += blockDim.x) {
       const T v = vals[r];
       if (v != T(0)) Val<T>::add_global(c_v + rp + lo + r, v);
     }
+  }
+  if (part == 0) {
+    __syncthreads();
+    int32_t *cols = reinterpret_cast<int32_t *>(vals);
+    for (int w = threadIdx.x; w < words; w += blockDim.x) {
+      const uint2 wd = rk[w];
+      int r = (int)wd.y;
+      if (r >= hi || r + __popc(wd.x) <= lo) continue;
+      for (unsigned bits = wd.x; bits != 0u; bits &= bits - 1u, ++r)
+        if (r >= lo && r < hi) cols[r - lo] = w * 32 + __ffs(bits) - 1;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < hi - lo; r += blockDim.x) c_ci[rp + lo + r] = cols[r];
   }
   if (threadIdx.x == 0 && tot != nnz) raise_err(a.err, kErrProbe);
 }
