@@ -13,6 +13,7 @@ been built (there is no fallback).
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 from dataclasses import dataclass
@@ -174,27 +175,61 @@ class DeviceCSR:
                    self.vals.cpu().numpy())
 
 
+class _Caller:
+    """The caller's current stream, read once per call, against the stream a
+    plan or batch runs on.  When they are the same stream (the usual case)
+    every method below is a no-op; entering torch.cuda.stream and reading
+    the current stream cost microseconds each, a large share of a small
+    product."""
+
+    __slots__ = ("stream", "cur", "same")
+
+    def __init__(self, stream):
+        self.stream = stream
+        try:
+            # (stream id, device index, device type) of the current stream,
+            # without building a Stream object
+            sid, dev, _ = torch._C._cuda_getCurrentStream(stream.device_index)
+            self.same = sid == stream.stream_id and dev == stream.device_index
+            self.cur = None if self.same else torch.cuda.current_stream(stream.device)
+        except AttributeError:
+            self.cur = torch.cuda.current_stream(stream.device)
+            self.same = self.cur == stream
+
+    def on(self):
+        """Context for allocations that belong to the plan's stream in torch's
+        caching allocator."""
+        return contextlib.nullcontext() if self.same else torch.cuda.stream(self.stream)
+
+    def before(self) -> None:
+        """Work queued on the plan's stream starts after what the caller's
+        stream has queued so far (the operands may still be in flight there)."""
+        if not self.same:
+            self.stream.wait_stream(self.cur)
+
+    def after(self, *tensors) -> None:
+        """Results written on the plan's stream, used on the caller's: the
+        caller's stream waits for the plan's, and the tensors' memory (which
+        belongs to the plan's stream) is not reused before the caller's work
+        on them has finished (torch's caching allocator only tracks the
+        allocating stream otherwise)."""
+        if self.same:
+            return
+        self.cur.wait_stream(self.stream)
+        for t in tensors:
+            if t is not None and t.numel() > 0:
+                t.record_stream(self.cur)
+
+
 def hand_over(stream, *tensors) -> None:
-    """Results written on `stream` and used on the caller's current stream:
-    the current stream waits for `stream`, and the tensors' memory (allocated
-    on `stream`) is not reused there before the current stream's work on
-    them has finished (torch's caching allocator only tracks the allocating
-    stream otherwise)."""
-    cur = torch.cuda.current_stream(stream.device)
-    if cur == stream:
-        return
-    cur.wait_stream(stream)
-    for t in tensors:
-        if t is not None and t.numel() > 0:
-            t.record_stream(cur)
+    """Results written on `stream`, used on the caller's current stream (see
+    _Caller.after)."""
+    _Caller(stream).after(*tensors)
 
 
 def _after_caller(stream) -> None:
-    """Work queued on `stream` starts after what the caller's current stream
-    has queued so far (the operands may still be in flight there)."""
-    cur = torch.cuda.current_stream(stream.device)
-    if cur != stream:
-        stream.wait_stream(cur)
+    """Work queued on `stream` starts after the caller's queued work."""
+    _Caller(stream).before()
 
 
 def to_device(m, device="cuda", dtype=None, non_blocking=False) -> DeviceCSR:
@@ -225,8 +260,11 @@ class Plan:
         self.A, self.B = A, B
         self.dtype = A.vals.dtype
         self.device = A.row_ptr.device
-        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        _after_caller(self.stream)
+        if stream is None:  # the caller's own stream: nothing to wait for
+            self.stream = torch.cuda.current_stream(self.device)
+        else:
+            self.stream = stream
+            _after_caller(stream)
         flags = (SPGEMM_SORTED if sorted_output else SPGEMM_UNSORTED) | (SPGEMM_TIMING if timing else 0) | \
             (SPGEMM_SERIAL if serial else 0) | _PROBES[probe] | _HASHES[hash] | \
             (SPGEMM_COUNT_PROBES if count_probes else 0)
@@ -243,42 +281,45 @@ class Plan:
         self.nnz_c = None
 
     def symbolic(self) -> int:
-        with torch.cuda.stream(self.stream):
+        c = _Caller(self.stream)
+        with c.on():
             self.c_row_ptr = torch.empty(self.A.nrows + 1, dtype=torch.int32, device=self.device)
         nnz = ctypes.c_int64()
         with torch.cuda.device(self.device):
             _check(self.lib.spgemm_symbolic(self.handle, self.c_row_ptr.data_ptr(), ctypes.byref(nnz)),
                    "spgemm_symbolic")
         self.nnz_c = int(nnz.value)
-        hand_over(self.stream, self.c_row_ptr)
+        c.after(self.c_row_ptr)
         return self.nnz_c
 
     def numeric(self, c_col_idx: torch.Tensor | None = None, c_vals: torch.Tensor | None = None) -> DeviceCSR:
-        with torch.cuda.stream(self.stream):
+        c = _Caller(self.stream)
+        with c.on():
             if c_col_idx is None:
                 c_col_idx = torch.empty(max(self.nnz_c, 0), dtype=torch.int32, device=self.device)
             if c_vals is None:
                 c_vals = torch.empty(max(self.nnz_c, 0), dtype=self.dtype, device=self.device)
         # the plan's stream must not run ahead of work the caller queued on the
         # operands (new values) or on these buffers
-        _after_caller(self.stream)
+        c.before()
         with torch.cuda.device(self.device):
             _check(self.lib.spgemm_numeric(self.handle, self.c_row_ptr.data_ptr(),
                                            c_col_idx.data_ptr() if self.nnz_c else None,
                                            c_vals.data_ptr() if self.nnz_c else None), "spgemm_numeric")
-        hand_over(self.stream, self.c_row_ptr, c_col_idx, c_vals)
+        c.after(self.c_row_ptr, c_col_idx, c_vals)
         return DeviceCSR(self.A.nrows, self.B.ncols, self.c_row_ptr, c_col_idx, c_vals)
 
     def numeric_graph(self, C: DeviceCSR) -> DeviceCSR:
         """Numeric phase again into C's buffers through a CUDA graph (captured
         on the first call for these buffers, replayed afterwards).  Only the
         values of A and B may have changed since the first numeric()."""
-        _after_caller(self.stream)
+        c = _Caller(self.stream)
+        c.before()
         with torch.cuda.device(self.device):
             _check(self.lib.spgemm_numeric_graph(self.handle, self.c_row_ptr.data_ptr(),
                                                  C.col_idx.data_ptr() if self.nnz_c else None,
                                                  C.vals.data_ptr() if self.nnz_c else None), "spgemm_numeric_graph")
-        hand_over(self.stream, C.col_idx, C.vals)
+        c.after(C.col_idx, C.vals)
         return C
 
     def stats(self) -> dict:
@@ -305,28 +346,31 @@ class Plan:
         return int(v.value)
 
     def row_flop(self) -> torch.Tensor:
-        with torch.cuda.stream(self.stream):
+        c = _Caller(self.stream)
+        with c.on():
             out = torch.empty(self.A.nrows, dtype=torch.int64, device=self.device)
         _check(self.lib.spgemm_plan_row_flop(self.handle, out.data_ptr()), "spgemm_plan_row_flop")
-        hand_over(self.stream, out)
+        c.after(out)
         return out
 
     def sym_bins(self):
         s = Stats()
         self.lib.spgemm_plan_stats(self.handle, ctypes.byref(s))
         offs = (ctypes.c_int64 * (s.n_sym_bins + 1))()
-        with torch.cuda.stream(self.stream):
+        c = _Caller(self.stream)
+        with c.on():
             perm = torch.empty(max(self.A.nrows, 1), dtype=torch.int32, device=self.device)
         _check(self.lib.spgemm_plan_sym_bins(self.handle, perm.data_ptr(), offs), "spgemm_plan_sym_bins")
-        hand_over(self.stream, perm)
+        c.after(perm)
         offsets = list(offs)
         return perm[: offsets[-1]], offsets
 
     def row_nnz(self) -> torch.Tensor:
-        with torch.cuda.stream(self.stream):
+        c = _Caller(self.stream)
+        with c.on():
             out = torch.empty(self.A.nrows, dtype=torch.int32, device=self.device)
         _check(self.lib.spgemm_plan_row_nnz(self.handle, out.data_ptr()), "spgemm_plan_row_nnz")
-        hand_over(self.stream, out)
+        c.after(out)
         return out
 
     def destroy(self):
@@ -418,9 +462,10 @@ def spgemm(A: DeviceCSR, B: DeviceCSR, sorted_output: bool = True, stream=None) 
     keep: dict[int, torch.Tensor] = {}
 
     s = stream if stream is not None else torch.cuda.current_stream(device)
+    c = _Caller(s)
 
     def _alloc(nbytes, _ctx):
-        with torch.cuda.stream(s):
+        with c.on():
             t = torch.empty(max(int(nbytes), 16), dtype=torch.uint8, device=device)
         keep[t.data_ptr()] = t
         return t.data_ptr()
@@ -429,7 +474,7 @@ def spgemm(A: DeviceCSR, B: DeviceCSR, sorted_output: bool = True, stream=None) 
     a, b = A.desc(), B.desc()
     rp, ci, cv = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
     nnz = ctypes.c_int64()
-    _after_caller(s)
+    c.before()
     with torch.cuda.device(device):
         status = lib.spgemm(ctypes.byref(a), ctypes.byref(b), _DTYPES[A.vals.dtype],
                             SPGEMM_SORTED if sorted_output else SPGEMM_UNSORTED, _stream_ptr(s), cb, None,
@@ -440,7 +485,7 @@ def spgemm(A: DeviceCSR, B: DeviceCSR, sorted_output: bool = True, stream=None) 
     cit = keep[ci.value][: n * 4].view(torch.int32)
     esz = torch.empty(0, dtype=A.vals.dtype).element_size()
     cvt = keep[cv.value][: n * esz].view(A.vals.dtype)
-    hand_over(s, rpt, cit, cvt)
+    c.after(rpt, cit, cvt)
     return DeviceCSR(A.nrows, B.ncols, rpt, cit, cvt)
 
 
@@ -548,8 +593,11 @@ class Batch:
             raise TypeError("all operands must share one value dtype among int64, float32, float64")
         self.As, self.Bs = list(As), list(Bs)
         self.device = As[0].row_ptr.device
-        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        _after_caller(self.stream)
+        if stream is None:  # the caller's own stream: nothing to wait for
+            self.stream = torch.cuda.current_stream(self.device)
+        else:
+            self.stream = stream
+            _after_caller(stream)
         flags = (SPGEMM_SORTED if sorted_output else SPGEMM_UNSORTED) | (SPGEMM_TIMING if timing else 0) | \
             (SPGEMM_SERIAL if serial else 0) | _PROBES[probe] | _HASHES[hash]
         n = len(As)
@@ -570,21 +618,23 @@ class Batch:
         self.row_off = None
 
     def symbolic(self) -> int:
-        with torch.cuda.stream(self.stream):
+        c = _Caller(self.stream)
+        with c.on():
             self.c_row_ptr = torch.empty(self.m + 1, dtype=torch.int32, device=self.device)
         nnz = ctypes.c_int64()
         off = (ctypes.c_int64 * (self.nprod + 1))()
         with torch.cuda.device(self.device):
             _check(self.lib.spgemm_batch_symbolic(self.handle, self.c_row_ptr.data_ptr(), ctypes.byref(nnz), off),
                    "spgemm_batch_symbolic")
-        hand_over(self.stream, self.c_row_ptr)
+        c.after(self.c_row_ptr)
         self.nnz_c = int(nnz.value)
         self.row_off = list(off)
         return self.nnz_c
 
     def numeric(self):
         """Returns (c_row_ptr, c_col_idx, c_vals) of the packed C; columns are local to each product."""
-        with torch.cuda.stream(self.stream):
+        c = _Caller(self.stream)
+        with c.on():
             ci = torch.empty(max(self.nnz_c, 0), dtype=torch.int32, device=self.device)
             cv = torch.empty(max(self.nnz_c, 0), dtype=self.dtype, device=self.device)
         with torch.cuda.device(self.device):
@@ -592,7 +642,7 @@ class Batch:
                                                  ci.data_ptr() if self.nnz_c else None,
                                                  cv.data_ptr() if self.nnz_c else None), "spgemm_batch_numeric")
         self.c_col_idx, self.c_vals = ci, cv
-        hand_over(self.stream, self.c_row_ptr, ci, cv)
+        c.after(self.c_row_ptr, ci, cv)
         return self.c_row_ptr, ci, cv
 
     def product(self, p: int, row_ptr_host=None) -> DeviceCSR:
