@@ -195,6 +195,24 @@ def test_bitmap_rows_split_into_several_windows(dt):
     assert_matches_oracle(C, A, B, True)
 
 
+@pytest.mark.parametrize("b_order", ["sorted", "shuffled"])
+@pytest.mark.parametrize("shape", ["windows", "windows_and_parts"])
+def test_windowed_rows_with_sorted_and_unsorted_b(b_order, shape):
+    """Rows split into rank windows, with column-sorted and with shuffled rows
+    of B, and rows split both into rank windows and into parts of their
+    stored a_ik (every window block of every part reads the part's products
+    and keeps those of its ranks)."""
+    if shape == "windows":
+        A, B = _heavy_rows(6, 64, 65536, 1000, seed=71)      # ~40k entries per row: 2 windows
+    else:
+        A, B = _heavy_rows(2, 2048, 65536, 1000, seed=72)    # ~65k entries, 2M flop: windows and parts
+    if b_order == "shuffled":
+        B = inputs.shuffle_rows(B, seed=73)
+    C, st = gpu_product(A, B, torch.float64, True)
+    assert st["num_bin_rows"][9] > A.nrows
+    assert_matches_oracle(C, A, B, True)
+
+
 @pytest.mark.parametrize("sorted_output", [True, False])
 @pytest.mark.parametrize("dt", ["f64", "i64", "f32"])
 def test_global_table_rows(sorted_output, dt):
