@@ -77,53 +77,87 @@ __device__ __forceinline__ int num_bin_of(int64_t nnz) {
   return t < 9 ? t : kNumGlobalBin;
 }
 
-// One warp per row of A, 8 rows per 256-thread block; every lane keeps four
-// independent gathers of B's row_ptr in flight, so a long row of A costs
-// len/128 dependent steps instead of len/8.
+// Sum over entries j0, j0 + stride, ... (below r1) of A's row of the lengths
+// of the rows of B they select, four independent gathers of B's row_ptr in
+// flight per thread; indices outside A's columns or malformed rows of B raise
+// kErrCsr and count nothing.
+__device__ __forceinline__ int64_t flop_span(const Args &a, int64_t j0, int64_t r1, int stride, int64_t nnz_b) {
+  int64_t f = 0;
+  for (; j0 < r1; j0 += 4 * stride) {
+    int32_t kk[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) kk[u] = j0 + stride * u < r1 ? __ldg(a.aci + j0 + stride * u) : -1;
+    int64_t b0[4], b1[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const bool ok = j0 + stride * u < r1 && (uint64_t)(int64_t)kk[u] < (uint64_t)a.n;
+      b0[u] = ok ? __ldg(a.brp + kk[u]) : 0;
+      b1[u] = ok ? __ldg(a.brp + kk[u] + 1) : 0;
+      if (j0 + stride * u < r1 && !ok) raise_err(a.err, kErrCsr);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (!(0 <= b0[u] && b0[u] <= b1[u] && b1[u] <= nnz_b)) {
+        raise_err(a.err, kErrCsr);
+        continue;
+      }
+      f += b1[u] - b0[u];
+    }
+  }
+  return f;
+}
+
+// Rows of A with more stored entries than this are summed by the whole
+// block instead of one warp (a hub row of thousands of entries would
+// otherwise hold its warp, and the launch, for its len/128 dependent steps).
+constexpr int64_t kFlopLongRow = 1024;
+
+// One warp per row of A, 8 rows per 256-thread block; the block's long rows
+// are then summed by all 256 threads together.
 __global__ void __launch_bounds__(256)
     k_row_flop(Args a, int64_t nnz_a, int64_t nnz_b, int64_t bitmap_min, int64_t *__restrict__ flop,
                uint8_t *__restrict__ rbin, int32_t *__restrict__ nnz_row, DevCounters *dc) {
   __shared__ unsigned int hist[kNumSymBins];
   __shared__ unsigned long long hflop[kNumSymBins];
   __shared__ unsigned long long s_tot, s_max, s_maxg, s_extra;
+  __shared__ unsigned long long s_long_f[8];
+  __shared__ unsigned s_long;  // bit w: row w of the block is long
   if (threadIdx.x < kNumSymBins) {
     hist[threadIdx.x] = 0;
     hflop[threadIdx.x] = 0;
   }
-  if (threadIdx.x == 0) s_tot = s_max = s_maxg = s_extra = 0;
+  if (threadIdx.x < 8) s_long_f[threadIdx.x] = 0;
+  if (threadIdx.x == 0) s_tot = s_max = s_maxg = s_extra = s_long = 0;
   __syncthreads();
-  const int sub = threadIdx.x & 31;
-  const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int sub = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t row = (int64_t)blockIdx.x * 8 + warp;
   int64_t f = 0;
+  int64_t r0 = 0, r1 = 0;
   if (row < a.m) {
-    int64_t r0 = a.arp[row], r1 = a.arp[row + 1];
+    r0 = a.arp[row];
+    r1 = a.arp[row + 1];
     if (!(0 <= r0 && r0 <= r1 && r1 <= nnz_a)) {
       if (sub == 0) raise_err(a.err, kErrCsr);
       r0 = r1 = 0;
     }
-    for (int64_t j0 = r0 + sub; j0 < r1; j0 += 128) {
-      int32_t kk[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) kk[u] = j0 + 32 * u < r1 ? __ldg(a.aci + j0 + 32 * u) : -1;
-      int64_t b0[4], b1[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const bool ok = j0 + 32 * u < r1 && (uint64_t)(int64_t)kk[u] < (uint64_t)a.n;
-        b0[u] = ok ? __ldg(a.brp + kk[u]) : 0;
-        b1[u] = ok ? __ldg(a.brp + kk[u] + 1) : 0;
-        if (j0 + 32 * u < r1 && !ok) raise_err(a.err, kErrCsr);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (!(0 <= b0[u] && b0[u] <= b1[u] && b1[u] <= nnz_b)) {
-          raise_err(a.err, kErrCsr);
-          continue;
-        }
-        f += b1[u] - b0[u];
-      }
+    if (r1 - r0 > kFlopLongRow) {
+      if (sub == 0) atomicOr(&s_long, 1u << warp);
+    } else {
+      f = flop_span(a, r0 + sub, r1, 32, nnz_b);
     }
   }
-  f = warp_sum(f);
+  __syncthreads();
+  const unsigned longs = s_long;
+  for (int w = 0; w < 8; ++w) {
+    if (!((longs >> w) & 1u)) continue;
+    const int64_t rw = (int64_t)blockIdx.x * 8 + w;  // a valid row, checked by its warp
+    int64_t g = flop_span(a, (int64_t)a.arp[rw] + threadIdx.x, a.arp[rw + 1], 256, nnz_b);
+    g = warp_sum(g);
+    if (sub == 0 && g) atomicAdd(&s_long_f[w], (unsigned long long)g);
+  }
+  if (longs) __syncthreads();
+  if ((longs >> warp) & 1u) f = (int64_t)s_long_f[warp];
+  else f = warp_sum(f);
   if (sub == 0 && row < a.m) {
     flop[row] = f;
     const int64_t bound = f < a.k ? f : a.k;
