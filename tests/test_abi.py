@@ -89,3 +89,41 @@ def test_binding_refuses_to_run_without_the_library(monkeypatch, tmp_path):
     monkeypatch.setattr(binding, "library_path", lambda: str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not built"):
         binding.library()
+
+
+def test_host_entry_point_checks_before_any_cuda_call(lib):
+    """spgemm_host validates its arguments, and the host row pointers of A
+    that index its row blocks, before it touches the device."""
+    import numpy as np
+    from paper_1804_01698_gb300 import binding
+    rp = np.array([0, 1, 3], dtype=np.int32)           # 2 rows, 3 entries
+    ci = np.array([0, 1, 2], dtype=np.int32)
+    v = np.ones(3)
+    a = binding.CsrDesc(2, 3, 3, rp.ctypes.data, ci.ctypes.data, v.ctypes.data)
+    b_bad = binding.CsrDesc(4, 3, 0, rp.ctypes.data, None, None)   # 3 != 4
+    b_ok = binding.CsrDesc(3, 3, 0, np.zeros(4, np.int32).ctypes.data, None, None)
+    calls = []
+
+    def alloc(nbytes, _ctx):
+        calls.append(nbytes)
+        return None
+
+    cb = binding.ALLOC_FN(alloc)
+    P, I64 = ctypes.c_void_p, ctypes.c_int64
+    out = [P(), P(), P()]
+    nnz = I64(-1)
+
+    def call(A, B, dtype=2, flags=1, alloc_fn=cb):
+        return lib.spgemm_host(ctypes.byref(A), ctypes.byref(B), dtype, flags, None, 0, alloc_fn, None,
+                               ctypes.byref(out[0]), ctypes.byref(out[1]), ctypes.byref(out[2]), ctypes.byref(nnz))
+
+    assert call(a, b_bad) == -1                         # inner dimensions differ
+    assert call(a, b_ok, dtype=9) == -1                 # value type
+    assert call(a, b_ok, flags=4) == -1                 # SPGEMM_TIMING needs a plan the caller keeps
+    assert b"TIMING" in lib.spgemm_last_error()
+    assert call(a, b_ok, alloc_fn=ctypes.cast(None, binding.ALLOC_FN)) == -1   # no allocator
+    short = np.array([0, 1, 2], dtype=np.int32)        # row_ptr[m] = 2 != nnz = 3
+    a_short = binding.CsrDesc(2, 3, 3, short.ctypes.data, ci.ctypes.data, v.ctypes.data)
+    assert call(a_short, b_ok) == -2
+    assert b"row_ptr" in lib.spgemm_last_error()
+    assert calls == [] and nnz.value == 0 and all(o.value is None for o in out)
