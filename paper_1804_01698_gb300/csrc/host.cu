@@ -14,6 +14,7 @@
 // phase (apart from the first block's) under that copy.
 #include <algorithm>
 #include <cstring>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -111,9 +112,42 @@ constexpr int64_t kRowBlockMinFlop = int64_t(1) << 26;
 
 using namespace sg;
 
+// A's row pointers are read on the host: refuse device memory, which the
+// host cannot dereference.  Without a usable driver the call cannot tell,
+// and the pointer is taken for host memory.
+static bool device_only(const void *ptr) {
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeDevice;
+}
+
+static int spgemm_host_impl(const spgemm_csr *A, const spgemm_csr *B, int dtype, unsigned flags, void *stream,
+                            int row_blocks, spgemm_alloc_fn host_alloc, void *alloc_ctx, int32_t **c_row_ptr,
+                            int32_t **c_col_idx, void **c_vals, int64_t *nnz_c);
+
 extern "C" int spgemm_host(const spgemm_csr *A, const spgemm_csr *B, int dtype, unsigned flags, void *stream,
                            int row_blocks, spgemm_alloc_fn host_alloc, void *alloc_ctx, int32_t **c_row_ptr,
                            int32_t **c_col_idx, void **c_vals, int64_t *nnz_c) {
+  // nothing may throw across the C boundary: host-side vectors sized by m
+  // can fail to allocate
+  try {
+    return spgemm_host_impl(A, B, dtype, flags, stream, row_blocks, host_alloc, alloc_ctx, c_row_ptr, c_col_idx,
+                            c_vals, nnz_c);
+  } catch (const std::bad_alloc &) {
+    set_last_error("spgemm_host: host memory exhausted");
+    return SPGEMM_ERR_OUT_OF_MEMORY;
+  } catch (...) {
+    set_last_error("spgemm_host: unexpected host-side failure");
+    return SPGEMM_ERR_DEVICE;
+  }
+}
+
+static int spgemm_host_impl(const spgemm_csr *A, const spgemm_csr *B, int dtype, unsigned flags, void *stream,
+                            int row_blocks, spgemm_alloc_fn host_alloc, void *alloc_ctx, int32_t **c_row_ptr,
+                            int32_t **c_col_idx, void **c_vals, int64_t *nnz_c) {
   NvtxRange nvtx("spgemm_host");
   if (!host_alloc || !c_row_ptr || !c_col_idx || !c_vals || !nnz_c) return SPGEMM_ERR_INVALID_ARGUMENT;
   *c_row_ptr = nullptr;
@@ -125,6 +159,10 @@ extern "C" int spgemm_host(const spgemm_csr *A, const spgemm_csr *B, int dtype, 
   if (dtype != SPGEMM_I64 && dtype != SPGEMM_F32 && dtype != SPGEMM_F64) return SPGEMM_ERR_INVALID_ARGUMENT;
   if (flags & SPGEMM_TIMING) {
     set_last_error("spgemm_host: SPGEMM_TIMING needs a plan the caller keeps; use spgemm_plan_create");
+    return SPGEMM_ERR_INVALID_ARGUMENT;
+  }
+  if (device_only(A->row_ptr)) {
+    set_last_error("spgemm_host: A's row_ptr is device memory; spgemm_host takes host arrays (see spgemm())");
     return SPGEMM_ERR_INVALID_ARGUMENT;
   }
   const int64_t m = A->nrows;

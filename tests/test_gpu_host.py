@@ -134,3 +134,22 @@ def test_rmat16_full_size_end_to_end():
     arena = sg.HostArena(sg.HostArena.bytes_for(A.nrows, expect[0].nnz, 8))
     C = sg.spgemm_host(P, P, True, arena=arena)
     assert_matches_oracle(_on_device(C), A, B, True, expect=expect)
+
+
+def test_device_pointers_are_refused():
+    """A's row pointers are read on the host, so device arrays are refused
+    with an argument error instead of a host fault."""
+    import ctypes
+    from paper_1804_01698_gb300 import binding as sg
+    A = inputs.rmat(8, 8, seed=4)
+    dA = sg.to_device(A)
+    lib = sg.library()
+    d = dA.desc()
+    out = [ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()]
+    nnz = ctypes.c_int64()
+    cb = sg.ALLOC_FN(lambda n, c: None)
+    status = lib.spgemm_host(ctypes.byref(d), ctypes.byref(d), sg.SPGEMM_F64, sg.SPGEMM_SORTED, None, 0, cb, None,
+                             ctypes.byref(out[0]), ctypes.byref(out[1]), ctypes.byref(out[2]), ctypes.byref(nnz))
+    assert status == -1
+    assert b"device memory" in lib.spgemm_last_error()
+    torch.cuda.synchronize()
