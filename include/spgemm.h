@@ -353,16 +353,22 @@ SPGEMM_API int spgemm_host(const spgemm_csr *A, const spgemm_csr *B, int dtype, 
  * `stream`, which is synchronised once before the call returns.
  *
  * It allocates nothing: no cudaMalloc, no cudaFree, no allocating library
- * routine.  Its scratch is one static device array of 32 MiB + 256 bytes
- * that every GPU holds from the moment the library is loaded on it until the
- * process exits.  That array holds 64 hash tables of 131072 keys; a row of C
- * whose key bound min(flop_i, ncols(B)) is 131072 or more is refused with
+ * routine.  Its scratch is one static device array of 32 MiB + 256 bytes.
+ * CUDA places it on a device when the library's module is first used there
+ * (modules load lazily: at the first kernel launch of this library on that
+ * device, or at this entry point's first call, which looks up the array's
+ * device address), and it stays until the process exits.  So make the first
+ * call on each device, or any other call of this library on it, before the
+ * region in which the caller cannot allocate, and before any stream
+ * capture.  The array holds 64 hash tables of 131072 keys; a row of C whose
+ * key bound min(flop_i, ncols(B)) is 131072 or more is refused with
  * SPGEMM_ERR_INVALID_ARGUMENT and a message in spgemm_last_error().
+ * Malformed CSR input (a column index outside its matrix, a bad row_ptr)
+ * gives SPGEMM_ERR_INVALID_CSR; such rows are never hashed.
  *
- * The first call on a device looks up the array's device address; make
- * that first call before any stream capture.  Every call shares the array
- * (the call clears the counters it needs): calls that overlap on the GPU,
- * from different streams or threads, race and give wrong results.
+ * Every call shares the array (the call clears the counters it needs):
+ * calls that overlap on the GPU, from different streams or threads, race
+ * and give wrong results.
  */
 SPGEMM_API int spgemm_symbolic_noalloc(const spgemm_csr *A, const spgemm_csr *B, int32_t *c_row_ptr,
                                        int64_t *nnz_c, void *stream);

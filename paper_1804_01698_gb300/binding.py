@@ -442,9 +442,13 @@ def spgemm_symbolic_noalloc(A: DeviceCSR, B: DeviceCSR, c_row_ptr: torch.Tensor,
     For callers that must not allocate device memory while they run: the
     library uses a static device array instead (one call at a time per GPU)."""
     lib = library()
+    dev = A.row_ptr.device
+    if (c_row_ptr.dtype != torch.int32 or not c_row_ptr.is_contiguous() or c_row_ptr.numel() < A.nrows + 1
+            or c_row_ptr.device != dev):
+        raise ValueError(f"c_row_ptr must be a contiguous int32 tensor of at least {A.nrows + 1} elements on {dev}")
     a, b = A.desc(), B.desc()
     nnz = ctypes.c_int64()
-    s = stream if stream is not None else torch.cuda.current_stream(A.row_ptr.device)
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
     _after_caller(s)
     with torch.cuda.device(A.row_ptr.device):
         _check(lib.spgemm_symbolic_noalloc(ctypes.byref(a), ctypes.byref(b), c_row_ptr.data_ptr(), ctypes.byref(nnz),

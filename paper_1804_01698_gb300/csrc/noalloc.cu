@@ -7,9 +7,13 @@
 // spgemm_symbolic_noalloc(): it counts the entries of every row of C = A*B
 // and writes C's row_ptr and nnz(C), like spgemm_symbolic, but its scratch
 // (the per-block hash tables and a few counters) is one file-scope device
-// array, g_noalloc_scratch, that exists from the moment the library is
-// loaded on a device until the process exits.  It makes no cudaMalloc or
-// cudaFree call and calls no library routine that allocates.
+// array, g_noalloc_scratch, that is placed on a device when the library's
+// module is first used there (CUDA loads modules lazily: at the first kernel
+// launch of this library or this entry point's first cudaGetSymbolAddress
+// on that device) and stays until the process exits.  So the first call on
+// each device, or any earlier call of this library on it, must come before
+// the region in which the caller cannot allocate; later calls make no
+// cudaMalloc or cudaFree call and call no library routine that allocates.
 //
 // The kernel is the global-table form of the symbolic phase: block b owns
 // one hash table of kNoallocSlots keys inside the array and walks rows b,
@@ -55,26 +59,30 @@ __global__ void __launch_bounds__(1024, 1)
   for (int64_t i = blockIdx.x; i < a.m; i += gridDim.x) {
     // row flop and input checks (as in the flop pass)
     int64_t r0 = a.arp[i], r1 = a.arp[i + 1];
-    bool bad = !(0 <= r0 && r0 <= r1 && r1 <= nnz_a);
-    long long f = 0;
-    if (!bad) {
+    const bool bad_rp = !(0 <= r0 && r0 <= r1 && r1 <= nnz_a);
+    long long f = 0, nbad = 0;
+    if (!bad_rp) {
       for (int64_t j = r0 + threadIdx.x; j < r1; j += blockDim.x) {
         const int32_t kk = a.aci[j];
         if ((uint64_t)(int64_t)kk >= (uint64_t)a.n) {
-          raise_err(a.err, kErrCsr);
+          ++nbad;
           continue;
         }
         const int64_t b0 = a.brp[kk], b1 = a.brp[kk + 1];
         if (!(0 <= b0 && b0 <= b1 && b1 <= nnz_b)) {
-          raise_err(a.err, kErrCsr);
+          ++nbad;
           continue;
         }
         f += b1 - b0;
       }
-    } else if (threadIdx.x == 0) {
-      raise_err(a.err, kErrCsr);
     }
     f = block_sum(f, red);
+    // A row with a column outside A, or one that selects a malformed row of
+    // B, is never hashed: the row loop below would read B's row_ptr and
+    // col_idx at the unchecked addresses.
+    nbad = block_sum(nbad, red);
+    const bool bad = bad_rp || nbad > 0;
+    if (bad && threadIdx.x == 0) raise_err(a.err, kErrCsr);
     const long long bound = f < a.k ? f : a.k;
     int cnt = 0;
     if (!bad && bound > 0) {
