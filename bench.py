@@ -194,6 +194,14 @@ def kernel_units(name: str, stats: dict) -> tuple[int, str]:
 
 # ---------------------------------------------------------------------------- reference arm
 
+def workload_config(name: str, A, B, flop: int, nnz_c: int, sorted_output: bool, replicas: int) -> dict:
+    """The `config` of a single-product bench line, the same for both arms."""
+    from paper_1804_01698_gb300 import inputs
+    return {"workload": name, "desc": inputs.WORKLOADS[name]["desc"], "m": A.nrows, "n": A.ncols, "k": B.ncols,
+            "nnz_a": A.nnz, "nnz_b": B.nnz, "flop": flop, "nnz_c": int(nnz_c), "sorted": bool(sorted_output),
+            "l2": "flushed between steps (256 MiB write, outside the events)", "replicas": replicas}
+
+
 def run_reference(args) -> int:
     import oracle
     from paper_1804_01698_gb300 import inputs
@@ -206,14 +214,16 @@ def run_reference(args) -> int:
                           f"{args.workload} is compared against one GPU call per product instead"}), flush=True)
         return 0
     A, B, sorted_default = inputs.workload(args.workload)
+    sorted_output = sorted_default and not args.unsorted
     cores = len(os.sched_getaffinity(0))
     flop = int(oracle.row_flop(A, B).sum())
+    nnz_c = 0
     for _ in range(args.warmup):
-        oracle.spgemm(A, B, nthreads=cores)
+        nnz_c = oracle.spgemm(A, B, nthreads=cores)[0].nnz
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.spgemm(A, B, nthreads=cores)
+        nnz_c = oracle.spgemm(A, B, nthreads=cores)[0].nnz
         times.append(time.perf_counter() - t0)
     mean = sum(times) / len(times)
     value = 2 * flop / mean / 1e9
@@ -222,8 +232,7 @@ def run_reference(args) -> int:
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if A.vals.dtype == np.float64 else "f32",
         "data": "synthetic",
-        "config": {"workload": args.workload, "m": A.nrows, "n": A.ncols, "k": B.ncols, "nnz_a": A.nnz,
-                   "nnz_b": B.nnz, "flop": flop, "sorted": True},
+        "config": workload_config(args.workload, A, B, flop, nnz_c, sorted_output, args.gpus),
         "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
                          "sample": "the whole product per step (dense-SPA Gustavson, rows split by RowsToThreads)"},
         "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -995,10 +1004,7 @@ def main() -> int:
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {torch.float64: "f64", torch.float32: "f32", torch.int64: "int64"}[vdtype],
             "data": "synthetic",
-            "config": {"workload": args.workload, "desc": inputs.WORKLOADS[args.workload]["desc"], "m": A.nrows,
-                       "n": A.ncols, "k": B.ncols, "nnz_a": A.nnz, "nnz_b": B.nnz, "flop": flop, "nnz_c": nnz_c,
-                       "sorted": sorted_output, "l2": "flushed between steps (256 MiB write, outside the events)",
-                       "replicas": world},
+            "config": workload_config(args.workload, A, B, flop, nnz_c, sorted_output, world),
             "roofline": roofline,
             "hbm_roofline_path": hbm_roofline,
             "cpu_baseline": cpu,
