@@ -136,6 +136,10 @@ typedef struct {
     int64_t sym_probes, sym_inserts;       /* hash-table slot reads (chunk reads under SPGEMM_PROBE_CHUNK4) and
                                               key insertions of the symbolic phase (SPGEMM_COUNT_PROBES only) */
     int64_t num_probes, num_inserts;       /* the same for the numeric phase */
+    int64_t nnz_a_walked;      /* stored a_ik the phases walk: nnz(A), or fewer when the plan dropped the
+                                  entries that select an empty row of B (fewer than half of A's were kept) */
+    int64_t long_rows;         /* long rows of B the bitmap rows take whole (spgemm_tuning::long_row_min) */
+    int64_t long_entries;      /* their entries */
 } spgemm_stats;
 
 typedef struct spgemm_plan_s *spgemm_plan_t;
@@ -169,12 +173,26 @@ SPGEMM_API int spgemm_plan_create(spgemm_plan_t *out, const spgemm_csr *A, const
  *                     0 = 2^31-1 (int32 indexing); a smaller limit caps the
  *                     output memory of a product (and lets tests reach the
  *                     overflow path on small inputs).
+ *   long_row_min      rows of B with at least this many entries are "long
+ *                     rows": inside bitmap rows of A their products are
+ *                     taken from a copy of the long row grouped by column
+ *                     owner (numeric) and its column bitmap (symbolic)
+ *                     instead of one by one: 0 = max(512, k/128); -1 = no
+ *                     long rows; otherwise a positive length.
+ *   warp_load_pct     largest key bound of a warp hash table, in percent of
+ *                     its slots (Sec. 4.2.1 sizes a table from the row's
+ *                     bound; lower loads shorten probes): 0 = 50; else
+ *                     5..95.
+ *   block_load_pct    the same for block hash tables: 0 = 75; else 5..95.
  */
 typedef struct {
     int32_t lanes_per_entry;
     int32_t reserved; /* must be 0 */
     int64_t bitmap_min_bound;
     int64_t max_nnz_c;
+    int64_t long_row_min;
+    int32_t warp_load_pct;
+    int32_t block_load_pct;
 } spgemm_tuning;
 
 /* spgemm_plan_create with a tuning (NULL: the defaults).  Out-of-range
@@ -299,6 +317,52 @@ SPGEMM_API int spgemm_batch_symbolic(spgemm_batch_t batch, int32_t *c_row_ptr, i
 SPGEMM_API int spgemm_batch_numeric(spgemm_batch_t batch, const int32_t *c_row_ptr, int32_t *c_col_idx, void *c_vals);
 SPGEMM_API spgemm_plan_t spgemm_batch_plan(spgemm_batch_t batch);
 SPGEMM_API int spgemm_batch_destroy(spgemm_batch_t batch);
+
+/*
+ * Batched products in ONE CUDA graph launch.  The paper runs one product at
+ * a time; balancing rows by flop over the workers (Sec. 4.1, Fig.
+ * "RowsToThreads") is what this batched form applies across products: every
+ * row of every product goes to the row bin its flop selects, and the bins
+ * run over all products together.
+ *
+ * spgemm_bgraph_create plans the batch once: it splits the products into
+ * waves of consecutive products whose C fits int32 indexing and `wave_nnz`
+ * entries (0: 2^31-1), runs a planning pass (flop pass and symbolic phase,
+ * host-synchronised) to size every workspace and a pool for each wave's C
+ * (its nnz(C) times 1 + pool_slack), and captures, for every wave in order,
+ * the packing of its operands, the flop pass, the symbolic kernels, the
+ * row_ptr scan, the numeric kernels, the column unpacking and the copy of
+ * the per-product counts to pinned host memory into one CUDA graph.  No
+ * step of the graph reads a count on the host: the bin kernels find their
+ * rows in device memory and walk them with grids sized to stay resident.
+ * A and B are arrays of nprod device CSR descriptors, borrowed until
+ * destroy; flags as for spgemm_plan_create without SPGEMM_TIMING and
+ * SPGEMM_COUNT_PROBES; column bitmaps are not used (rows above the shared
+ * tables use global-memory tables sized by the planning pass).
+ *
+ * spgemm_bgraph_launch enqueues the whole batch as one cudaGraphLaunch on
+ * `stream`, recomputing every product from the operands' current contents.
+ * spgemm_bgraph_wait synchronises that stream and returns the status:
+ * SPGEMM_ERR_OUT_OF_MEMORY when a product no longer fits what was planned
+ * (nothing is then written outside the pools), SPGEMM_ERR_INVALID_CSR for
+ * malformed input.  spgemm_bgraph_product_nnz gives nnz(C_p) (host) and
+ * spgemm_bgraph_product_copy copies C_p into caller buffers (device: m_p+1
+ * row pointers from 0, nnz col_idx and values), stream-ordered on `stream`.
+ * spgemm_bgraph_info reports the waves, the kernel nodes of the graph and
+ * the device bytes held.  There are no waits on the device inside the
+ * graph: its kernels follow each other in stream order.
+ */
+typedef struct spgemm_bgraph_s *spgemm_bgraph_t;
+SPGEMM_API int spgemm_bgraph_create(spgemm_bgraph_t *out, int64_t nprod, const spgemm_csr *A, const spgemm_csr *B,
+                                    int dtype, unsigned flags, void *stream, const spgemm_tuning *tuning,
+                                    int64_t wave_nnz, double pool_slack);
+SPGEMM_API int spgemm_bgraph_launch(spgemm_bgraph_t graph, void *stream);
+SPGEMM_API int spgemm_bgraph_wait(spgemm_bgraph_t graph);
+SPGEMM_API int spgemm_bgraph_product_nnz(spgemm_bgraph_t graph, int64_t p, int64_t *nnz);
+SPGEMM_API int spgemm_bgraph_product_copy(spgemm_bgraph_t graph, int64_t p, int32_t *c_row_ptr, int32_t *c_col_idx,
+                                          void *c_vals, void *stream);
+SPGEMM_API int spgemm_bgraph_info(spgemm_bgraph_t graph, int64_t *waves, int64_t *kernel_nodes, int64_t *bytes);
+SPGEMM_API int spgemm_bgraph_destroy(spgemm_bgraph_t graph);
 
 /*
  * C = A*B with A, B and C in HOST memory, the copy of C to the host

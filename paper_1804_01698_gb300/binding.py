@@ -61,22 +61,29 @@ class Stats(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_int64), ("kernel_launches", ctypes.c_int32), ("state", ctypes.c_int32),
                 ("sym_bin_flop", ctypes.c_int64 * MAX_BINS), ("num_bin_flop", ctypes.c_int64 * MAX_BINS),
                 ("sym_probes", ctypes.c_int64), ("sym_inserts", ctypes.c_int64),
-                ("num_probes", ctypes.c_int64), ("num_inserts", ctypes.c_int64)]
+                ("num_probes", ctypes.c_int64), ("num_inserts", ctypes.c_int64),
+                ("nnz_a_walked", ctypes.c_int64), ("long_rows", ctypes.c_int64), ("long_entries", ctypes.c_int64)]
 
 
 class Tuning(ctypes.Structure):
     _fields_ = [("lanes_per_entry", ctypes.c_int32), ("reserved", ctypes.c_int32), ("bitmap_min_bound", ctypes.c_int64),
-                ("max_nnz_c", ctypes.c_int64)]
+                ("max_nnz_c", ctypes.c_int64), ("long_row_min", ctypes.c_int64), ("warp_load_pct", ctypes.c_int32),
+                ("block_load_pct", ctypes.c_int32)]
+
+
+TUNING_KEYS = ("lanes_per_entry", "bitmap_min_bound", "max_nnz_c", "long_row_min", "warp_load_pct", "block_load_pct")
 
 
 def _tuning(t):
-    """A spgemm_tuning from a dict {lanes_per_entry, bitmap_min_bound, max_nnz_c} (None: defaults)."""
+    """A spgemm_tuning from a dict with keys among TUNING_KEYS (None: defaults;
+    a missing key takes the default, 0)."""
     if t is None:
         return None
-    unknown = set(t) - {"lanes_per_entry", "bitmap_min_bound", "max_nnz_c"}
+    unknown = set(t) - set(TUNING_KEYS)
     if unknown:
         raise ValueError(f"unknown tuning keys {sorted(unknown)}")
-    return Tuning(int(t.get("lanes_per_entry", 0)), 0, int(t.get("bitmap_min_bound", 0)), int(t.get("max_nnz_c", 0)))
+    return Tuning(int(t.get("lanes_per_entry", 0)), 0, int(t.get("bitmap_min_bound", 0)), int(t.get("max_nnz_c", 0)),
+                  int(t.get("long_row_min", 0)), int(t.get("warp_load_pct", 0)), int(t.get("block_load_pct", 0)))
 
 
 class KernelTime(ctypes.Structure):
@@ -90,7 +97,9 @@ EXPORTED = ("spgemm_plan_create", "spgemm_symbolic", "spgemm_numeric", "spgemm_p
             "spgemm_plan_row_nnz", "spgemm_plan_kernel_times", "spgemm", "spgemm_status_string",
             "spgemm_last_error", "spgemm_symbolic_noalloc", "spgemm_batch_create", "spgemm_batch_symbolic",
             "spgemm_batch_numeric", "spgemm_batch_destroy", "spgemm_plan_create_tuned", "spgemm_batch_create_tuned",
-            "spgemm_numeric_graph", "spgemm_host")
+            "spgemm_numeric_graph", "spgemm_host", "spgemm_bgraph_create", "spgemm_bgraph_launch",
+            "spgemm_bgraph_wait", "spgemm_bgraph_product_nnz", "spgemm_bgraph_product_copy", "spgemm_bgraph_info",
+            "spgemm_bgraph_destroy")
 
 
 def library_path() -> str:
@@ -136,6 +145,14 @@ def library():
                            ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(I64)]
     lib.spgemm_host.argtypes = [ctypes.POINTER(CsrDesc), ctypes.POINTER(CsrDesc), I32, ctypes.c_uint, P, I32, ALLOC_FN,
                                 P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(I64)]
+    lib.spgemm_bgraph_create.argtypes = [ctypes.POINTER(P), I64, ctypes.POINTER(CsrDesc), ctypes.POINTER(CsrDesc),
+                                         I32, ctypes.c_uint, P, ctypes.POINTER(Tuning), I64, ctypes.c_double]
+    lib.spgemm_bgraph_launch.argtypes = [P, P]
+    lib.spgemm_bgraph_wait.argtypes = [P]
+    lib.spgemm_bgraph_product_nnz.argtypes = [P, I64, ctypes.POINTER(I64)]
+    lib.spgemm_bgraph_product_copy.argtypes = [P, I64, P, P, P, P]
+    lib.spgemm_bgraph_info.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)]
+    lib.spgemm_bgraph_destroy.argtypes = [P]
     for name in EXPORTED:
         getattr(lib, name).restype = ctypes.c_int
     lib.spgemm_status_string.argtypes = [I32]
@@ -717,3 +734,83 @@ def spgemm_batch_numeric(batch: Batch):
 
 def spgemm_batch_destroy(batch: Batch) -> None:
     batch.destroy()
+
+
+class BatchGraph:
+    """Independent products C_p = A_p * B_p, all of them in one CUDA graph
+    launch; mirrors spgemm_bgraph_create / _launch / _wait / _product_*.
+    The operands stay borrowed (their tensors must outlive the object):
+    every launch recomputes every product from their current contents."""
+
+    def __init__(self, As, Bs, sorted_output: bool = True, stream=None, probe: str = "linear",
+                 tuning: dict | None = None, hash: str = "high", wave_nnz: int = 0, pool_slack: float = 0.0):
+        self.lib = library()
+        if len(As) != len(Bs) or not As:
+            raise ValueError("need the same positive number of A and B operands")
+        self.dtype = As[0].vals.dtype
+        if self.dtype not in _DTYPES or any(m.vals.dtype != self.dtype for m in list(As) + list(Bs)):
+            raise TypeError("all operands must share one value dtype among int64, float32, float64")
+        self.As, self.Bs = list(As), list(Bs)
+        self.device = As[0].row_ptr.device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        flags = (SPGEMM_SORTED if sorted_output else SPGEMM_UNSORTED) | _PROBES[probe] | _HASHES[hash]
+        n = len(As)
+        self._a = (CsrDesc * n)(*[m.desc() for m in As])
+        self._b = (CsrDesc * n)(*[m.desc() for m in Bs])
+        h = ctypes.c_void_p()
+        _after_caller(self.stream)
+        with torch.cuda.device(self.device):
+            self._tuning = _tuning(tuning)
+            _check(self.lib.spgemm_bgraph_create(ctypes.byref(h), n, self._a, self._b, _DTYPES[self.dtype], flags,
+                                                 _stream_ptr(self.stream),
+                                                 ctypes.byref(self._tuning) if self._tuning else None,
+                                                 int(wave_nnz), float(pool_slack)), "spgemm_bgraph_create")
+        self.handle = h
+        self.nprod = n
+
+    def launch(self):
+        """One cudaGraphLaunch of the whole batch on the object's stream (no host sync)."""
+        with torch.cuda.device(self.device):
+            _check(self.lib.spgemm_bgraph_launch(self.handle, _stream_ptr(self.stream)), "spgemm_bgraph_launch")
+
+    def wait(self):
+        with torch.cuda.device(self.device):
+            _check(self.lib.spgemm_bgraph_wait(self.handle), "spgemm_bgraph_wait")
+
+    def info(self) -> dict:
+        w, k, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(self.lib.spgemm_bgraph_info(self.handle, ctypes.byref(w), ctypes.byref(k), ctypes.byref(b)),
+               "spgemm_bgraph_info")
+        return {"waves": w.value, "kernel_nodes": k.value, "bytes": b.value}
+
+    def product(self, p: int) -> DeviceCSR:
+        """C_p of the last launch (after wait()), copied into new tensors."""
+        nnz = ctypes.c_int64()
+        _check(self.lib.spgemm_bgraph_product_nnz(self.handle, p, ctypes.byref(nnz)), "spgemm_bgraph_product_nnz")
+        A, B = self.As[p], self.Bs[p]
+        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+            rp = torch.empty(A.nrows + 1, dtype=torch.int32, device=self.device)
+            ci = torch.empty(max(nnz.value, 0), dtype=torch.int32, device=self.device)
+            cv = torch.empty(max(nnz.value, 0), dtype=self.dtype, device=self.device)
+            _check(self.lib.spgemm_bgraph_product_copy(self.handle, p, rp.data_ptr(),
+                                                       ci.data_ptr() if nnz.value else None,
+                                                       cv.data_ptr() if nnz.value else None,
+                                                       _stream_ptr(self.stream)), "spgemm_bgraph_product_copy")
+        return DeviceCSR(A.nrows, B.ncols, rp, ci, cv)
+
+    def destroy(self):
+        if self.handle:
+            self.lib.spgemm_bgraph_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

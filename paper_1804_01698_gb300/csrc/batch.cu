@@ -118,10 +118,13 @@ __global__ void __launch_bounds__(256)
 // One warp per row of C: subtract the column offset of the row's product.
 __global__ void __launch_bounds__(256)
     k_batch_unpack(const int32_t *__restrict__ c_rp, int32_t *__restrict__ c_ci, int64_t m,
-                   const long long *__restrict__ row_off, const long long *__restrict__ col_off, int64_t nprod) {
+                   const long long *__restrict__ row_off, const long long *__restrict__ col_off, int64_t nprod,
+                   const uint32_t *abort) {
   const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= m) return;
+  // graph mode: C did not fit its pool, so neither its row pointers nor its columns are valid
+  if (abort && (*(volatile const uint32_t *)abort & (kErrOverflow | kErrCapacity))) return;
   int64_t lo = 0, hi = nprod - 1;  // last product whose first row is <= row
   while (lo < hi) {
     const int64_t mid = (lo + hi + 1) >> 1;
@@ -149,6 +152,10 @@ struct spgemm_batch_s {
   std::vector<long long> row_off;  // host copy, nprod + 1
   int64_t m, k;
   int state;  // 0 planned, 1 symbolic done, 2 numeric done
+  // packing (batch graphs repack on every launch)
+  sg::BatchDev *d_desc;
+  int64_t chunks, an, bm, bn, widest;
+  int vsize;
 };
 
 namespace {
@@ -168,12 +175,16 @@ int spgemm_batch_create(spgemm_batch_t *out, int64_t nprod, const spgemm_csr *A,
   return spgemm_batch_create_tuned(out, nprod, A, B, dtype, flags, stream, nullptr);
 }
 
-int spgemm_batch_create_tuned(spgemm_batch_t *out, int64_t nprod, const spgemm_csr *A, const spgemm_csr *B,
-                              int dtype, unsigned flags, void *stream, const spgemm_tuning *tuning) {
-  NvtxRange nvtx("spgemm_batch_create");
-  if (!out) return SPGEMM_ERR_INVALID_ARGUMENT;
+}  // extern "C"
+
+namespace sg {
+
+// Checks the products, allocates the packed operands and their offsets and
+// packs them once (synchronising `stream` to read the packing's error word).
+// The batch has no plan yet.
+int batch_pack(spgemm_batch_s **out, int64_t nprod, const spgemm_csr *A, const spgemm_csr *B, int dtype,
+               cudaStream_t stream) {
   *out = nullptr;
-  set_last_error("");
   if (nprod < 1 || !A || !B) return SPGEMM_ERR_INVALID_ARGUMENT;
   if (dtype != SPGEMM_I64 && dtype != SPGEMM_F32 && dtype != SPGEMM_F64) return SPGEMM_ERR_INVALID_ARGUMENT;
   const int vsize = dtype == SPGEMM_F32 ? 4 : 8;
@@ -280,19 +291,60 @@ int spgemm_batch_create_tuned(spgemm_batch_t *out, int64_t nprod, const spgemm_c
     set_last_error("a product of the batch has an index out of range or a malformed row_ptr");
     return SPGEMM_ERR_INVALID_CSR;
   }
-  spgemm_csr pa{am, bm, an, b->arp, b->aci, b->av};
-  spgemm_csr pb{bm, bk, bn, b->brp, b->bci, b->bv};
-  int rc = spgemm_plan_create_tuned(&b->plan, &pa, &pb, dtype, flags, stream, tuning);
+  b->chunks = chunks;
+  b->d_desc = d_desc;
+  b->vsize = vsize;
+  b->an = an;
+  b->bm = bm;
+  b->bn = bn;
+  int64_t widest = 0;
+  for (int64_t q = 0; q < nprod; ++q) widest = B[q].ncols > widest ? B[q].ncols : widest;
+  b->widest = widest;
+  *out = b;
+  return SPGEMM_OK;
+}
+
+// The packing kernel again (the operands' current contents), on `st`.
+cudaError_t batch_repack(spgemm_batch_s *b, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(b->d_err, 0, 4, st);
+  if (e != cudaSuccess) return e;
+  k_batch_pack<<<(unsigned)b->chunks, 256, 0, st>>>(b->d_desc, b->nprod, b->vsize, b->arp, b->aci,
+                                                      (unsigned char *)b->av, b->brp, b->bci, (unsigned char *)b->bv,
+                                                      b->d_err);
+  return cudaGetLastError();
+}
+
+void batch_free(spgemm_batch_s *b) {
+  if (!b) return;
+  if (b->plan) spgemm_plan_destroy(b->plan);
+  if (b->ws) cudaFreeAsync(b->ws, b->stream);
+  delete b;
+}
+
+}  // namespace sg
+
+extern "C" {
+
+int spgemm_batch_create_tuned(spgemm_batch_t *out, int64_t nprod, const spgemm_csr *A, const spgemm_csr *B,
+                              int dtype, unsigned flags, void *stream, const spgemm_tuning *tuning) {
+  NvtxRange nvtx("spgemm_batch_create");
+  if (!out) return SPGEMM_ERR_INVALID_ARGUMENT;
+  *out = nullptr;
+  set_last_error("");
+  spgemm_batch_s *b = nullptr;
+  int rc = batch_pack(&b, nprod, A, B, dtype, (cudaStream_t)stream);
+  if (rc != SPGEMM_OK) return rc;
+  spgemm_csr pa{b->m, b->bm, b->an, b->arp, b->aci, b->av};
+  spgemm_csr pb{b->bm, b->k, b->bn, b->brp, b->bci, b->bv};
+  rc = spgemm_plan_create_tuned(&b->plan, &pa, &pb, dtype, flags, stream, tuning);
   if (rc != SPGEMM_OK) {
-    cudaFreeAsync(b->ws, b->stream);
-    delete b;
+    b->plan = nullptr;
+    batch_free(b);
     return rc;
   }
   // a row of the packed C spans at most its own product's columns: the block
   // bins' sort window is sized from the widest product, not the packed k
-  int64_t widest = 0;
-  for (int64_t q = 0; q < nprod; ++q) widest = B[q].ncols > widest ? B[q].ncols : widest;
-  b->plan->span_cols = widest;
+  b->plan->span_cols = b->widest;
   b->state = 0;
   *out = b;
   return SPGEMM_OK;
@@ -317,7 +369,7 @@ int spgemm_batch_numeric(spgemm_batch_t b, const int32_t *c_row_ptr, int32_t *c_
   if (b->m > 0 && c_col_idx) {
     KernelScope ks(b->plan, "batch_unpack");
     k_batch_unpack<<<(unsigned)((b->m + 7) / 8), 256, 0, b->stream>>>(c_row_ptr, c_col_idx, b->m, b->d_row_off,
-                                                                      b->d_col_off, b->nprod);
+                                                                      b->d_col_off, b->nprod, nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
       set_last_error(std::string("batch unpack: ") + cudaGetErrorString(e));
@@ -331,10 +383,461 @@ int spgemm_batch_numeric(spgemm_batch_t b, const int32_t *c_row_ptr, int32_t *c_
 spgemm_plan_t spgemm_batch_plan(spgemm_batch_t b) { return b ? b->plan : nullptr; }
 
 int spgemm_batch_destroy(spgemm_batch_t b) {
-  if (!b) return SPGEMM_OK;
-  spgemm_plan_destroy(b->plan);
-  if (b->ws) cudaFreeAsync(b->ws, b->stream);
-  delete b;
+  batch_free(b);
+  return SPGEMM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batch graphs: every product of a batch in ONE CUDA graph launch.
+//
+// The products are split into waves (consecutive products whose C fits
+// int32 indexing and a stated pool).  Each wave keeps its packed operands, a
+// graph-mode plan (sized by a planning pass at creation: no host reads of
+// counts while it runs) and its pool for C.  The graph holds, for every
+// wave: the packing of its products, the flop pass, the symbolic bins, the
+// row_ptr scan, the numeric bins, the column unpacking and the copy of the
+// per-product entry counts and error words to pinned host memory.  A launch
+// is one cudaGraphLaunch on the caller's stream, with no host
+// synchronisation until the caller waits for it; it recomputes every
+// product from the current contents of the operands, so new values, or a
+// new structure that fits the planned capacities, give new products.
+
+namespace sg {
+
+// out[p] = entries of C before product p's first row (c_rp[row_off[p]]),
+// p = 0 .. nprod (so out[nprod] = nnz of the wave's C).
+__global__ void k_wave_prod_nnz(const int32_t *__restrict__ c_rp, const long long *__restrict__ row_off, int64_t nprod,
+                                const uint32_t *abort, long long *__restrict__ out) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p > nprod) return;
+  const bool stop = *(volatile const uint32_t *)abort & (kErrOverflow | kErrCapacity);
+  out[p] = stop ? 0 : c_rp[row_off[p]];
+}
+
+// Sum of v over the rows of each product (planning pass): block p, rows
+// row_off[p] .. row_off[p+1]-1.
+template <typename V>
+__global__ void __launch_bounds__(256)
+    k_prod_sum(const V *__restrict__ v, const long long *__restrict__ row_off, long long *__restrict__ out) {
+  __shared__ long long red[33];
+  const int64_t p = blockIdx.x;
+  long long s = 0;
+  for (int64_t r = row_off[p] + threadIdx.x; r < row_off[p + 1]; r += blockDim.x) s += v[r];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) out[p] = s;
+}
+
+}  // namespace sg
+
+struct GraphWave {
+  int64_t p0 = 0, p1 = 0;          // products p0 .. p1-1
+  spgemm_batch_s *b = nullptr;     // packed operands and offsets (its own plan freed)
+  spgemm_plan_s *plan = nullptr;   // graph-mode plan on the packed operands
+  void *cws = nullptr;             // C: row_ptr (m+1), col_idx and values (nnz_cap each)
+  int32_t *c_rp = nullptr, *c_ci = nullptr;
+  void *c_v = nullptr;
+  int64_t nnz_cap = 0;
+  long long *d_pnnz = nullptr;     // entries before each product (p1-p0+1)
+};
+
+struct spgemm_bgraph_s {
+  int64_t nprod = 0;
+  int dtype = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<GraphWave> waves;
+  std::vector<int64_t> wave_of;        // per product
+  cudaGraphExec_t exec = nullptr;
+  int64_t kernel_nodes = 0;
+  long long *h_pnnz = nullptr;         // pinned: per wave, p1-p0+1 counts (written by the graph)
+  uint32_t *h_err = nullptr;           // pinned: per wave, plan and packing error words
+  std::vector<int64_t> h_off;          // per wave, offset into h_pnnz
+  size_t bytes = 0;
+  bool launched = false;
+  cudaStream_t last_stream = nullptr;
+};
+
+namespace {
+
+using sg::GraphCaps;
+
+// Products [p0, p1) fit one packed batch (int32 indexing of its operands).
+bool packable(const spgemm_csr *A, const spgemm_csr *B, int64_t p0, int64_t p1) {
+  long long am = 0, an = 0, bm = 0, bn = 0, bk = 0, ch = 0;
+  for (int64_t p = p0; p < p1; ++p) {
+    am += A[p].nrows;
+    an += A[p].nnz;
+    bm += B[p].nrows;
+    bn += B[p].nnz;
+    bk += B[p].ncols;
+    ch += sg::pack_chunks(A[p], B[p]);
+  }
+  return am < INT32_MAX && an <= INT32_MAX && bm < INT32_MAX && bn <= INT32_MAX && bk <= INT32_MAX && ch <= INT32_MAX;
+}
+
+// What the planning pass learns about the products of one packed group.
+struct Planned {
+  std::vector<long long> flop, nnz;  // per product
+  int64_t max_flop = 0, max_bound = 0, max_nnz = 0;
+};
+
+// Planning pass of products [p0, p1): pack them, run the flop pass and the
+// symbolic phase once (host-driven, no bitmap rows so that the heavy rows
+// show their global-table sizes), and read per-product flop and nnz(C).
+int plan_group(const spgemm_csr *A, const spgemm_csr *B, int64_t p0, int64_t p1, int dtype, unsigned flags,
+               cudaStream_t st, const spgemm_tuning *tuning, Planned *out) {
+  spgemm_tuning t{};
+  if (tuning) t = *tuning;
+  t.bitmap_min_bound = -1;
+  t.long_row_min = -1;
+  t.max_nnz_c = 0;
+  spgemm_batch_s *b = nullptr;
+  const int64_t np = p1 - p0;
+  int rc = spgemm_batch_create_tuned(&b, np, A + p0, B + p0, dtype, flags & ~SPGEMM_TIMING, st, &t);
+  if (rc != SPGEMM_OK) return rc;
+  int32_t *rp = nullptr;
+  long long *sums = nullptr;
+  cudaError_t e = cudaMallocAsync((void **)&rp, (size_t)(b->m + 1) * 4, st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void **)&sums, (size_t)np * 2 * 8, st);
+  if (e != cudaSuccess) {
+    if (rp) cudaFreeAsync(rp, st);
+    sg::batch_free(b);
+    sg::set_last_error(std::string("batch graph planning: ") + cudaGetErrorString(e));
+    return SPGEMM_ERR_OUT_OF_MEMORY;
+  }
+  int64_t nnz = 0;
+  rc = spgemm_batch_symbolic(b, rp, &nnz, nullptr);
+  // a group whose C passes int32 indexing still has every row's count
+  if (rc == SPGEMM_ERR_INDEX_OVERFLOW) rc = SPGEMM_OK;
+  if (rc == SPGEMM_OK) {
+    spgemm_plan_s *p = b->plan;
+    sg::k_prod_sum<int32_t><<<(unsigned)np, 256, 0, st>>>(p->nnz_row, b->d_row_off, sums);
+    sg::k_prod_sum<int64_t><<<(unsigned)np, 256, 0, st>>>(p->flop, b->d_row_off, sums + np);
+    out->nnz.resize((size_t)np);
+    out->flop.resize((size_t)np);
+    e = cudaMemcpyAsync(out->nnz.data(), sums, (size_t)np * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out->flop.data(), sums + np, (size_t)np * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      sg::set_last_error(std::string("batch graph planning: ") + cudaGetErrorString(e));
+      rc = SPGEMM_ERR_DEVICE;
+    }
+    out->max_flop = p->max_flop;
+    out->max_bound = (int64_t)p->hc->max_bound_global;
+    out->max_nnz = (int64_t)p->hc->max_nnz_global;
+  }
+  cudaFreeAsync(sums, st);
+  cudaFreeAsync(rp, st);
+  sg::batch_free(b);
+  return rc;
+}
+
+void free_graph(spgemm_bgraph_s *g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  for (auto &w : g->waves) {
+    if (w.plan) sg::plan_free(w.plan);
+    if (w.cws) cudaFreeAsync(w.cws, g->stream);
+    if (w.d_pnnz) cudaFreeAsync(w.d_pnnz, g->stream);
+    sg::batch_free(w.b);
+  }
+  if (g->h_pnnz) cudaFreeHost(g->h_pnnz);
+  if (g->h_err) cudaFreeHost(g->h_err);
+  delete g;
+}
+
+}  // namespace
+
+namespace {
+
+// out[i] = in[i] - sub, i < n (one product's row pointers, rebased to 0).
+__global__ void k_rebase_rp(const int32_t *__restrict__ in, int64_t n, int32_t sub, int32_t *__restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = in[i] - sub;
+}
+
+// Captures every wave, in order, into one graph on a private stream (the
+// caller's stream may be a default stream, which cannot be captured), and
+// instantiates it.
+int bgraph_capture(spgemm_bgraph_s *g) {
+  cudaError_t e = cudaStreamSynchronize(g->stream);  // planning passes and allocations done
+  size_t tot = 0;
+  for (auto &w : g->waves) {
+    g->h_off.push_back((int64_t)tot);
+    tot += (size_t)(w.p1 - w.p0 + 1);
+  }
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&g->h_pnnz, tot * 8);
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&g->h_err, 2 * g->waves.size() * 4 + 4);
+  if (e != cudaSuccess) {
+    set_last_error(std::string("batch graph: ") + cudaGetErrorString(e));
+    return SPGEMM_ERR_OUT_OF_MEMORY;
+  }
+  std::memset(g->h_pnnz, 0, tot * 8);
+  std::memset(g->h_err, 0, 2 * g->waves.size() * 4 + 4);
+  cudaStream_t cap = nullptr;
+  e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    set_last_error(std::string("batch graph capture stream: ") + cudaGetErrorString(e));
+    return SPGEMM_ERR_DEVICE;
+  }
+  for (auto &w : g->waves) {
+    w.plan->stream = cap;
+    w.b->stream = cap;
+  }
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  cudaError_t el = cudaSuccess;
+  for (size_t i = 0; i < g->waves.size() && e == cudaSuccess && el == cudaSuccess; ++i) {
+    GraphWave &w = g->waves[i];
+    const int64_t np = w.p1 - w.p0, m = w.b->m;
+    const uint32_t *abort = &w.plan->dc->err;
+    el = sg::batch_repack(w.b, cap);
+    if (el == cudaSuccess) el = sg::plan_enqueue_graph(w.plan, w.c_rp, w.c_ci, w.c_v);
+    if (el == cudaSuccess && m > 0) {
+      sg::k_batch_unpack<<<(unsigned)((m + 7) / 8), 256, 0, cap>>>(w.c_rp, w.c_ci, m, w.b->d_row_off,
+                                                                   w.b->d_col_off, np, abort);
+      el = cudaGetLastError();
+    }
+    if (el == cudaSuccess) {
+      sg::k_wave_prod_nnz<<<(unsigned)((np + 256) / 256), 256, 0, cap>>>(w.c_rp, w.b->d_row_off, np, abort,
+                                                                          w.d_pnnz);
+      el = cudaGetLastError();
+    }
+    if (el == cudaSuccess)
+      el = cudaMemcpyAsync(g->h_pnnz + g->h_off[i], w.d_pnnz, (size_t)(np + 1) * 8, cudaMemcpyDeviceToHost, cap);
+    if (el == cudaSuccess) el = cudaMemcpyAsync(g->h_err + 2 * i, abort, 4, cudaMemcpyDeviceToHost, cap);
+    if (el == cudaSuccess) el = cudaMemcpyAsync(g->h_err + 2 * i + 1, w.b->d_err, 4, cudaMemcpyDeviceToHost, cap);
+  }
+  cudaGraph_t graph = nullptr;
+  if (e == cudaSuccess) e = cudaStreamEndCapture(cap, &graph);
+  for (auto &w : g->waves) {
+    w.plan->stream = g->stream;
+    w.b->stream = g->stream;
+  }
+  if (e == cudaSuccess && el == cudaSuccess) {
+    size_t n = 0;
+    e = cudaGraphGetNodes(graph, nullptr, &n);
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (e == cudaSuccess && n > 0) e = cudaGraphGetNodes(graph, nodes.data(), &n);
+    for (size_t i = 0; i < n && e == cudaSuccess; ++i) {
+      cudaGraphNodeType t;
+      if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++g->kernel_nodes;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, graph, 0);
+  }
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cap);
+  if (el != cudaSuccess || e != cudaSuccess) {
+    g->exec = nullptr;
+    set_last_error(std::string("batch graph capture: ") + cudaGetErrorString(el != cudaSuccess ? el : e));
+    return SPGEMM_ERR_DEVICE;
+  }
+  return SPGEMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int spgemm_bgraph_create(spgemm_bgraph_t *out, int64_t nprod, const spgemm_csr *A, const spgemm_csr *B, int dtype,
+                         unsigned flags, void *stream, const spgemm_tuning *tuning, int64_t wave_nnz,
+                         double pool_slack) {
+  NvtxRange nvtx("spgemm_bgraph_create");
+  if (!out) return SPGEMM_ERR_INVALID_ARGUMENT;
+  *out = nullptr;
+  set_last_error("");
+  if (nprod < 1 || !A || !B || wave_nnz < 0 || wave_nnz > INT32_MAX || !(pool_slack >= 0.0 && pool_slack <= 16.0))
+    return SPGEMM_ERR_INVALID_ARGUMENT;
+  if (flags & (SPGEMM_TIMING | SPGEMM_COUNT_PROBES)) {
+    set_last_error("a batch graph replays captured kernels: SPGEMM_TIMING and SPGEMM_COUNT_PROBES do not apply");
+    return SPGEMM_ERR_INVALID_ARGUMENT;
+  }
+  for (int64_t p = 0; p < nprod; ++p)
+    if (bad(A[p]) || bad(B[p]) || A[p].ncols != B[p].nrows) {
+      set_last_error("product " + std::to_string(p) + ": bad descriptor or inner dimensions differ");
+      return SPGEMM_ERR_INVALID_ARGUMENT;
+    }
+  const int64_t limit = wave_nnz > 0 ? wave_nnz : INT32_MAX;
+  cudaStream_t st = (cudaStream_t)stream;
+  spgemm_bgraph_s *g = new (std::nothrow) spgemm_bgraph_s();
+  if (!g) return SPGEMM_ERR_OUT_OF_MEMORY;
+  g->nprod = nprod;
+  g->dtype = dtype;
+  g->stream = st;
+  g->wave_of.assign((size_t)nprod, 0);
+  int rc = SPGEMM_OK;
+  // 1. groups that pack (int32 operands), planned one after another; waves:
+  //    consecutive products of a group whose nnz(C) stays within the limit
+  std::vector<std::pair<int64_t, int64_t>> waves;
+  std::vector<GraphCaps> caps;
+  for (int64_t g0 = 0; g0 < nprod && rc == SPGEMM_OK;) {
+    int64_t g1 = g0 + 1;
+    while (g1 < nprod && packable(A, B, g0, g1 + 1)) ++g1;
+    if (!packable(A, B, g0, g1)) {
+      set_last_error("product " + std::to_string(g0) + " alone exceeds int32 indexing");
+      rc = SPGEMM_ERR_INDEX_OVERFLOW;
+      break;
+    }
+    Planned pl;
+    rc = plan_group(A, B, g0, g1, dtype, flags, st, tuning, &pl);
+    for (int64_t p = g0; p < g1 && rc == SPGEMM_OK;) {
+      GraphCaps c{};
+      int64_t q = p, nnz = 0;
+      while (q < g1 && nnz + pl.nnz[(size_t)(q - g0)] <= limit) nnz += pl.nnz[(size_t)(q++ - g0)];
+      if (q == p) {
+        set_last_error("product " + std::to_string(p) + ": nnz(C) exceeds the wave limit");
+        rc = SPGEMM_ERR_INDEX_OVERFLOW;
+        break;
+      }
+      for (int64_t r = p; r < q; ++r) {
+        c.total_flop += pl.flop[(size_t)(r - g0)];
+        c.span_cols = std::max<int64_t>(c.span_cols, B[r].ncols);
+      }
+      c.max_flop = pl.max_flop;
+      c.max_bound = pl.max_bound;
+      c.max_nnz = pl.max_nnz;
+      c.nnz_cap = std::min<int64_t>(INT32_MAX, (int64_t)((double)nnz * (1.0 + pool_slack)) + 1);
+      waves.push_back({p, q});
+      caps.push_back(c);
+      p = q;
+    }
+    g0 = g1;
+  }
+  // 2. per wave: packed operands, graph-mode plan, pool for C
+  const size_t vs = dtype == SPGEMM_F32 ? 4 : 8;
+  for (size_t w = 0; w < waves.size() && rc == SPGEMM_OK; ++w) {
+    GraphWave gw;
+    gw.p0 = waves[w].first;
+    gw.p1 = waves[w].second;
+    const int64_t np = gw.p1 - gw.p0;
+    rc = sg::batch_pack(&gw.b, np, A + gw.p0, B + gw.p0, dtype, st);
+    if (rc != SPGEMM_OK) break;
+    spgemm_csr pa{gw.b->m, gw.b->bm, gw.b->an, gw.b->arp, gw.b->aci, gw.b->av};
+    spgemm_csr pb{gw.b->bm, gw.b->k, gw.b->bn, gw.b->brp, gw.b->bci, gw.b->bv};
+    rc = sg::plan_create_graph(&gw.plan, &pa, &pb, dtype, flags, st, tuning, caps[w]);
+    gw.nnz_cap = caps[w].nnz_cap;
+    const size_t o_ci = up256((size_t)(gw.b->m + 1) * 4);
+    const size_t o_v = o_ci + up256((size_t)gw.nnz_cap * 4);
+    const size_t bytes = o_v + up256((size_t)gw.nnz_cap * vs);
+    if (rc == SPGEMM_OK) {
+      cudaError_t e = cudaMallocAsync(&gw.cws, bytes, st);
+      if (e == cudaSuccess) e = cudaMallocAsync((void **)&gw.d_pnnz, (size_t)(np + 1) * 8, st);
+      if (e != cudaSuccess) {
+        set_last_error(std::string("batch graph pools: ") + cudaGetErrorString(e));
+        rc = SPGEMM_ERR_OUT_OF_MEMORY;
+      } else {
+        gw.c_rp = static_cast<int32_t *>(gw.cws);
+        gw.c_ci = reinterpret_cast<int32_t *>(static_cast<char *>(gw.cws) + o_ci);
+        gw.c_v = static_cast<char *>(gw.cws) + o_v;
+        g->bytes += bytes;
+      }
+    }
+    for (int64_t p = gw.p0; p < gw.p1; ++p) g->wave_of[(size_t)p] = (int64_t)g->waves.size();
+    g->waves.push_back(gw);
+  }
+  if (rc == SPGEMM_OK) rc = bgraph_capture(g);
+  if (rc != SPGEMM_OK) {
+    cudaStreamSynchronize(st);
+    free_graph(g);
+    return rc;
+  }
+  *out = g;
+  return SPGEMM_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+int spgemm_bgraph_launch(spgemm_bgraph_t g, void *stream) {
+  if (!g || !g->exec) return SPGEMM_ERR_INVALID_ARGUMENT;
+  const cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    set_last_error(std::string("batch graph launch: ") + cudaGetErrorString(e));
+    return SPGEMM_ERR_DEVICE;
+  }
+  g->launched = true;
+  g->last_stream = (cudaStream_t)stream;
+  return SPGEMM_OK;
+}
+
+int spgemm_bgraph_wait(spgemm_bgraph_t g) {
+  if (!g) return SPGEMM_ERR_INVALID_ARGUMENT;
+  if (!g->launched) return SPGEMM_ERR_BAD_STATE;
+  const cudaError_t e = cudaStreamSynchronize(g->last_stream);
+  if (e != cudaSuccess) {
+    set_last_error(std::string("batch graph: ") + cudaGetErrorString(e));
+    return SPGEMM_ERR_DEVICE;
+  }
+  for (size_t i = 0; i < g->waves.size(); ++i) {
+    const uint32_t pe = g->h_err[2 * i], be = g->h_err[2 * i + 1];
+    const std::string at = "batch graph wave " + std::to_string(i) + ": ";
+    if (be || (pe & kErrCsr)) {
+      set_last_error(at + "a product has an index out of range or a malformed row_ptr");
+      return SPGEMM_ERR_INVALID_CSR;
+    }
+    if (pe & (kErrOverflow | kErrCapacity)) {
+      set_last_error(at + "C or one of its rows exceeds the capacity the graph was planned with");
+      return SPGEMM_ERR_OUT_OF_MEMORY;
+    }
+    if (pe) {
+      set_last_error(at + "device-side check failed (hash probe or atomic retry bound)");
+      return SPGEMM_ERR_DEVICE;
+    }
+  }
+  return SPGEMM_OK;
+}
+
+int spgemm_bgraph_product_nnz(spgemm_bgraph_t g, int64_t p, int64_t *nnz) {
+  if (!g || !nnz || p < 0 || p >= g->nprod) return SPGEMM_ERR_INVALID_ARGUMENT;
+  if (!g->launched) return SPGEMM_ERR_BAD_STATE;
+  const size_t w = (size_t)g->wave_of[(size_t)p];
+  const int64_t i = p - g->waves[w].p0;
+  const long long *c = g->h_pnnz + g->h_off[w];
+  *nnz = c[i + 1] - c[i];
+  return SPGEMM_OK;
+}
+
+int spgemm_bgraph_product_copy(spgemm_bgraph_t g, int64_t p, int32_t *c_row_ptr, int32_t *c_col_idx, void *c_vals,
+                               void *stream) {
+  if (!g || !c_row_ptr || p < 0 || p >= g->nprod) return SPGEMM_ERR_INVALID_ARGUMENT;
+  if (!g->launched) return SPGEMM_ERR_BAD_STATE;
+  const size_t w = (size_t)g->wave_of[(size_t)p];
+  const GraphWave &gw = g->waves[w];
+  const int64_t i = p - gw.p0;
+  const long long first = g->h_pnnz[g->h_off[w] + i];
+  const long long nnz = g->h_pnnz[g->h_off[w] + i + 1] - first;
+  if (nnz > 0 && (!c_col_idx || !c_vals)) return SPGEMM_ERR_INVALID_ARGUMENT;
+  const int64_t row0 = gw.b->row_off[(size_t)i], rows = gw.b->row_off[(size_t)i + 1] - row0;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t vs = g->dtype == SPGEMM_F32 ? 4 : 8;
+  const int64_t nb = (rows + 1 + 255) / 256;
+  k_rebase_rp<<<(unsigned)(nb < 4096 ? nb : 4096), 256, 0, st>>>(gw.c_rp + row0, rows + 1, (int32_t)first, c_row_ptr);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && nnz > 0)
+    e = cudaMemcpyAsync(c_col_idx, gw.c_ci + first, (size_t)nnz * 4, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess && nnz > 0)
+    e = cudaMemcpyAsync(c_vals, static_cast<char *>(gw.c_v) + (size_t)first * vs, (size_t)nnz * vs,
+                        cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) {
+    set_last_error(std::string("batch graph product copy: ") + cudaGetErrorString(e));
+    return SPGEMM_ERR_DEVICE;
+  }
+  return SPGEMM_OK;
+}
+
+int spgemm_bgraph_info(spgemm_bgraph_t g, int64_t *waves, int64_t *kernel_nodes, int64_t *bytes) {
+  if (!g) return SPGEMM_ERR_INVALID_ARGUMENT;
+  if (waves) *waves = (int64_t)g->waves.size();
+  if (kernel_nodes) *kernel_nodes = g->kernel_nodes;
+  if (bytes) *bytes = (int64_t)g->bytes;
+  return SPGEMM_OK;
+}
+
+int spgemm_bgraph_destroy(spgemm_bgraph_t g) {
+  if (!g) return SPGEMM_OK;
+  if (g->launched) cudaStreamSynchronize(g->last_stream);
+  free_graph(g);
   return SPGEMM_OK;
 }
 

@@ -31,6 +31,7 @@ enum : uint32_t {
   kErrProbe = 2u,     // a probe sequence visited the whole table without a slot
   kErrOverflow = 4u,  // nnz(C) does not fit int32 indexing
   kErrRetry = 8u,     // an atomic update retried past its bound
+  kErrCapacity = 16u, // graph mode: C or a heavy row exceeds what was planned
 };
 
 __device__ __forceinline__ void raise_err(uint32_t *err, uint32_t bit) { atomicOr(err, bit); }
@@ -131,6 +132,41 @@ template <> struct Val<double> {
   }
   static __device__ __forceinline__ void acc_global(double *p, double a, double b) { atomicAdd(p, a * b); }
   static __device__ __forceinline__ void add_global(double *p, double v) { atomicAdd(p, v); }
+  // U accumulations vals[r[u]] += a[u]*b[u] (where act[u]) at once: every
+  // slot is read, every FMA done and every compare-and-swap issued before
+  // any result is checked, so the U dependent chains (load, FMA, CAS)
+  // overlap instead of running one after another; a failed swap (another
+  // thread, or an earlier u of this lane, changed the slot) retries with the
+  // value it found.
+  template <int U>
+  static __device__ __forceinline__ void acc_shared_batch(double *vals, const int (&r)[U], const double (&a)[U],
+                                                          const double (&b)[U], const bool (&act)[U], uint32_t *err) {
+    unsigned long long old[U];
+    bool pend[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      pend[u] = act[u];
+      old[u] = pend[u] ? *reinterpret_cast<volatile unsigned long long *>(vals + r[u]) : 0ull;
+    }
+    for (int it = 0; it < kMaxCasRetries; ++it) {
+      bool any = false;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (pend[u]) {
+          const double nv = fma(a[u], b[u], __longlong_as_double((long long)old[u]));
+          const unsigned long long got = atomicCAS(reinterpret_cast<unsigned long long *>(vals + r[u]), old[u],
+                                                   (unsigned long long)__double_as_longlong(nv));
+          pend[u] = got != old[u];
+          old[u] = got;
+          any |= pend[u];
+        }
+      }
+      if (!any) return;
+    }
+    raise_err(err, kErrRetry);
+  }
+  // owner-only update (no other thread touches the slot): c + a*b
+  static __device__ __forceinline__ double mad(double c, double a, double b) { return fma(a, b, c); }
 };
 
 template <> struct Val<float> {
@@ -140,6 +176,14 @@ template <> struct Val<float> {
   }
   static __device__ __forceinline__ void acc_global(float *p, float a, float b) { atomicAdd(p, a * b); }
   static __device__ __forceinline__ void add_global(float *p, float v) { atomicAdd(p, v); }
+  template <int U>
+  static __device__ __forceinline__ void acc_shared_batch(float *vals, const int (&r)[U], const float (&a)[U],
+                                                          const float (&b)[U], const bool (&act)[U], uint32_t *) {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (act[u]) atomicAdd(vals + r[u], a[u] * b[u]);
+  }
+  static __device__ __forceinline__ float mad(float c, float a, float b) { return fmaf(a, b, c); }
 };
 
 template <> struct Val<int64_t> {
@@ -153,7 +197,49 @@ template <> struct Val<int64_t> {
   static __device__ __forceinline__ void add_global(int64_t *p, int64_t v) {
     atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
   }
+  template <int U>
+  static __device__ __forceinline__ void acc_shared_batch(int64_t *vals, const int (&r)[U], const int64_t (&a)[U],
+                                                          const int64_t (&b)[U], const bool (&act)[U], uint32_t *) {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (act[u])
+        atomicAdd(reinterpret_cast<unsigned long long *>(vals + r[u]),
+                  (unsigned long long)a[u] * (unsigned long long)b[u]);
+  }
+  static __device__ __forceinline__ int64_t mad(int64_t c, int64_t a, int64_t b) {
+    return (int64_t)((unsigned long long)c + (unsigned long long)a * (unsigned long long)b);
+  }
 };
+
+// ---------------------------------------------------------------------------
+// Entries of the grouped copies of long rows of B: column and value, read
+// with one 16-byte (8-byte for f32) load.
+template <typename T> struct alignas(16) LEnt {
+  int32_t col;
+  int32_t pad;
+  T v;
+};
+template <> struct alignas(8) LEnt<float> {
+  int32_t col;
+  float v;
+};
+
+__device__ __forceinline__ void load_lent(const LEnt<double> *p, int32_t *col, double *v) {
+  const int4 raw = __ldg(reinterpret_cast<const int4 *>(p));
+  *col = raw.x;
+  *v = __hiloint2double(raw.w, raw.z);
+}
+__device__ __forceinline__ void load_lent(const LEnt<int64_t> *p, int32_t *col, int64_t *v) {
+  const int4 raw = __ldg(reinterpret_cast<const int4 *>(p));
+  *col = raw.x;
+  *v = (int64_t)(((unsigned long long)(unsigned)raw.w << 32) | (unsigned)raw.z);
+}
+__device__ __forceinline__ void load_lent(const LEnt<float> *p, int32_t *col, float *v) {
+  const int2 raw = __ldg(reinterpret_cast<const int2 *>(p));
+  *col = raw.x;
+  *v = __int_as_float(raw.y);
+}
+
 
 // ---------------------------------------------------------------------------
 // Reductions and scans.
@@ -307,6 +393,8 @@ template <typename T> struct Stage {
   Entry<T> *ent;    // kStageN entries
   int *next;        // next unclaimed chunk
   long long *wsum;  // scratch for the scan (8 warp totals)
+  int *lidx = nullptr;  // long-row loop: staged entries of long rows (kStageN)
+  int *lcnt = nullptr;  // long-row loop: long entries per staging warp (8)
 };
 
 // Processes flat products [p0, p1) of a staged round of n entries, lane l
@@ -413,6 +501,175 @@ __device__ __forceinline__ void block_row_products(int64_t a0, int64_t a1, int G
       process_flat<U, NEED_VAL>(st.ent, n, (int)p0, (int)p1, G, lig, bci, bv, ncols, err, f);
     }
     __syncthreads();
+    j0 += n;
+  }
+}
+
+// Processes flat products [p0, p1) like process_flat, but hands each lane's
+// U gathered products to fb(c, a, b, ok) at once (ok[u]: product u exists
+// and its column is inside B).  Software-pipelined: the loads of the next U
+// products are issued before fb works on the current ones, so their L2
+// latency overlaps fb's shared-memory updates.
+template <int U, bool NEED_VAL, bool PIPE, typename T, typename FB>
+__device__ __forceinline__ void process_flat_batch(const Entry<T> *ent, int n, int p0, int p1, int G, int lig,
+                                                   const int32_t *__restrict__ bci, const T *__restrict__ bv,
+                                                   int32_t ncols, uint32_t *err, FB &&fb) {
+  if constexpr (!PIPE) {
+    // the same without the second set of registers (kernels at 32-40
+    // registers a thread would spill it)
+    process_flat<U, NEED_VAL>(ent, n, p0, p1, G, lig, bci, bv, ncols, err, [&](int32_t c, T a, T b) {
+      int32_t cc[U];
+      T aa[U], bb[U];
+      bool ok[U];
+      cc[0] = c;
+      aa[0] = a;
+      bb[0] = b;
+      ok[0] = true;
+#pragma unroll
+      for (int u = 1; u < U; ++u) ok[u] = false, cc[u] = -1, aa[u] = bb[u] = T(0);
+      fb(cc, aa, bb, ok);
+    });
+    return;
+  }
+  int p = p0 + lig;
+  if (p >= p1) return;
+  int lo = 0, hi = n - 1;  // first entry e with end[e] > p
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (ent[mid].end > p) hi = mid;
+    else lo = mid + 1;
+  }
+  int e = lo;
+  Entry<T> cur = ent[e];
+  // the next U products of this lane: columns, values, a_ik, presence
+  auto gather = [&](int32_t(&c)[U], T(&v)[U], T(&au)[U], bool(&ok)[U]) {
+    int32_t q[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      ok[u] = p < p1;
+      q[u] = 0;
+      au[u] = T(0);
+      if (ok[u]) {
+        while (p >= cur.end) cur = ent[++e];
+        q[u] = cur.off + p;
+        au[u] = cur.a;
+      }
+      p += G;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      c[u] = ok[u] ? __ldg(bci + q[u]) : -1;
+      v[u] = (NEED_VAL && ok[u]) ? __ldg(bv + q[u]) : T(0);
+    }
+  };
+  int32_t c0[U], c1[U];
+  T v0[U], v1[U], a0[U], a1[U];
+  bool k0[U], k1[U];
+  gather(c0, v0, a0, k0);
+  while (k0[0]) {
+    gather(c1, v1, a1, k1);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (k0[u] && !((uint32_t)c0[u] < (uint32_t)ncols)) {
+        raise_err(err, kErrCsr);
+        k0[u] = false;
+      }
+    }
+    fb(c0, a0, v0, k0);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      c0[u] = c1[u];
+      v0[u] = v1[u];
+      a0[u] = a1[u];
+      k0[u] = k1[u];
+    }
+  }
+}
+
+// Block-wide row loop of the bitmap rows, with long rows of B (lmap[k] >= 0,
+// lmap null: none).  Like block_row_products, except that a staged entry
+// whose row of B is long adds no flat products: its staged record keeps the
+// long-row index in `off` (and a_ik), and after the round's flat products
+// and a barrier every thread calls flong(nlong, lidx), lidx[0..nlong) being
+// the round's long entries in stored order; a barrier follows.  Flat
+// products go to fb (process_flat_batch).  Every thread of the block calls
+// it (blockDim.x >= kStageN).
+template <int U, bool NEED_VAL, bool PIPE, typename T, typename FB, typename FL>
+__device__ __forceinline__ void block_row_products_long(int64_t a0, int64_t a1, int G,
+                                                        const int32_t *__restrict__ aci, const T *__restrict__ av,
+                                                        const int32_t *__restrict__ brp,
+                                                        const int32_t *__restrict__ bci, const T *__restrict__ bv,
+                                                        int32_t ncols, uint32_t *err, const int32_t *__restrict__ lmap,
+                                                        Stage<T> st, FB &&fb, FL &&flong) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, lig = tid & (G - 1);
+  const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+  const int leader = lane & ~(G - 1);
+  const int ngroups = blockDim.x / G;
+  int64_t j0 = a0;
+  while (j0 < a1) {
+    const int n0 = (int)((a1 - j0) < kStageN ? (a1 - j0) : kStageN);
+    long long len = 0;
+    int32_t bs = 0, d = -1;
+    T av_t = T(0);
+    if (tid < n0) {
+      const int32_t kk = __ldg(aci + j0 + tid);
+      if (lmap) d = __ldg(lmap + kk);
+      if (d < 0) {
+        bs = __ldg(brp + kk);
+        len = __ldg(brp + kk + 1) - bs;
+      }
+      if (NEED_VAL) av_t = __ldg(av + j0 + tid);
+    }
+    long long inc = len;
+    if (wid < kStageN / 32) {
+      inc = warp_incl_scan(len);
+      if (lane == 31) st.wsum[wid] = inc;
+    }
+    if (tid == 0) *st.next = 0;
+    __syncthreads();
+    if (wid < kStageN / 32) {
+      long long base = 0;
+      for (int w = 0; w < wid; ++w) base += st.wsum[w];
+      inc += base;
+    }
+    const bool keep = tid < n0 && (tid == 0 || inc <= 2147483647LL);
+    const int n = __syncthreads_count(keep);
+    unsigned lm = 0;
+    if (keep) st.ent[tid] = Entry<T>{(int)inc, d < 0 ? (int)(bs - (inc - len)) : d, av_t};
+    if (wid < kStageN / 32) {
+      lm = __ballot_sync(0xffffffffu, keep && d >= 0);
+      if (lane == 0) st.lcnt[wid] = __popc(lm);
+    }
+    __syncthreads();
+    int nlong = 0;
+    if (lmap) {
+#pragma unroll
+      for (int w = 0; w < kStageN / 32; ++w) {
+        if (w == wid && keep && d >= 0) st.lidx[nlong + __popc(lm & ((1u << lane) - 1u))] = tid;
+        nlong += st.lcnt[w];
+      }
+    }
+    const int total = st.ent[n - 1].end;
+    if (total > 0) {
+      long long chunk = ((long long)total + 4LL * ngroups - 1) / (4LL * ngroups);
+      chunk = chunk < 4LL * G ? 4LL * G : chunk > 32LL * G ? 32LL * G : chunk;
+      chunk = (chunk + G - 1) / G * G;
+      const int nchunks = (int)(((long long)total + chunk - 1) / chunk);
+      for (;;) {
+        int cidx = 0;
+        if (lig == 0) cidx = atomicAdd(st.next, 1);
+        cidx = __shfl_sync(gmask, cidx, leader);
+        if (cidx >= nchunks) break;
+        const long long p0 = (long long)cidx * chunk;
+        const long long p1 = p0 + chunk < total ? p0 + chunk : total;
+        process_flat_batch<U, NEED_VAL, PIPE>(st.ent, n, (int)p0, (int)p1, G, lig, bci, bv, ncols, err, fb);
+      }
+    }
+    __syncthreads();
+    if (nlong > 0) {
+      flong(nlong, (const int *)st.lidx);
+      __syncthreads();
+    }
     j0 += n;
   }
 }

@@ -10,6 +10,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "../../include/spgemm.h"
+#include "common.cuh"
 
 namespace sg {
 
@@ -49,8 +50,9 @@ constexpr int kNumBitmapMBin = 12;   // medium class
 constexpr int kNumNumBins = 13;
 constexpr int kWarpsPerBlock = 4;  // warp bins: rows per block
 // shared memory kept free beside a bitmap kernel's dynamic allocation for
-// its static arrays (staging of 256 entries, reductions)
-constexpr int kStaticSmemReserve = 256 * 20 + 2048;
+// its static arrays (staging of 256 entries and their long-row list,
+// reductions)
+constexpr int kStaticSmemReserve = 256 * 24 + 2048;
 
 // Symbolic bins 0..9: tables 64 .. 32768 slots, load factor 1/2 for warp
 // tables and 3/4 for block tables (the bound overestimates the key count
@@ -109,6 +111,51 @@ __host__ __device__ inline int bm_split_parts(long long flop, long long nnz) {
   if (parts > kSplitMaxParts) parts = kSplitMaxParts;
   return (int)parts;
 }
+// Long rows of B.  Inside bitmap rows of A, the products of a row k of B
+// with at least long_row_min entries are not taken one by one: the symbolic
+// phase ORs k's saved column bitmap into the row's bitmap, and the numeric
+// phase reads a copy of row k sorted by column, split into kLongRanges
+// column ranges of equal mass over all long rows; warp w of a block of NW
+// warps owns ranges [w*kLongRanges/NW, (w+1)*kLongRanges/NW) of every long
+// row, and so every column in them, and adds into their sums with plain
+// loads and stores.  The rule below is the default threshold
+// (spgemm_tuning).
+constexpr int kLongRanges = 32;
+// Measured on R-MAT A*A, scale 16 (k = 2^16): thresholds 256, 512 and 1024
+// gave 4.26, 4.23 and 4.25 ms per product; 64 and 128 were 10-30% slower.
+inline int64_t long_row_min_default(int64_t k) {
+  const int64_t q = k / 128;
+  return q > 512 ? q : 512;
+}
+
+// Device view of a plan's long rows (map == nullptr: none).
+struct LongRows {
+  const int32_t *map;    // per row of B: its long-row index d, or -1
+  const uint32_t *bits;  // column bitmap of long row d: bits[d * words + w]
+  const int32_t *off;    // off[d * (kLongRanges + 1) + r]: first entry of range r (absolute index)
+  const void *ent;       // entries {column, value}, each long row sorted by column (LEnt<T>)
+};
+
+// Rows of one bin: perm[off[bin]] .. perm[off[bin + 1] - 1].  The offsets
+// live in device memory, written by a kernel from the bin counts, so that
+// the bin kernels also find their rows when the host has not read the
+// counts (a captured CUDA graph of whole products); the kernels walk their
+// rows grid-stride, with exact grids when the host knows the counts and
+// persistent grids otherwise.
+struct BinRows {
+  const int32_t *perm;
+  const long long *off;
+  int bin;
+};
+
+// Largest key bound of each hash bin (warp tables 64..1024 slots, block
+// tables 2048..16384): a row goes to the first bin whose cap holds its
+// bound.  Default loads: 1/2 of a warp table, 3/4 of a block table.
+struct HashCaps {
+  long long cap[9];
+};
+HashCaps hash_caps(int warp_load_pct, int block_load_pct);
+
 // block-bin sort: a row whose columns span at most 4096 words (131072
 // columns) is ranked through a bitmap of its window; measured on R-MAT
 // scale 17 A*A (2^17 columns), 4096 words ran sorted output 17% faster than
@@ -133,6 +180,10 @@ struct DevCounters {
   unsigned long long bm_flop[3];        // flop of the rows of each class
   unsigned long long sym_split_extra;   // heavy symbolic bitmap rows: parts beyond one per row
   unsigned long long sym_item_cursor;
+  unsigned long long n_long;            // long rows of B, and their entries
+  unsigned long long long_tot;
+  unsigned long long nnz_a_used;        // stored a_ik whose row of B is not empty
+  unsigned long long scan_total;        // total of the compacted A's row scan
   // SPGEMM_COUNT_PROBES: rows 0/1 symbolic probes/inserts, 2/3 numeric,
   // each spread over kProbeSlots counters to limit atomic contention
   unsigned long long probe_stats[4][kProbeSlots];
@@ -157,7 +208,16 @@ struct Args {
   int probe = 0;  // hash tables: kProbeChunk (SPGEMM_PROBE_CHUNK4) | kProbeHashHi (unless SPGEMM_HASH_LOW_BITS)
   // SPGEMM_COUNT_PROBES: this phase's probe counters (inserts at +kProbeSlots), else null
   unsigned long long *probe_ctr = nullptr;
+  // graph mode: the plan's error word; a numeric kernel returns at once when
+  // it holds kErrOverflow or kErrCapacity (C would not fit its buffers)
+  const uint32_t *abort = nullptr;
 };
+
+// A numeric kernel of a graph-mode plan skips its work when the symbolic
+// phase found that C does not fit the planned buffers.
+__device__ __forceinline__ bool aborted(const Args &a) {
+  return a.abort && (*(volatile const uint32_t *)a.abort & (kErrOverflow | kErrCapacity));
+}
 
 }  // namespace sg
 
@@ -186,6 +246,31 @@ struct spgemm_plan_s {
   int64_t tune_bm_min;   // spgemm_tuning::bitmap_min_bound (0: default rule, -1: no bitmaps)
   int64_t max_nnz_c;     // largest nnz(C) accepted (spgemm_tuning::max_nnz_c, default 2^31-1)
   int64_t span_cols;     // bound on the column span of any row of C: k, or a batch's widest product
+  sg::HashCaps caps;     // hash-bin key caps (spgemm_tuning load factors)
+  // long rows of B (spgemm_tuning::long_row_min; long_min 0: none)
+  int64_t long_min;
+  int64_t long_cap;      // room in lrow/lbase: nnz(B) / long_min + 1
+  int64_t n_long, long_tot;
+  int32_t *lmap;         // per row of B (fixed workspace)
+  int32_t *lrow, *lbase; // per long row: row of B, first entry (fixed workspace)
+  void *long_ws;         // bitmaps, group offsets, entries, entry sources
+  size_t long_ws_bytes;
+  uint32_t *lbits;
+  int32_t *loff;
+  void *lent;
+  int32_t *lsrc;
+  bool long_ready;       // built: the plan has bitmap rows and long rows
+  // compacted A (entries selecting a non-empty row of B), walked by the
+  // phases instead of A when it holds fewer than half of A's entries
+  long long *eflop;      // flop pass: per stored a_ik the length of its row of B, then their
+                         // exclusive prefix (nnz(A) + 1 entries, fixed workspace)
+  long long *epart;      // scan partials of eflop (fixed workspace)
+  int64_t nnz_a_used;
+  bool a_compact;
+  void *acmp_ws;
+  size_t acmp_bytes;
+  int32_t *karp, *kaci, *asrc;
+  void *kav;
   // spgemm_numeric_graph: the captured numeric launches and the output buffers baked into them
   cudaGraphExec_t graph_exec;
   const void *graph_rp, *graph_ci, *graph_cv;
@@ -202,6 +287,14 @@ struct spgemm_plan_s {
   int32_t *nnz_row;
   uint8_t *rbin2;  // numeric bin of each row
   int32_t *perm2;  // rows grouped by numeric bin
+  long long *d_sym_off, *d_num_off;  // device bin offsets (16 each), as sym_off / num_off
+  // graph mode (batched products replayed as one CUDA graph): no host read
+  // of counts; bins are launched with persistent grids over device ranges,
+  // and the workspace is sized from capacities instead of counts
+  bool ddrive;
+  // graph mode: the largest symbolic bound and row nnz the global tables
+  // were planned for (-1: not graph mode, no check)
+  int64_t gcap_bound = -1, gcap_nnz = -1;
   uint32_t *bitmaps;  // one bitmap per row of the symbolic bitmap bin
   size_t bitmaps_bytes;
   int4 *bm_items;     // numeric bitmap work items (bitmap index, window, part, parts)
@@ -275,6 +368,56 @@ inline bool use_side_streams(const spgemm_plan_s *p) {
 }
 cudaStream_t bin_stream(spgemm_plan_s *p, int i);
 cudaError_t join(spgemm_plan_s *p);
+
+// Long rows: marks the long rows of B (before the flop pass's counters are
+// read), then builds their bitmaps and owner groups (when bitmap rows
+// exist), and refreshes the grouped copies' values before a numeric phase.
+cudaError_t long_rows_mark(spgemm_plan_s *p);
+cudaError_t long_rows_build(spgemm_plan_s *p);
+cudaError_t long_rows_values(spgemm_plan_s *p);
+inline LongRows long_rows(const spgemm_plan_s *p) {
+  if (!p->long_ready) return LongRows{nullptr, nullptr, nullptr, nullptr};
+  return LongRows{p->lmap, p->lbits, p->loff, p->lent};
+}
+size_t long_entry_bytes(int dtype);
+// Compacted A: keep flags of the entries (from the flop pass's prefix),
+// then, from their exclusive scan pos, the copy's row pointers, columns and
+// sources; its values before every numeric phase.
+cudaError_t compact_a_keep(spgemm_plan_s *p, int32_t *pos);
+cudaError_t compact_a_gather(spgemm_plan_s *p, const int32_t *pos);
+cudaError_t compact_a_values(spgemm_plan_s *p);
+// Arguments of the phase kernels: the compacted A when the plan has one.
+inline Args phase_args(const spgemm_plan_s *p, uint32_t *err, int probe, unsigned long long *ctr) {
+  const bool c = p->a_compact;
+  return Args{p->m, p->n, p->k, c ? p->karp : p->arp, c ? p->kaci : p->aci, p->brp, p->bci,
+              c ? (const void *)p->kav : p->av, p->bv, p->G, err, probe, ctr};
+}
+
+// Blocks of a bin launch: `exact` (one per row or per 4 rows) when the host
+// knows the bin's count; in graph mode at most the blocks that stay
+// resident on the GPU at once (the kernels walk their rows grid-stride).
+int64_t launch_blocks(const spgemm_plan_s *p, const void *kernel, int threads, size_t smem, int64_t exact);
+// Graph mode: an upper bound on the rows of bin b (0: the bin never runs).
+int64_t ddrive_bin_rows(const spgemm_plan_s *p, int b, bool symbolic);
+
+// Graph mode (batched products replayed as one CUDA graph): what a plan is
+// sized for, taken from a planning pass.  A replay whose product exceeds it
+// reports SPGEMM_ERR_OUT_OF_MEMORY and writes nothing out of bounds.
+struct GraphCaps {
+  int64_t total_flop;  // sets the lanes per stored a_ik and the side streams
+  int64_t max_flop;
+  int64_t max_bound;   // largest symbolic bound of a row (global tables above 3/4 of 32768)
+  int64_t max_nnz;     // largest nnz of a row (global tables above the largest shared table)
+  int64_t nnz_cap;     // room for nnz(C)
+  int64_t span_cols;   // bound on the column span of a row of C
+};
+int plan_create_graph(spgemm_plan_s **out, const spgemm_csr *A, const spgemm_csr *B, int dtype, unsigned flags,
+                      cudaStream_t stream, const spgemm_tuning *tuning, const GraphCaps &caps);
+// Enqueues the whole product (flop pass, symbolic phase, row_ptr scan,
+// numeric phase) on the plan's stream without any host synchronisation.
+cudaError_t plan_enqueue_graph(spgemm_plan_s *p, int32_t *c_rp, int32_t *c_ci, void *c_v);
+// Frees a plan (the public spgemm_plan_destroy).
+void plan_free(spgemm_plan_s *p);
 
 // Launchers (return a cudaError_t from the launch).
 cudaError_t launch_symbolic(spgemm_plan_s *p);

@@ -270,27 +270,20 @@ __device__ __forceinline__ bool bucket_sort_store(int32_t *keys, T *vals, int cn
   return true;
 }
 
+// One row of a warp bin: accumulate into the warp's table, then store the
+// row (sorted when requested).
 template <typename T, int S>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 8)
-    k_num_warp(Args a, const int32_t *__restrict__ rows, int64_t nrows, const int32_t *__restrict__ c_rp,
-               int32_t *__restrict__ c_ci, T *__restrict__ c_v, int sorted) {
-  extern __shared__ __align__(16) unsigned char sm_num_warp[];
-  __shared__ Entry<T> s_ent[kWarpsPerBlock][32];
-  __shared__ int s_next[kWarpsPerBlock];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
-  if (w >= nrows) return;
-  int32_t *keys = reinterpret_cast<int32_t *>(sm_num_warp) + warp * S;
-  T *vals = reinterpret_cast<T *>(sm_num_warp + (size_t)kWarpsPerBlock * S * sizeof(int32_t)) + warp * S;
+__device__ __forceinline__ void num_warp_row(const Args &a, int32_t i, int32_t *keys, T *vals, Entry<T> *ent,
+                                             int *next, const int32_t *__restrict__ c_rp, int32_t *__restrict__ c_ci,
+                                             T *__restrict__ c_v, int sorted, int lane) {
   for (int s = lane; s < S; s += 32) {
     keys[s] = kEmpty;
     vals[s] = T(0);
   }
   __syncwarp();
-  const int32_t i = rows[w];
   const int G = a.G;
   warp_row_products<kUN, true, T>(a.arp[i], a.arp[i + 1], G, a.aci, (const T *)a.av, a.brp, a.bci, (const T *)a.bv,
-                                  (int32_t)a.k, a.err, Stage<T>{s_ent[warp], &s_next[warp], nullptr},
+                                  (int32_t)a.k, a.err, Stage<T>{ent, next, nullptr},
                                  [&](int32_t c, T av, T bv) { insert_acc<T, false>(keys, vals, S - 1, c, av, bv, a.err, a.probe, a.probe_ctr); });
   __syncwarp();
   const int32_t rp = c_rp[i];
@@ -317,7 +310,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 8)
     }
     const int cnt = min(base, nnz);
     if (cnt <= 32) warp_sort_store<T, 1>(keys, vals, cnt, lane, c_ci + rp, c_v + rp);
-    else if (bucket_sort_store<T, S>(keys, vals, cnt, lane, c_ci + rp, c_v + rp)) {
+    else if (cnt <= S / 2 && bucket_sort_store<T, S>(keys, vals, cnt, lane, c_ci + rp, c_v + rp)) {
     } else if (cnt <= 64) warp_sort_store<T, 2>(keys, vals, cnt, lane, c_ci + rp, c_v + rp);
     else if (cnt <= 128) warp_sort_store<T, 4>(keys, vals, cnt, lane, c_ci + rp, c_v + rp);
     else if (cnt <= 256) warp_sort_store<T, 8>(keys, vals, cnt, lane, c_ci + rp, c_v + rp);
@@ -352,6 +345,25 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 8)
   }
 }
 
+template <typename T, int S>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 8)
+    k_num_warp(Args a, BinRows br, const int32_t *__restrict__ c_rp, int32_t *__restrict__ c_ci,
+               T *__restrict__ c_v, int sorted) {
+  extern __shared__ __align__(16) unsigned char sm_num_warp[];
+  __shared__ Entry<T> s_ent[kWarpsPerBlock][32];
+  __shared__ int s_next[kWarpsPerBlock];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (aborted(a)) return;
+  const long long o0 = br.off[br.bin], nrows = br.off[br.bin + 1] - o0;
+  int32_t *keys = reinterpret_cast<int32_t *>(sm_num_warp) + warp * S;
+  T *vals = reinterpret_cast<T *>(sm_num_warp + (size_t)kWarpsPerBlock * S * sizeof(int32_t)) + warp * S;
+  // one warp per row (no block barrier below)
+  for (int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + warp; w < nrows; w += (int64_t)gridDim.x * kWarpsPerBlock) {
+    num_warp_row<T, S>(a, br.perm[o0 + w], keys, vals, s_ent[warp], &s_next[warp], c_rp, c_ci, c_v, sorted, lane);
+    __syncwarp();
+  }
+}
+
 // sort_mode: 0 unsorted, 1 bitonic sort of the table, 2 rank by column
 // bitmap (needs 2 * words * 4 bytes more shared memory).
 // Threads of the block bins (as kNumBins) and the blocks per SM their shared
@@ -360,10 +372,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 8)
 template <int S> constexpr int num_block_threads() { return S <= 2048 ? 256 : S <= 4096 ? 512 : 1024; }
 template <int S> constexpr int num_block_min_blocks() { return S <= 2048 ? 5 : S <= 4096 ? 3 : 1; }
 
+// One row of a block bin (whole block).
 template <typename T, int S>
-__global__ void __launch_bounds__(num_block_threads<S>(), num_block_min_blocks<S>())
-    k_num_block(Args a, const int32_t *__restrict__ rows, const int32_t *__restrict__ c_rp,
-                int32_t *__restrict__ c_ci, T *__restrict__ c_v, int sort_mode, int words) {
+__device__ __forceinline__ void num_block_row(const Args &a, int32_t i, const int32_t *__restrict__ c_rp,
+                                              int32_t *__restrict__ c_ci, T *__restrict__ c_v, int sort_mode,
+                                              int words) {
   extern __shared__ __align__(16) unsigned char sm_num_block[];
   __shared__ int red[33];
   __shared__ Entry<T> s_ent[kStageN];
@@ -378,7 +391,6 @@ __global__ void __launch_bounds__(num_block_threads<S>(), num_block_min_blocks<S
   }
   if (threadIdx.x == 0) cursor = 0;
   __syncthreads();
-  const int32_t i = rows[blockIdx.x];
   const int G = a.G;
   block_row_products<kUN, true, T>(a.arp[i], a.arp[i + 1], G, a.aci, (const T *)a.av, a.brp, a.bci,
                                    (const T *)a.bv, (int32_t)a.k, a.err, Stage<T>{s_ent, &s_next, s_wsum},
@@ -471,6 +483,18 @@ __global__ void __launch_bounds__(num_block_threads<S>(), num_block_min_blocks<S
   }
 }
 
+template <typename T, int S>
+__global__ void __launch_bounds__(num_block_threads<S>(), num_block_min_blocks<S>())
+    k_num_block(Args a, BinRows br, const int32_t *__restrict__ c_rp, int32_t *__restrict__ c_ci,
+                T *__restrict__ c_v, int sort_mode, int words) {
+  if (aborted(a)) return;
+  const long long o0 = br.off[br.bin], nrows = br.off[br.bin + 1] - o0;
+  for (int64_t b = blockIdx.x; b < nrows; b += gridDim.x) {  // one block per row
+    num_block_row<T, S>(a, br.perm[o0 + b], c_rp, c_ci, c_v, sort_mode, words);
+    __syncthreads();  // the shared table is cleared for the next row
+  }
+}
+
 // Values of the split bitmap rows start at zero: their parts add into them.
 // One warp per bitmap row.
 template <typename T>
@@ -500,17 +524,25 @@ constexpr long long kAggregateMinRatio = 32;
 // row's stored a_ik.  A row in one part stores its values; a split row's
 // parts add theirs into C (zeroed by k_bm_zero_split) and part 0 stores
 // the columns.
+// Products of long rows of B (lr.map) are taken from their column-sorted
+// copies: warp w owns its share of the column ranges of every long row,
+// hence the output ranks of those columns, and adds into them with plain
+// shared-memory loads and stores; the other products go through
+// compare-and-swap accumulation (f64) or atomic adds.
 template <typename T, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
     k_num_bitmap(Args a, const int32_t *__restrict__ bm_rows, const int4 *__restrict__ items,
                  const int64_t *__restrict__ flop, const uint32_t *__restrict__ bitmaps, int words, int cap,
                  const int32_t *__restrict__ c_rp,
-                 int32_t *__restrict__ c_ci, T *__restrict__ c_v) {
+                 int32_t *__restrict__ c_ci, T *__restrict__ c_v, LongRows lr) {
+  static_assert(kLongRanges % (NT / 32) == 0, "every warp owns whole column ranges of a long row");
   extern __shared__ __align__(16) unsigned char sm_num_bm[];
   __shared__ int red[33];
   __shared__ Entry<T> s_ent[kStageN];
   __shared__ long long s_wsum[8];
   __shared__ int s_next;
+  __shared__ int s_lidx[kStageN];
+  __shared__ int s_lcnt[kStageN / 32];
   T *vals = reinterpret_cast<T *>(sm_num_bm);
   // word w of the row's column bitmap and the number of set bits before it
   uint2 *rk = reinterpret_cast<uint2 *>(sm_num_bm + (size_t)cap * sizeof(T));
@@ -542,28 +574,129 @@ __global__ void __launch_bounds__(NT, MINB)
   if (parts > 1) part_range(a, i, part, parts, &j_lo, &j_hi);
   __syncthreads();
   const int G = a.G;
-  block_row_products<kUN, true, T>(j_lo, j_hi, G, a.aci, (const T *)a.av, a.brp, a.bci,
-                                   (const T *)a.bv, (int32_t)a.k, a.err, Stage<T>{s_ent, &s_next, s_wsum},
-                                 [&](int32_t c, T av, T bv) {
-                                   const uint2 word = rk[c >> 5];
-                                   const int r = (int)word.y + __popc(word.x & ((1u << (c & 31)) - 1u));
-                                   if (r >= lo && r < hi) {
-                                     if (agg) {
-                                       const unsigned act = __activemask();
-                                       const unsigned grp = __match_any_sync(act, r);
-                                       const int ln = threadIdx.x & 31;
-                                       if (grp != (1u << ln)) {
-                                         const T v = av * bv;
-                                         T sum = T(0);
-                                         for (unsigned m = grp; m; m &= m - 1) sum += __shfl_sync(grp, v, __ffs(m) - 1);
-                                         if (ln == __ffs(grp) - 1 && !Val<T>::acc_shared(vals + (r - lo), sum, T(1)))
-                                           raise_err(a.err, kErrRetry);
-                                         return;
-                                       }
-                                     }
-                                     if (!Val<T>::acc_shared(vals + (r - lo), av, bv)) raise_err(a.err, kErrRetry);
-                                   }
-                                 });
+  const int span = hi - lo;
+  // rank of column c among the row's columns, relative to the window
+  auto rank_of = [&](int32_t c) {
+    const uint2 word = rk[c >> 5];
+    return (int)word.y + __popc(word.x & ((1u << (c & 31)) - 1u)) - lo;
+  };
+  // The large class (one block per SM) runs without long rows; the medium
+  // and small classes (more resident warps) take long rows whole.  Measured
+  // on R-MAT A*A, scale 16: long rows made the large class 35% slower and the
+  // medium class 6% faster; loading the next products before the current
+  // ones' updates (as the symbolic bitmap kernels do) made the large class 8%
+  // slower, the others spill it.
+  constexpr bool kLarge = MINB == 1;
+  block_row_products_long<kUN, true, false, T>(
+      j_lo, j_hi, G, a.aci, (const T *)a.av, a.brp, a.bci, (const T *)a.bv, (int32_t)a.k, a.err,
+      kLarge ? nullptr : lr.map,
+      Stage<T>{s_ent, &s_next, s_wsum, s_lidx, s_lcnt},
+      [&](const int32_t (&c)[kUN], const T (&av)[kUN], const T (&bv)[kUN], const bool (&ok)[kUN]) {
+        int r[kUN];
+        bool act[kUN];
+#pragma unroll
+        for (int u = 0; u < kUN; ++u) {
+          r[u] = ok[u] ? rank_of(c[u]) : -1;
+          act[u] = ok[u] && (unsigned)r[u] < (unsigned)span;
+        }
+        if (!agg) {
+          // one product after another (measured: issuing the kUN swaps together
+          // retried more and ran the large class 30% slower)
+#pragma unroll
+          for (int u = 0; u < kUN; ++u)
+            if (act[u] && !Val<T>::acc_shared(vals + r[u], av[u], bv[u])) raise_err(a.err, kErrRetry);
+          return;
+        }
+#pragma unroll
+        for (int u = 0; u < kUN; ++u) {
+          if (!act[u]) continue;
+          const unsigned actm = __activemask();
+          const unsigned grp = __match_any_sync(actm, r[u]);
+          const int ln = threadIdx.x & 31;
+          if (grp != (1u << ln)) {
+            const T v = av[u] * bv[u];
+            T sum = T(0);
+            for (unsigned m = grp; m; m &= m - 1) sum += __shfl_sync(grp, v, __ffs(m) - 1);
+            if (ln == __ffs(grp) - 1 && !Val<T>::acc_shared(vals + r[u], sum, T(1))) raise_err(a.err, kErrRetry);
+            continue;
+          }
+          if (!Val<T>::acc_shared(vals + r[u], av[u], bv[u])) raise_err(a.err, kErrRetry);
+        }
+      },
+      [&](int nlong, const int *lidx) {
+        // Warp w owns column ranges [w*kRPW, (w+1)*kRPW) of every long row.
+        // Its work is a sequence of slices: 32 consecutive entries of one long
+        // row's part in those ranges (distinct columns), long rows in stored
+        // order.  Slices are loaded kDepth ahead of the one being added, so the
+        // L2 latency of the loads overlaps the shared-memory updates; a
+        // __syncwarp after each slice orders the updates of long rows that
+        // share a column.
+        constexpr int kNW = NT / 32, kRPW = kLongRanges / kNW, kDepth = 4;
+        const unsigned full = 0xffffffffu;
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        const LEnt<T> *ent = reinterpret_cast<const LEnt<T> *>(lr.ent);
+        for (int l0 = 0; l0 < nlong; l0 += 32) {
+          const int cnt = min(32, nlong - l0);
+          int s0 = 0, s1 = 0;  // lane l: this warp's part of long entry l0 + l
+          T al = T(0);
+          if (lane < cnt) {
+            const Entry<T> st_e = s_ent[lidx[l0 + lane]];
+            const int32_t *o = lr.off + (size_t)st_e.off * (kLongRanges + 1) + wid * kRPW;
+            s0 = __ldg(o);
+            s1 = __ldg(o + kRPW);
+            al = st_e.a;
+          }
+          // next slice to load (warp-uniform): long entry ij, entries [ib, ie)
+          int ij = 0, ib = __shfl_sync(full, s0, 0), ie = __shfl_sync(full, s1, 0);
+          while (ij < cnt && ib >= ie) {
+            ++ij;
+            if (ij < cnt) {
+              ib = __shfl_sync(full, s0, ij);
+              ie = __shfl_sync(full, s1, ij);
+            }
+          }
+          int jq[kDepth];
+          int32_t cq[kDepth];
+          T vq[kDepth];
+          auto issue = [&](int k) {
+            jq[k] = -1;
+            cq[k] = -1;
+            vq[k] = T(0);
+            if (ij < cnt) {
+              jq[k] = ij;
+              if (ib + lane < ie) load_lent(ent + ib + lane, &cq[k], &vq[k]);
+              ib += 32;
+              while (ij < cnt && ib >= ie) {
+                ++ij;
+                if (ij < cnt) {
+                  ib = __shfl_sync(full, s0, ij);
+                  ie = __shfl_sync(full, s1, ij);
+                }
+              }
+            }
+          };
+#pragma unroll
+          for (int k = 0; k < kDepth; ++k) issue(k);
+          bool more = true;
+          while (more) {
+#pragma unroll
+            for (int k = 0; k < kDepth; ++k) {
+              if (!more) continue;
+              if (jq[k] < 0) {
+                more = false;
+                continue;
+              }
+              const T a = __shfl_sync(full, al, jq[k]);
+              if (cq[k] >= 0) {
+                const int r = rank_of(cq[k]);
+                if ((unsigned)r < (unsigned)span) vals[r] = Val<T>::mad(vals[r], a, vq[k]);
+              }
+              __syncwarp();
+              issue(k);
+            }
+          }
+        }
+      });
   __syncthreads();
   // Store ranks [lo, hi).  vals[] is already in rank order, so the block
   // copies it out with coalesced writes (a split row's parts add theirs).
@@ -601,20 +734,22 @@ __global__ void __launch_bounds__(NT, MINB)
 // bitmap of win_words words.
 template <typename T>
 __global__ void __launch_bounds__(1024, 1)
-    k_num_global(Args a, const int32_t *__restrict__ rows, int64_t nrows, int32_t *__restrict__ keys_all,
-                 T *__restrict__ vals_all, int64_t S, const int32_t *__restrict__ c_rp, int32_t *__restrict__ c_ci,
-                 T *__restrict__ c_v, int sorted, int win_words) {
+    k_num_global(Args a, BinRows br, int32_t *__restrict__ keys_all, T *__restrict__ vals_all, int64_t S,
+                 const int32_t *__restrict__ c_rp, int32_t *__restrict__ c_ci, T *__restrict__ c_v, int sorted,
+                 int win_words) {
   extern __shared__ __align__(16) unsigned char sm_num_gl[];
   __shared__ int red[33];
   __shared__ Entry<T> s_ent[kStageN];
   __shared__ long long s_wsum[8];
   __shared__ int s_next;
   __shared__ int cursor;
+  if (aborted(a)) return;
   int32_t *keys = keys_all + (size_t)blockIdx.x * S;
   T *vals = vals_all + (size_t)blockIdx.x * S;
   const uint32_t mask = (uint32_t)(S - 1);
   const int G = a.G;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const long long o0 = br.off[br.bin], nrows = br.off[br.bin + 1] - o0;
   for (int64_t r = blockIdx.x; r < nrows; r += gridDim.x) {
     for (int64_t s = threadIdx.x; s < S; s += blockDim.x) {
       keys[s] = kEmpty;
@@ -622,7 +757,7 @@ __global__ void __launch_bounds__(1024, 1)
     }
     if (threadIdx.x == 0) cursor = 0;
     __syncthreads();
-    const int32_t i = rows[r];
+    const int32_t i = br.perm[o0 + r];
     block_row_products<kUN, true, T>(a.arp[i], a.arp[i + 1], G, a.aci, (const T *)a.av, a.brp, a.bci,
                                    (const T *)a.bv, (int32_t)a.k, a.err, Stage<T>{s_ent, &s_next, s_wsum},
                                    [&](int32_t c, T av, T bv) { insert_acc<T, true>(keys, vals, mask, c, av, bv, a.err, a.probe, a.probe_ctr); });
@@ -702,22 +837,23 @@ static cudaError_t prep_num(K kernel, size_t smem) {
 }
 
 template <typename T, int S>
-static cudaError_t num_warp(spgemm_plan_s *p, cudaStream_t st, const Args &a, const int32_t *rows, int64_t n,
+static cudaError_t num_warp(spgemm_plan_s *p, cudaStream_t st, const Args &a, BinRows br, int64_t n,
                             const int32_t *c_rp, int32_t *c_ci, T *c_v) {
   const size_t smem = (size_t)kWarpsPerBlock * S * (sizeof(int32_t) + sizeof(T));
   cudaError_t e = prep_num(k_num_warp<T, S>, smem);
   if (e != cudaSuccess) return e;
-  const int64_t blocks = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  const int64_t blocks = launch_blocks(p, reinterpret_cast<const void *>(k_num_warp<T, S>), kWarpsPerBlock * 32, smem,
+                                       (n + kWarpsPerBlock - 1) / kWarpsPerBlock);
   {
     KernelScope ks(p, "num_warp_" + std::to_string(S), st);
-    k_num_warp<T, S><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, st>>>(
-        a, rows, n, c_rp, c_ci, c_v, (p->flags & SPGEMM_SORTED) ? 1 : 0);
+    k_num_warp<T, S><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, st>>>(a, br, c_rp, c_ci, c_v,
+                                                                           (p->flags & SPGEMM_SORTED) ? 1 : 0);
   }
   return cudaGetLastError();
 }
 
 template <typename T, int S>
-static cudaError_t num_block(spgemm_plan_s *p, cudaStream_t st, const Args &a, const int32_t *rows, int64_t n,
+static cudaError_t num_block(spgemm_plan_s *p, cudaStream_t st, const Args &a, BinRows br, int64_t n,
                              int threads, const int32_t *c_rp, int32_t *c_ci, T *c_v) {
   size_t smem = (size_t)S * (sizeof(int32_t) + sizeof(T));
   int mode = 0;
@@ -735,24 +871,28 @@ static cudaError_t num_block(spgemm_plan_s *p, cudaStream_t st, const Args &a, c
   }
   cudaError_t e = prep_num(k_num_block<T, S>, smem);
   if (e != cudaSuccess) return e;
+  const int64_t blocks = launch_blocks(p, reinterpret_cast<const void *>(k_num_block<T, S>), threads, smem, n);
   {
     KernelScope ks(p, "num_block_" + std::to_string(S), st);
-    k_num_block<T, S><<<(unsigned)n, threads, smem, st>>>(a, rows, c_rp, c_ci, c_v, mode, words);
+    k_num_block<T, S><<<(unsigned)blocks, threads, smem, st>>>(a, br, c_rp, c_ci, c_v, mode, words);
   }
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_numeric_t(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_ci, T *c_v) {
-  Args a{p->m, p->n, p->k, p->arp, p->aci, p->brp, p->bci, p->av, p->bv, p->G, &p->dc->err,
-         probe_mode(p->flags), (p->flags & SPGEMM_COUNT_PROBES) ? &p->dc->probe_stats[2][0] : nullptr};
+  Args a = phase_args(p, &p->dc->err, probe_mode(p->flags),
+                      (p->flags & SPGEMM_COUNT_PROBES) ? &p->dc->probe_stats[2][0] : nullptr);
+  if (p->ddrive) a.abort = &p->dc->err;
   // heavy bins first, each bin on the next side stream
   static const int order[kNumNumBins] = {kNumBitmapBin, kNumBitmapMBin, kNumBitmapSBin, kNumGlobalBin, 8, 7, 6, 5,
                                          4, 3, 2, 1, 0};
   const bool concurrent = use_side_streams(p);
   cudaError_t e = cudaSuccess;
   const int64_t nbm = p->sym_count[kSymBitmapBin] + p->sym_count[kSymBitmapMidBin];
-  if (nbm > 0 && p->bm_item_off[3] > 0) {
+  if (p->a_compact) e = compact_a_values(p);
+  if (e == cudaSuccess && p->long_ready && p->bm_item_off[3] > 0) e = long_rows_values(p);
+  if (e == cudaSuccess && nbm > 0 && p->bm_item_off[3] > 0) {
     // before the fork: every bitmap launch adds into the zeroed split rows
     KernelScope ks(p, "bm_zero_split");
     k_bm_zero_split<T><<<(unsigned)((nbm + 7) / 8), 256, 0, p->stream>>>(p->perm + p->sym_off[kSymBitmapBin], nbm,
@@ -763,21 +903,22 @@ cudaError_t launch_numeric_t(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_c
   int launched = 0;
   for (int o = 0; o < kNumNumBins && e == cudaSuccess; ++o) {
     const int b = order[o];
-    const int64_t n = p->num_count[b];
+    // a graph-mode plan launches every bin it may need (counts unknown on the host)
+    const int64_t n = p->ddrive ? ddrive_bin_rows(p, b, false) : p->num_count[b];
     if (n == 0) continue;
-    const int32_t *rows = p->perm2 + p->num_off[b];
+    const BinRows br{p->perm2, p->d_num_off, b};
     const BinCfg &c = kNumBins[b];
     cudaStream_t st = concurrent ? bin_stream(p, launched++) : p->stream;
     switch (b) {
-      case 0: e = num_warp<T, 64>(p, st, a, rows, n, c_rp, c_ci, c_v); break;
-      case 1: e = num_warp<T, 128>(p, st, a, rows, n, c_rp, c_ci, c_v); break;
-      case 2: e = num_warp<T, 256>(p, st, a, rows, n, c_rp, c_ci, c_v); break;
-      case 3: e = num_warp<T, 512>(p, st, a, rows, n, c_rp, c_ci, c_v); break;
-      case 4: e = num_warp<T, 1024>(p, st, a, rows, n, c_rp, c_ci, c_v); break;
-      case 5: e = num_block<T, 2048>(p, st, a, rows, n, c.threads, c_rp, c_ci, c_v); break;
-      case 6: e = num_block<T, 4096>(p, st, a, rows, n, c.threads, c_rp, c_ci, c_v); break;
-      case 7: e = num_block<T, 8192>(p, st, a, rows, n, c.threads, c_rp, c_ci, c_v); break;
-      case 8: e = num_block<T, 16384>(p, st, a, rows, n, c.threads, c_rp, c_ci, c_v); break;
+      case 0: e = num_warp<T, 64>(p, st, a, br, n, c_rp, c_ci, c_v); break;
+      case 1: e = num_warp<T, 128>(p, st, a, br, n, c_rp, c_ci, c_v); break;
+      case 2: e = num_warp<T, 256>(p, st, a, br, n, c_rp, c_ci, c_v); break;
+      case 3: e = num_warp<T, 512>(p, st, a, br, n, c_rp, c_ci, c_v); break;
+      case 4: e = num_warp<T, 1024>(p, st, a, br, n, c_rp, c_ci, c_v); break;
+      case 5: e = num_block<T, 2048>(p, st, a, br, n, c.threads, c_rp, c_ci, c_v); break;
+      case 6: e = num_block<T, 4096>(p, st, a, br, n, c.threads, c_rp, c_ci, c_v); break;
+      case 7: e = num_block<T, 8192>(p, st, a, br, n, c.threads, c_rp, c_ci, c_v); break;
+      case 8: e = num_block<T, 16384>(p, st, a, br, n, c.threads, c_rp, c_ci, c_v); break;
       case kNumBitmapSBin:
       case kNumBitmapMBin:
       case kNumBitmapBin: {
@@ -794,7 +935,7 @@ cudaError_t launch_numeric_t(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_c
           KernelScope ks(p, cls == 0 ? "num_bitmap_s" : cls == 1 ? "num_bitmap_m" : "num_bitmap_l", st);
           kern<<<(unsigned)n, p->bm_threads[cls], smem, st>>>(
               a, p->perm + p->sym_off[kSymBitmapBin], p->bm_items + p->bm_item_off[cls], p->flop, p->bitmaps, p->bm_words,
-              (int)p->bm_cap[cls], c_rp, c_ci, c_v);
+              (int)p->bm_cap[cls], c_rp, c_ci, c_v, long_rows(p));
         }
         e = cudaGetLastError();
         break;
@@ -809,7 +950,7 @@ cudaError_t launch_numeric_t(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_c
         {
           KernelScope ks(p, "num_global", st);
           k_num_global<T><<<(unsigned)p->gtab_blocks, c.threads, smem, st>>>(
-              a, rows, n, keys, vals, p->gtab_slots, c_rp, c_ci, c_v, (p->flags & SPGEMM_SORTED) ? 1 : 0, win_words);
+              a, br, keys, vals, p->gtab_slots, c_rp, c_ci, c_v, (p->flags & SPGEMM_SORTED) ? 1 : 0, win_words);
         }
         e = cudaGetLastError();
         break;

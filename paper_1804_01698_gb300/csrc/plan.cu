@@ -49,19 +49,28 @@ cudaError_t launch_numeric_f64(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c
 cudaError_t launch_numeric_f32(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_ci, void *c_v);
 cudaError_t launch_numeric_i64(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_ci, void *c_v);
 
-__constant__ int64_t c_hash_caps[9] = {32, 64, 128, 256, 512, 1536, 3072, 6144, 12288};
+HashCaps hash_caps(int warp_load_pct, int block_load_pct) {
+  const int wp = warp_load_pct > 0 ? warp_load_pct : 50;
+  const int bp = block_load_pct > 0 ? block_load_pct : 75;
+  HashCaps c{};
+  for (int t = 0; t < 9; ++t) {
+    const long long slots = 64LL << t;
+    c.cap[t] = slots * (t < 5 ? wp : bp) / 100;
+  }
+  return c;
+}
 
-__device__ __forceinline__ int hash_bin_of(int64_t b) {
+__device__ __forceinline__ int hash_bin_of(int64_t b, const HashCaps &caps) {
 #pragma unroll
   for (int t = 0; t < 9; ++t)
-    if (b <= c_hash_caps[t]) return t;
+    if (b <= caps.cap[t]) return t;
   return 9;
 }
 
-__device__ __forceinline__ int sym_bin_of(int64_t b, int64_t bitmap_min) {
+__device__ __forceinline__ int sym_bin_of(int64_t b, int64_t bitmap_min, const HashCaps &caps) {
   if (b <= 0) return 255;
   if (bitmap_min > 0 && b > bitmap_min) return b > kBitmapMidMax ? kSymBitmapBin : kSymBitmapMidBin;
-  const int t = hash_bin_of(b);
+  const int t = hash_bin_of(b, caps);
   if (t < 9) return t;
   if (b <= kBlockSymMax) return 9;
   return kSymGlobalBin;
@@ -71,97 +80,94 @@ __device__ __forceinline__ bool is_bitmap_row(int sym_bin) {
   return sym_bin == kSymBitmapBin || sym_bin == kSymBitmapMidBin;
 }
 
-__device__ __forceinline__ int num_bin_of(int64_t nnz) {
+__device__ __forceinline__ int num_bin_of(int64_t nnz, const HashCaps &caps) {
   if (nnz <= 0) return 255;
-  const int t = hash_bin_of(nnz);
+  const int t = hash_bin_of(nnz, caps);
   return t < 9 ? t : kNumGlobalBin;
 }
 
-// Sum over entries j0, j0 + stride, ... (below r1) of A's row of the lengths
-// of the rows of B they select, four independent gathers of B's row_ptr in
-// flight per thread; indices outside A's columns or malformed rows of B raise
-// kErrCsr and count nothing.
-__device__ __forceinline__ int64_t flop_span(const Args &a, int64_t j0, int64_t r1, int stride, int64_t nnz_b) {
-  int64_t f = 0;
-  for (; j0 < r1; j0 += 4 * stride) {
+// The flop pass (Sec. 4.1, Fig. "RowsToThreads", step 1) in two sweeps, so
+// that no thread walks a row: every stored a_ik first gets the length of the
+// row of B it selects, an exclusive prefix sum P of those lengths follows,
+// and row i's flop is then P[rp[i+1]] - P[rp[i]].  One thread per entry and
+// per row keeps every SM busy whatever the row lengths (a warp per row would
+// wait on its dependent loads row after row, and a hub row of thousands of
+// entries would hold it for len/32 steps).
+
+// elen[j] = nnz(b_k*) for stored entry j (column k); columns outside A or
+// malformed rows of B raise kErrCsr and count 0.  Counts the entries that
+// select a non-empty row of B.
+__global__ void __launch_bounds__(256)
+    k_entry_flop(Args a, int64_t nnz_a, int64_t nnz_b, long long *__restrict__ elen, DevCounters *dc) {
+  __shared__ unsigned long long s_nz;
+  if (threadIdx.x == 0) s_nz = 0;
+  __syncthreads();
+  unsigned long long nz = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
+  for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x * 4 + threadIdx.x; j0 < nnz_a; j0 += stride) {
     int32_t kk[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) kk[u] = j0 + stride * u < r1 ? __ldg(a.aci + j0 + stride * u) : -1;
+    for (int u = 0; u < 4; ++u) kk[u] = j0 + u * blockDim.x < nnz_a ? __ldg(a.aci + j0 + u * blockDim.x) : 0;
     int64_t b0[4], b1[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const bool ok = j0 + stride * u < r1 && (uint64_t)(int64_t)kk[u] < (uint64_t)a.n;
+      const bool in = j0 + u * blockDim.x < nnz_a;
+      const bool ok = in && (uint64_t)(int64_t)kk[u] < (uint64_t)a.n;
       b0[u] = ok ? __ldg(a.brp + kk[u]) : 0;
       b1[u] = ok ? __ldg(a.brp + kk[u] + 1) : 0;
-      if (j0 + stride * u < r1 && !ok) raise_err(a.err, kErrCsr);
+      if (in && !ok) raise_err(a.err, kErrCsr);
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      if (!(0 <= b0[u] && b0[u] <= b1[u] && b1[u] <= nnz_b)) {
-        raise_err(a.err, kErrCsr);
-        continue;
-      }
-      f += b1[u] - b0[u];
+      const int64_t j = j0 + u * blockDim.x;
+      if (j >= nnz_a) continue;
+      long long len = 0;
+      if (0 <= b0[u] && b0[u] <= b1[u] && b1[u] <= nnz_b) len = b1[u] - b0[u];
+      else raise_err(a.err, kErrCsr);
+      elen[j] = len;
+      nz += len > 0;
     }
   }
-  return f;
+  nz = warp_sum(nz);
+  if ((threadIdx.x & 31) == 0 && nz) atomicAdd(&s_nz, nz);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_nz) atomicAdd(&dc->nnz_a_used, s_nz);
 }
 
-// Rows of A with more stored entries than this are summed by the whole
-// block instead of one warp (a hub row of thousands of entries would
-// otherwise hold its warp, and the launch, for its len/128 dependent steps).
-constexpr int64_t kFlopLongRow = 1024;
-
-// One warp per row of A, 8 rows per 256-thread block; the block's long rows
-// are then summed by all 256 threads together.
+// Row i (grid-stride): flop[i] = P[rp[i+1]] - P[rp[i]], its symbolic bin and
+// the plan's counters.  Row pointers must run from 0 to nnz(A) without
+// decreasing; a row that breaks it raises kErrCsr and counts no flop.
 __global__ void __launch_bounds__(256)
-    k_row_flop(Args a, int64_t nnz_a, int64_t nnz_b, int64_t bitmap_min, int64_t *__restrict__ flop,
-               uint8_t *__restrict__ rbin, int32_t *__restrict__ nnz_row, DevCounters *dc) {
+    k_row_flop(Args a, int64_t nnz_a, int64_t bitmap_min, HashCaps caps, int64_t gcap,
+               const long long *__restrict__ P, int64_t *__restrict__ flop, uint8_t *__restrict__ rbin,
+               int32_t *__restrict__ nnz_row, DevCounters *dc) {
   __shared__ unsigned int hist[kNumSymBins];
   __shared__ unsigned long long hflop[kNumSymBins];
   __shared__ unsigned long long s_tot, s_max, s_maxg, s_extra;
-  __shared__ unsigned long long s_long_f[8];
-  __shared__ unsigned s_long;  // bit w: row w of the block is long
   if (threadIdx.x < kNumSymBins) {
     hist[threadIdx.x] = 0;
     hflop[threadIdx.x] = 0;
   }
-  if (threadIdx.x < 8) s_long_f[threadIdx.x] = 0;
-  if (threadIdx.x == 0) s_tot = s_max = s_maxg = s_extra = s_long = 0;
+  if (threadIdx.x == 0) s_tot = s_max = s_maxg = s_extra = 0;
   __syncthreads();
-  const int sub = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t row = (int64_t)blockIdx.x * 8 + warp;
-  int64_t f = 0;
-  int64_t r0 = 0, r1 = 0;
-  if (row < a.m) {
-    r0 = a.arp[row];
-    r1 = a.arp[row + 1];
-    if (!(0 <= r0 && r0 <= r1 && r1 <= nnz_a)) {
-      if (sub == 0) raise_err(a.err, kErrCsr);
-      r0 = r1 = 0;
-    }
-    if (r1 - r0 > kFlopLongRow) {
-      if (sub == 0) atomicOr(&s_long, 1u << warp);
+  unsigned long long tot = 0, mx = 0, mxg = 0, extra = 0;
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < a.m;
+       row += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r0 = a.arp[row], r1 = a.arp[row + 1];
+    int64_t f = 0;
+    if (0 <= r0 && r0 <= r1 && r1 <= nnz_a && (row > 0 || r0 == 0) && (row < a.m - 1 || r1 == nnz_a)) {
+      f = P[r1] - P[r0];
     } else {
-      f = flop_span(a, r0 + sub, r1, 32, nnz_b);
+      raise_err(a.err, kErrCsr);
     }
-  }
-  __syncthreads();
-  const unsigned longs = s_long;
-  for (int w = 0; w < 8; ++w) {
-    if (!((longs >> w) & 1u)) continue;
-    const int64_t rw = (int64_t)blockIdx.x * 8 + w;  // a valid row, checked by its warp
-    int64_t g = flop_span(a, (int64_t)a.arp[rw] + threadIdx.x, a.arp[rw + 1], 256, nnz_b);
-    g = warp_sum(g);
-    if (sub == 0 && g) atomicAdd(&s_long_f[w], (unsigned long long)g);
-  }
-  if (longs) __syncthreads();
-  if ((longs >> warp) & 1u) f = (int64_t)s_long_f[warp];
-  else f = warp_sum(f);
-  if (sub == 0 && row < a.m) {
     flop[row] = f;
     const int64_t bound = f < a.k ? f : a.k;
-    const int bin = sym_bin_of(bound, bitmap_min);
+    int bin = sym_bin_of(bound, bitmap_min, caps);
+    if (bin == kSymGlobalBin && gcap >= 0 && bound >= gcap) {
+      // graph mode: no table was planned for a row this large
+      raise_err(a.err, kErrCapacity);
+      bin = 255;
+    }
     rbin[row] = (uint8_t)bin;
     if (bin == 255) {
       nnz_row[row] = 0;
@@ -169,10 +175,20 @@ __global__ void __launch_bounds__(256)
       atomicAdd(&hist[bin], 1u);
       atomicAdd(&hflop[bin], (unsigned long long)f);
     }
-    if (bin == kSymGlobalBin) atomicMax(&s_maxg, (unsigned long long)bound);
-    if (bin == kSymBitmapBin && sym_split_parts(f) > 1) atomicAdd(&s_extra, (unsigned long long)(sym_split_parts(f) - 1));
-    atomicAdd(&s_tot, (unsigned long long)f);
-    atomicMax(&s_max, (unsigned long long)f);
+    if (bin == kSymGlobalBin && (unsigned long long)bound > mxg) mxg = (unsigned long long)bound;
+    if (bin == kSymBitmapBin && sym_split_parts(f) > 1) extra += (unsigned long long)(sym_split_parts(f) - 1);
+    tot += (unsigned long long)f;
+    if ((unsigned long long)f > mx) mx = (unsigned long long)f;
+  }
+  tot = warp_sum(tot);
+  extra = warp_sum(extra);
+  mx = warp_max(mx);
+  mxg = warp_max(mxg);
+  if ((threadIdx.x & 31) == 0) {
+    if (tot) atomicAdd(&s_tot, tot);
+    if (extra) atomicAdd(&s_extra, extra);
+    if (mx) atomicMax(&s_max, mx);
+    if (mxg) atomicMax(&s_maxg, mxg);
   }
   __syncthreads();
   if (threadIdx.x < kNumSymBins && hist[threadIdx.x]) {
@@ -182,19 +198,26 @@ __global__ void __launch_bounds__(256)
   if (threadIdx.x == 0) {
     if (s_tot) atomicAdd(&dc->total_flop, s_tot);
     if (s_extra) atomicAdd(&dc->sym_split_extra, s_extra);
-    atomicMax(&dc->max_flop, s_max);
-    atomicMax(&dc->max_bound_global, s_maxg);
+    if (s_max) atomicMax(&dc->max_flop, s_max);
+    if (s_maxg) atomicMax(&dc->max_bound_global, s_maxg);
   }
 }
 
-struct Offsets {
-  long long v[16];
-};
+// off[b] = rows of bins below b (off[0] = 0 .. off[nbins]), on the device.
+__global__ void k_bin_offsets(const unsigned long long *__restrict__ count, int nbins, long long *__restrict__ off) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  long long run = 0;
+  for (int b = 0; b < nbins; ++b) {
+    off[b] = run;
+    run += (long long)count[b];
+  }
+  off[nbins] = run;
+}
 
 // Rows i with bin_of[i] != 255 go to perm[off[bin] + arbitrary rank].
 __global__ void __launch_bounds__(256)
-    k_bin_scatter(const uint8_t *__restrict__ bin_of, int64_t m, Offsets off, unsigned long long *cursor,
-                  int32_t *__restrict__ perm, int nbins) {
+    k_bin_scatter(const uint8_t *__restrict__ bin_of, int64_t m, const long long *__restrict__ off,
+                  unsigned long long *cursor, int32_t *__restrict__ perm, int nbins) {
   __shared__ unsigned int hist[16];
   __shared__ unsigned long long base[16];
   if (threadIdx.x < 16) hist[threadIdx.x] = 0;
@@ -206,15 +229,16 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   if (threadIdx.x < nbins && hist[threadIdx.x]) base[threadIdx.x] = atomicAdd(&cursor[threadIdx.x], hist[threadIdx.x]);
   __syncthreads();
-  if (b < nbins) perm[off.v[b] + (long long)base[b] + local] = (int32_t)i;
+  if (b < nbins) perm[off[b] + (long long)base[b] + local] = (int32_t)i;
 }
 
 constexpr int kScanThreads = 1024;
 constexpr int kScanPer = 4;
 constexpr int kScanTile = kScanThreads * kScanPer;
 
+template <typename InT>
 __global__ void __launch_bounds__(kScanThreads)
-    k_scan_reduce(const int32_t *__restrict__ x, int64_t m, long long *__restrict__ partial) {
+    k_scan_reduce(const InT *__restrict__ x, int64_t m, long long *__restrict__ partial) {
   __shared__ long long red[33];
   const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
   long long s = 0;
@@ -226,7 +250,7 @@ __global__ void __launch_bounds__(kScanThreads)
 }
 
 __global__ void __launch_bounds__(kScanThreads)
-    k_scan_spine(long long *partial, int64_t nblk, long long max_nnz, DevCounters *dc) {
+    k_scan_spine(long long *partial, int64_t nblk, long long max_nnz, unsigned long long *total, uint32_t *err) {
   __shared__ long long red[33];
   long long carry = 0;
   for (int64_t c0 = 0; c0 < nblk; c0 += kScanThreads) {
@@ -238,17 +262,19 @@ __global__ void __launch_bounds__(kScanThreads)
     carry += tot;
   }
   if (threadIdx.x == 0) {
-    dc->nnz_c = (unsigned long long)carry;
-    if (carry > max_nnz) raise_err(&dc->err, kErrOverflow);
+    *total = (unsigned long long)carry;
+    if (carry > max_nnz) raise_err(err, kErrOverflow);
   }
 }
 
+// out[i] = x[0] + ... + x[i-1] for i = 0..m; out may be x itself (each thread
+// reads its elements before it writes them, and the reduce pass is done).
+template <typename InT, typename OutT>
 __global__ void __launch_bounds__(kScanThreads)
-    k_scan_apply(const int32_t *__restrict__ x, int64_t m, const long long *__restrict__ partial,
-                 int32_t *__restrict__ out) {
+    k_scan_apply(const InT *x, int64_t m, const long long *__restrict__ partial, OutT *out) {
   __shared__ long long red[33];
   const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
-  int32_t v[kScanPer];
+  InT v[kScanPer];
   long long s = 0;
 #pragma unroll
   for (int u = 0; u < kScanPer; ++u) {
@@ -259,15 +285,16 @@ __global__ void __launch_bounds__(kScanThreads)
   long long run = partial[blockIdx.x] + block_excl_scan(s, red, &tot);
 #pragma unroll
   for (int u = 0; u < kScanPer; ++u) {
-    if (base + u < m) out[base + u] = (int32_t)run;
+    if (base + u < m) out[base + u] = (OutT)run;
     run += v[u];
-    if (base + u == m - 1) out[m] = (int32_t)run;
+    if (base + u == m - 1) out[m] = (OutT)run;
   }
 }
 
 __global__ void __launch_bounds__(256)
     k_num_classify(const int32_t *__restrict__ nnz_row, const uint8_t *__restrict__ rbin,
-                   const int64_t *__restrict__ flop, int64_t m, uint8_t *__restrict__ rbin2, DevCounters *dc) {
+                   const int64_t *__restrict__ flop, int64_t m, HashCaps caps, int64_t gcap,
+                   uint8_t *__restrict__ rbin2, DevCounters *dc) {
   __shared__ unsigned int hist[kNumNumBins];
   __shared__ unsigned long long hflop[kNumNumBins];
   __shared__ unsigned long long s_maxg;
@@ -282,7 +309,11 @@ __global__ void __launch_bounds__(256)
     int b = 255;
     if (!is_bitmap_row(rbin[i])) {
       const int32_t z = nnz_row[i];
-      b = num_bin_of(z);
+      b = num_bin_of(z, caps);
+      if (b == kNumGlobalBin && gcap >= 0 && (int64_t)z * 4 / 3 >= gcap) {
+        raise_err(&dc->err, kErrCapacity);  // graph mode: the planned tables are too small
+        b = 255;
+      }
       if (b == kNumGlobalBin) atomicMax(&s_maxg, (unsigned long long)z);
     }
     rbin2[i] = (uint8_t)b;
@@ -398,6 +429,38 @@ static int sm_count() {
     cached[dev] = v > 0 ? v : 1;
   }
   return cached[dev];
+}
+
+int64_t launch_blocks(const spgemm_plan_s *p, const void *kernel, int threads, size_t smem, int64_t exact) {
+  if (!p->ddrive) return exact;
+  static std::mutex mu;
+  static std::map<std::pair<const void *, size_t>, int> cache;
+  int per_sm = 0;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    auto it = cache.find({kernel, smem});
+    if (it != cache.end()) per_sm = it->second;
+  }
+  if (per_sm == 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
+      per_sm = 1;
+    std::lock_guard<std::mutex> g(mu);
+    cache[{kernel, smem}] = per_sm;
+  }
+  const int64_t resident = (int64_t)per_sm * sm_count();
+  return std::max<int64_t>(1, std::min<int64_t>(exact, resident));
+}
+
+int64_t ddrive_bin_rows(const spgemm_plan_s *p, int b, bool symbolic) {
+  // graph mode has no bitmap rows; the global bin runs only with its tables
+  if (symbolic) {
+    if (b == kSymBitmapBin || b == kSymBitmapMidBin) return 0;
+    if (b == kSymGlobalBin) return p->gtab ? p->m : 0;
+    return p->m;
+  }
+  if (b == kNumBitmapBin || b == kNumBitmapSBin || b == kNumBitmapMBin) return 0;
+  if (b == kNumGlobalBin) return p->gtab ? p->m : 0;
+  return p->m;
 }
 
 // Side streams and their fork/join events come from a per-device pool: a
@@ -538,9 +601,14 @@ int read_counters(spgemm_plan_s *p) {
     g_last_error = "input CSR has an index out of range or a malformed row_ptr";
     return SPGEMM_ERR_INVALID_CSR;
   }
+  if (err & kErrCapacity) {
+    g_last_error = "C or one of its rows exceeds the capacity the batch graph was planned with";
+    return SPGEMM_ERR_OUT_OF_MEMORY;
+  }
   if (err & kErrOverflow) {
-    g_last_error = "nnz(C) exceeds int32 indexing";
-    return SPGEMM_ERR_INDEX_OVERFLOW;
+    g_last_error = p->ddrive ? "nnz(C) exceeds the pool the batch graph was planned with"
+                             : "nnz(C) exceeds int32 indexing";
+    return p->ddrive ? SPGEMM_ERR_OUT_OF_MEMORY : SPGEMM_ERR_INDEX_OVERFLOW;
   }
   if (err) {
     g_last_error = "device-side check failed (hash probe or atomic retry bound)";
@@ -582,6 +650,12 @@ void free_ws(spgemm_plan_s *p) {
   if (p->bm_items) cudaFreeAsync(p->bm_items, p->stream);
   if (p->sym_items) cudaFreeAsync(p->sym_items, p->stream);
   if (p->gtab) cudaFreeAsync(p->gtab, p->stream);
+  if (p->long_ws) cudaFreeAsync(p->long_ws, p->stream);
+  if (p->acmp_ws) cudaFreeAsync(p->acmp_ws, p->stream);
+  p->acmp_ws = nullptr;
+  p->a_compact = false;
+  p->long_ws = nullptr;
+  p->long_ready = false;
   p->ws_fixed = nullptr;
   p->bitmaps = nullptr;
   p->bm_items = nullptr;
@@ -616,6 +690,51 @@ int alloc_gtab(spgemm_plan_s *p, int64_t slots, size_t entry_bytes, int64_t rows
   return SPGEMM_OK;
 }
 
+// Compacted A (Sec. 4.1's flop pass counts, per row, the stored a_ik whose
+// row of B is not empty): when fewer than half of A's entries select a
+// non-empty row of B, as in the BFS-frontier product A * F, the phases walk
+// a copy of A without the others, which add nothing to C.  Row pointers are
+// the scan of the counts; the copy's columns and sources are gathered once,
+// its values before every numeric phase.
+int compact_a(spgemm_plan_s *p) {
+  const int64_t m = p->m, nz = p->nnz_a_used, ne = p->nnz_a;
+  const size_t vs = value_size(p->dtype);
+  const size_t o_rp = 0;
+  const size_t o_ci = align_up((size_t)(m + 1) * 4, 256);
+  const size_t o_v = o_ci + align_up((size_t)nz * 4, 256);
+  const size_t o_src = o_v + align_up((size_t)nz * vs, 256);
+  const size_t o_pos = o_src + align_up((size_t)nz * 4, 256);
+  const size_t bytes = o_pos + align_up((size_t)(ne + 1) * 4, 256);
+  cudaError_t e = cudaMallocAsync(&p->acmp_ws, bytes, p->stream);
+  if (e != cudaSuccess) {
+    p->acmp_ws = nullptr;
+    return fail_cuda(e, "allocating the compacted A");
+  }
+  p->acmp_bytes = bytes;
+  char *b = static_cast<char *>(p->acmp_ws);
+  p->karp = reinterpret_cast<int32_t *>(b + o_rp);
+  p->kaci = reinterpret_cast<int32_t *>(b + o_ci);
+  p->kav = b + o_v;
+  p->asrc = reinterpret_cast<int32_t *>(b + o_src);
+  int32_t *pos = reinterpret_cast<int32_t *>(b + o_pos);
+  // pos[j] = kept entries before entry j (kept: P[j + 1] > P[j])
+  const int64_t nblk = (ne + kScanTile - 1) / kScanTile;
+  {
+    KernelScope ks(p, "compact_a");
+    e = compact_a_keep(p, pos);
+    if (e == cudaSuccess) {
+      k_scan_reduce<<<(unsigned)nblk, kScanThreads, 0, p->stream>>>(pos, ne, p->epart);
+      k_scan_spine<<<1, kScanThreads, 0, p->stream>>>(p->epart, nblk, INT32_MAX, &p->dc->scan_total, &p->dc->err);
+      k_scan_apply<<<(unsigned)nblk, kScanThreads, 0, p->stream>>>(pos, ne, p->epart, pos);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = compact_a_gather(p, pos);
+  }
+  if (e != cudaSuccess) return fail_cuda(e, "compacting A");
+  p->a_compact = true;
+  return SPGEMM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -641,18 +760,25 @@ int spgemm_plan_create(spgemm_plan_t *out, const spgemm_csr *A, const spgemm_csr
   return spgemm_plan_create_tuned(out, A, B, dtype, flags, stream, nullptr);
 }
 
-int spgemm_plan_create_tuned(spgemm_plan_t *out, const spgemm_csr *A, const spgemm_csr *B, int dtype,
-                             unsigned flags, void *stream, const spgemm_tuning *tuning) {
-  NvtxRange nvtx("spgemm_plan_create");
+}  // extern "C"
+
+namespace sg {
+
+// Validates the arguments, fills the plan and allocates its fixed
+// workspace.  A graph-mode plan has no bitmap rows and no long rows.
+int plan_init(spgemm_plan_s **out, const spgemm_csr *A, const spgemm_csr *B, int dtype, unsigned flags,
+              cudaStream_t stream, const spgemm_tuning *tuning, bool graph) {
   if (!out) return SPGEMM_ERR_INVALID_ARGUMENT;
   *out = nullptr;
   g_last_error.clear();
   if (tuning) {
     const int g = tuning->lanes_per_entry;
+    auto pct_ok = [](int v) { return v == 0 || (v >= 5 && v <= 95); };
     if ((g != 0 && g != 4 && g != 8 && g != 16 && g != 32) || tuning->reserved != 0 ||
-        tuning->bitmap_min_bound < -1 || tuning->max_nnz_c < 0 || tuning->max_nnz_c > INT32_MAX) {
-      set_last_error("tuning: lanes_per_entry must be 0, 4, 8, 16 or 32, bitmap_min_bound >= -1 and "
-                     "0 <= max_nnz_c <= 2^31-1");
+        tuning->bitmap_min_bound < -1 || tuning->max_nnz_c < 0 || tuning->max_nnz_c > INT32_MAX ||
+        tuning->long_row_min < -1 || !pct_ok(tuning->warp_load_pct) || !pct_ok(tuning->block_load_pct)) {
+      set_last_error("tuning: lanes_per_entry must be 0, 4, 8, 16 or 32, bitmap_min_bound >= -1, "
+                     "0 <= max_nnz_c <= 2^31-1, long_row_min >= -1 and the load percentages 0 or 5..95");
       return SPGEMM_ERR_INVALID_ARGUMENT;
     }
   }
@@ -687,14 +813,15 @@ int spgemm_plan_create_tuned(spgemm_plan_t *out, const spgemm_csr *A, const spge
   p->bv = B->vals;
   p->dtype = dtype;
   p->flags = flags;
-  p->stream = (cudaStream_t)stream;
+  p->stream = stream;
   p->device = dev;
   p->G = 32;  // set from the flop pass below
   p->tune_G = tuning ? tuning->lanes_per_entry : 0;
   p->tune_bm_min = tuning ? tuning->bitmap_min_bound : 0;
   p->max_nnz_c = tuning && tuning->max_nnz_c > 0 ? tuning->max_nnz_c : INT32_MAX;
   p->span_cols = p->k;
-  p->bitmap_ok = p->k <= kBitmapMaxCols;
+  p->bitmap_ok = !graph && p->k <= kBitmapMaxCols;
+  p->ddrive = graph;
   p->bm_words = (int)((p->k + 31) / 32);
   // bitmap classes: 3, 2 and 1 blocks per SM (228 KB per SM, 1 KB per block kept by the system)
   p->bm_cap[2] = bitmap_capacity(dtype, p->bm_words, max_smem_per_block());
@@ -704,6 +831,12 @@ int spgemm_plan_create_tuned(spgemm_plan_t *out, const spgemm_csr *A, const spge
   p->bm_threads[1] = kNumBins[kNumBitmapMBin].threads;
   p->bm_threads[2] = kNumBins[kNumBitmapBin].threads;
   if (p->bitmap_ok && p->bm_cap[2] < 256) p->bitmap_ok = false;
+  p->caps = hash_caps(tuning ? tuning->warp_load_pct : 0, tuning ? tuning->block_load_pct : 0);
+  {
+    const int64_t lt = tuning ? tuning->long_row_min : 0;
+    p->long_min = !p->bitmap_ok || lt < 0 || p->nnz_b == 0 ? 0 : lt > 0 ? lt : long_row_min_default(p->k);
+    p->long_cap = p->long_min > 0 ? p->nnz_b / p->long_min + 1 : 0;
+  }
 
   // fixed workspace: counters, then per-row arrays
   const int64_t m = p->m;
@@ -725,6 +858,19 @@ int spgemm_plan_create_tuned(spgemm_plan_t *out, const spgemm_csr *A, const spge
   off = align_up(off + (size_t)m * 4, 256);
   const size_t o_part = off;
   off = align_up(off + (size_t)nblk * 8, 256);
+  const int64_t nblk_e = (p->nnz_a + kScanTile - 1) / kScanTile + 1;
+  const size_t o_eflop = off;
+  off = align_up(off + (size_t)(p->nnz_a + 1) * 8, 256);
+  const size_t o_epart = off;
+  off = align_up(off + (size_t)nblk_e * 8, 256);
+  const size_t o_doff = off;
+  off = align_up(off + 2 * 16 * sizeof(long long), 256);
+  const size_t o_lmap = off;
+  if (p->long_min > 0) off = align_up(off + (size_t)p->n * 4, 256);
+  const size_t o_lrow = off;
+  if (p->long_min > 0) off = align_up(off + (size_t)p->long_cap * 4, 256);
+  const size_t o_lbase = off;
+  if (p->long_min > 0) off = align_up(off + (size_t)p->long_cap * 4, 256);
   e = cudaMallocAsync(&p->ws_fixed, off, p->stream);
   if (e != cudaSuccess) {
     p->ws_fixed = nullptr;
@@ -743,21 +889,133 @@ int spgemm_plan_create_tuned(spgemm_plan_t *out, const spgemm_csr *A, const spge
   p->rbin2 = (uint8_t *)(base + o_rbin2);
   p->perm2 = (int32_t *)(base + o_perm2);
   (void)o_part;
+  p->eflop = (long long *)(base + o_eflop);
+  p->epart = (long long *)(base + o_epart);
+  p->d_sym_off = (long long *)(base + o_doff);
+  p->d_num_off = p->d_sym_off + 16;
+  if (p->long_min > 0) {
+    p->lmap = (int32_t *)(base + o_lmap);
+    p->lrow = (int32_t *)(base + o_lrow);
+    p->lbase = (int32_t *)(base + o_lbase);
+  }
 
-  int rc = SPGEMM_OK;
-  e = cudaMemsetAsync(p->dc, 0, sizeof(DevCounters), p->stream);
-  if (e == cudaSuccess && m > 0) {
-    Args a{p->m, p->n, p->k, p->arp, p->aci, p->brp, p->bci, p->av, p->bv, p->G, &p->dc->err};
+  *out = p;
+  return SPGEMM_OK;
+}
+
+// The flop pass, the symbolic bin offsets and the long rows' marks, on the
+// plan's stream (Sec. 4.1, Fig. "RowsToThreads", step 1).
+cudaError_t enqueue_flop(spgemm_plan_s *p) {
+  const int64_t m = p->m;
+  cudaError_t e = cudaMemsetAsync(p->dc, 0, sizeof(DevCounters), p->stream);
+  if (e != cudaSuccess || m == 0) return e;
+  Args a{p->m, p->n, p->k, p->arp, p->aci, p->brp, p->bci, p->av, p->bv, p->G, &p->dc->err};
+  {
+    KernelScope ks(p, "row_flop");
+    const int64_t bm_min = !p->bitmap_ok || p->tune_bm_min < 0 ? 0
+                           : p->tune_bm_min > 0                 ? p->tune_bm_min
+                                                                : bitmap_min_bound(p->k);
+    const int64_t ne = p->nnz_a;
+    if (ne > 0) {
+      const int64_t nblk = (ne + kScanTile - 1) / kScanTile;
+      const int64_t eb = std::min<int64_t>((ne + 1023) / 1024, 8 * (int64_t)sm_count());
+      k_entry_flop<<<(unsigned)eb, 256, 0, p->stream>>>(a, ne, p->nnz_b, p->eflop, p->dc);
+      k_scan_reduce<<<(unsigned)nblk, kScanThreads, 0, p->stream>>>(p->eflop, ne, p->epart);
+      k_scan_spine<<<1, kScanThreads, 0, p->stream>>>(p->epart, nblk, LLONG_MAX, &p->dc->scan_total, &p->dc->err);
+      k_scan_apply<<<(unsigned)nblk, kScanThreads, 0, p->stream>>>(p->eflop, ne, p->epart, p->eflop);
+    } else {
+      e = cudaMemsetAsync(p->eflop, 0, sizeof(long long), p->stream);
+    }
+    const int64_t rb = std::min<int64_t>((m + 255) / 256, 8 * (int64_t)sm_count());
+    k_row_flop<<<(unsigned)rb, 256, 0, p->stream>>>(a, p->nnz_a, bm_min, p->caps, p->gcap_bound, p->eflop, p->flop,
+                                                    p->rbin, p->nnz_row, p->dc);
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    k_bin_offsets<<<1, 32, 0, p->stream>>>(p->dc->sym_count, kNumSymBins, p->d_sym_off);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = long_rows_mark(p);
+  return e;
+}
+
+// The symbolic kernels, the scan of the row counts into c_row_ptr (with the
+// nnz(C) limit), the numeric bins and their device offsets.
+cudaError_t enqueue_symbolic(spgemm_plan_s *p, int32_t *c_row_ptr) {
+  cudaError_t e = launch_symbolic(p);
+  if (e != cudaSuccess) return e;
+  const int64_t m = p->m;
+  if (m == 0) {
+    e = cudaMemsetAsync(c_row_ptr, 0, sizeof(int32_t), p->stream);
+  } else {
+    const int64_t nblk = (m + kScanTile - 1) / kScanTile;
+    // partial[] is the last segment of the fixed workspace, after perm2
+    long long *partial = (long long *)((char *)p->perm2 + align_up((size_t)m * 4, 256));
     {
-      KernelScope ks(p, "row_flop");
-      const int64_t bm_min = !p->bitmap_ok || p->tune_bm_min < 0 ? 0
-                             : p->tune_bm_min > 0                 ? p->tune_bm_min
-                                                                  : bitmap_min_bound(p->k);
-      k_row_flop<<<(unsigned)((m + 7) / 8), 256, 0, p->stream>>>(a, p->nnz_a, p->nnz_b, bm_min,
-                                                                    p->flop, p->rbin, p->nnz_row, p->dc);
+      KernelScope ks(p, "scan_reduce");
+      k_scan_reduce<<<(unsigned)nblk, kScanThreads, 0, p->stream>>>(p->nnz_row, m, partial);
+    }
+    {
+      KernelScope ks(p, "scan_spine");
+      k_scan_spine<<<1, kScanThreads, 0, p->stream>>>(partial, nblk, p->max_nnz_c, &p->dc->nnz_c, &p->dc->err);
+    }
+    {
+      KernelScope ks(p, "scan_apply");
+      k_scan_apply<<<(unsigned)nblk, kScanThreads, 0, p->stream>>>(p->nnz_row, m, partial, c_row_ptr);
+    }
+    {
+      KernelScope ks(p, "num_classify");
+      k_num_classify<<<(unsigned)((m + 255) / 256), 256, 0, p->stream>>>(p->nnz_row, p->rbin, p->flop, m, p->caps,
+                                                                         p->gcap_nnz, p->rbin2, p->dc);
+      k_bin_offsets<<<1, 32, 0, p->stream>>>(p->dc->num_count, kNumNumBins, p->d_num_off);
+    }
+    const int64_t nbm = p->sym_count[kSymBitmapBin] + p->sym_count[kSymBitmapMidBin];
+    if (nbm > 0) {
+      KernelScope ks(p, "bm_items_count");
+      BmCaps caps{{p->bm_cap[0], p->bm_cap[1], p->bm_cap[2]}, {0, 0, 0}};
+      k_bm_items_count<<<(unsigned)((nbm + 255) / 256), 256, 0, p->stream>>>(
+          p->perm + p->sym_off[kSymBitmapBin], nbm, p->nnz_row, p->flop, caps, p->dc);
     }
     e = cudaGetLastError();
   }
+  return e;
+}
+
+// Rows grouped by numeric bin (after enqueue_symbolic).
+cudaError_t enqueue_num_scatter(spgemm_plan_s *p) {
+  if (p->m == 0) return cudaSuccess;
+  KernelScope ks(p, "bin_rows_num");
+  k_bin_scatter<<<(unsigned)((p->m + 255) / 256), 256, 0, p->stream>>>(p->rbin2, p->m, p->d_num_off,
+                                                                      p->dc->num_cursor, p->perm2, kNumNumBins);
+  return cudaGetLastError();
+}
+
+// Rows grouped by symbolic bin (after enqueue_flop).
+cudaError_t enqueue_sym_scatter(spgemm_plan_s *p) {
+  if (p->m == 0) return cudaSuccess;
+  KernelScope ks(p, "bin_rows_sym");
+  k_bin_scatter<<<(unsigned)((p->m + 255) / 256), 256, 0, p->stream>>>(p->rbin, p->m, p->d_sym_off, p->dc->sym_cursor,
+                                                                      p->perm, kNumSymBins);
+  return cudaGetLastError();
+}
+
+}  // namespace sg
+
+extern "C" {
+
+int spgemm_plan_create_tuned(spgemm_plan_t *out, const spgemm_csr *A, const spgemm_csr *B, int dtype,
+                             unsigned flags, void *stream, const spgemm_tuning *tuning) {
+  NvtxRange nvtx("spgemm_plan_create");
+  if (!out) return SPGEMM_ERR_INVALID_ARGUMENT;
+  *out = nullptr;
+  spgemm_plan_s *p = nullptr;
+  {
+    const int rc0 = plan_init(&p, A, B, dtype, flags, (cudaStream_t)stream, tuning, false);
+    if (rc0 != SPGEMM_OK) return rc0;
+  }
+  const int64_t m = p->m;
+  int rc = SPGEMM_OK;
+  cudaError_t e = enqueue_flop(p);
   if (e != cudaSuccess) rc = fail_cuda(e, "row flop pass");
   if (rc == SPGEMM_OK) rc = read_counters(p);
   if (rc == SPGEMM_OK) {
@@ -765,7 +1023,10 @@ int spgemm_plan_create_tuned(spgemm_plan_t *out, const spgemm_csr *A, const spge
     p->max_flop = (int64_t)p->hc->max_flop;
     // lanes per stored a_ik: the mean length of the B rows the products come
     // from (flop / nnz(A)), so that long rows get whole warps
-    const double per_entry = p->nnz_a > 0 ? (double)p->total_flop / (double)p->nnz_a : 0.0;
+    p->nnz_a_used = (int64_t)p->hc->nnz_a_used;
+    const bool compact = m > 0 && p->total_flop > 0 && 2 * p->nnz_a_used < p->nnz_a;
+    const int64_t walked = compact ? p->nnz_a_used : p->nnz_a;
+    const double per_entry = walked > 0 ? (double)p->total_flop / (double)walked : 0.0;
     p->G = per_entry >= 24 ? 32 : per_entry >= 12 ? 16 : per_entry >= 6 ? 8 : 4;
     if (p->tune_G) p->G = p->tune_G;
     p->sym_off[0] = 0;
@@ -774,8 +1035,15 @@ int spgemm_plan_create_tuned(spgemm_plan_t *out, const spgemm_csr *A, const spge
       p->sym_count[b] = (int64_t)p->hc->sym_count[b];
       p->sym_off[b + 1] = p->sym_off[b] + p->sym_count[b];
     }
+    if (compact) rc = compact_a(p);
     const int64_t nbm = p->sym_count[kSymBitmapBin] + p->sym_count[kSymBitmapMidBin];
-    if (nbm > 0) {
+    p->n_long = p->long_min > 0 ? std::min<int64_t>((int64_t)p->hc->n_long, p->long_cap) : 0;
+    p->long_tot = p->long_min > 0 ? (int64_t)p->hc->long_tot : 0;
+    if (rc == SPGEMM_OK && nbm > 0 && p->n_long > 0) {
+      e = long_rows_build(p);
+      if (e != cudaSuccess) rc = fail_cuda(e, "long rows of B");
+    }
+    if (rc == SPGEMM_OK && nbm > 0) {
       p->bitmaps_bytes = (size_t)nbm * p->bm_words * 4;
       e = cudaMallocAsync((void **)&p->bitmaps, p->bitmaps_bytes, p->stream);
       if (e != cudaSuccess) {
@@ -788,14 +1056,7 @@ int spgemm_plan_create_tuned(spgemm_plan_t *out, const spgemm_csr *A, const spge
       rc = alloc_gtab(p, std::max<int64_t>(64, pow2_above((int64_t)p->hc->max_bound_global)), 4,
                       p->sym_count[kSymGlobalBin]);
     if (rc == SPGEMM_OK && m > 0) {
-      Offsets o{};
-      for (int b = 0; b < kNumSymBins; ++b) o.v[b] = p->sym_off[b];
-      {
-        KernelScope ks(p, "bin_rows_sym");
-        k_bin_scatter<<<(unsigned)((m + 255) / 256), 256, 0, p->stream>>>(p->rbin, m, o, p->dc->sym_cursor,
-                                                                          p->perm, kNumSymBins);
-      }
-      e = cudaGetLastError();
+      e = enqueue_sym_scatter(p);
       if (e != cudaSuccess) rc = fail_cuda(e, "row binning");
     }
   }
@@ -815,43 +1076,9 @@ int spgemm_symbolic(spgemm_plan_t p, int32_t *c_row_ptr, int64_t *nnz_c) {
   if (!p || !c_row_ptr || !nnz_c) return SPGEMM_ERR_INVALID_ARGUMENT;
   if (p->state != 0) return SPGEMM_ERR_BAD_STATE;
   g_last_error.clear();
-  cudaError_t e = launch_symbolic(p);
-  if (e != cudaSuccess) return fail_cuda(e, "symbolic kernels");
+  cudaError_t e = enqueue_symbolic(p, c_row_ptr);
+  if (e != cudaSuccess) return fail_cuda(e, "symbolic phase");
   const int64_t m = p->m;
-  if (m == 0) {
-    e = cudaMemsetAsync(c_row_ptr, 0, sizeof(int32_t), p->stream);
-    if (e != cudaSuccess) return fail_cuda(e, "row_ptr");
-  } else {
-    const int64_t nblk = (m + kScanTile - 1) / kScanTile;
-    // partial[] is the last segment of the fixed workspace, after perm2
-    long long *partial = (long long *)((char *)p->perm2 + align_up((size_t)m * 4, 256));
-    {
-      KernelScope ks(p, "scan_reduce");
-      k_scan_reduce<<<(unsigned)nblk, kScanThreads, 0, p->stream>>>(p->nnz_row, m, partial);
-    }
-    {
-      KernelScope ks(p, "scan_spine");
-      k_scan_spine<<<1, kScanThreads, 0, p->stream>>>(partial, nblk, p->max_nnz_c, p->dc);
-    }
-    {
-      KernelScope ks(p, "scan_apply");
-      k_scan_apply<<<(unsigned)nblk, kScanThreads, 0, p->stream>>>(p->nnz_row, m, partial, c_row_ptr);
-    }
-    {
-      KernelScope ks(p, "num_classify");
-      k_num_classify<<<(unsigned)((m + 255) / 256), 256, 0, p->stream>>>(p->nnz_row, p->rbin, p->flop, m, p->rbin2,
-                                                                         p->dc);
-    }
-    const int64_t nbm = p->sym_count[kSymBitmapBin] + p->sym_count[kSymBitmapMidBin];
-    if (nbm > 0) {
-      KernelScope ks(p, "bm_items_count");
-      BmCaps caps{{p->bm_cap[0], p->bm_cap[1], p->bm_cap[2]}, {0, 0, 0}};
-      k_bm_items_count<<<(unsigned)((nbm + 255) / 256), 256, 0, p->stream>>>(
-          p->perm + p->sym_off[kSymBitmapBin], nbm, p->nnz_row, p->flop, caps, p->dc);
-    }
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return fail_cuda(e, "row_ptr scan");
-  }
   int rc = read_counters(p);
   if (rc != SPGEMM_OK) return rc;
   p->nnz_c = m > 0 ? (int64_t)p->hc->nnz_c : 0;
@@ -899,14 +1126,8 @@ static int numeric_prepare(spgemm_plan_t p) {
     const int rc = alloc_gtab(p, slots, 4 + value_size(p->dtype), p->num_count[kNumGlobalBin]);
     if (rc != SPGEMM_OK) return rc;
   }
-  Offsets o{};
-  for (int b = 0; b < kNumNumBins; ++b) o.v[b] = p->num_off[b];
-  {
-    KernelScope ks(p, "bin_rows_num");
-    k_bin_scatter<<<(unsigned)((m + 255) / 256), 256, 0, p->stream>>>(p->rbin2, m, o, p->dc->num_cursor, p->perm2,
-                                                                      kNumNumBins);
-  }
-  e = cudaGetLastError();
+  (void)m;
+  e = enqueue_num_scatter(p);
   if (e != cudaSuccess) return fail_cuda(e, "numeric binning");
   return SPGEMM_OK;
 }
@@ -1035,7 +1256,7 @@ int spgemm_plan_kernel_times(spgemm_plan_t p, spgemm_kernel_time *out, int max_e
 int spgemm_plan_workspace_bytes(spgemm_plan_t p, size_t *bytes) {
   if (!p || !bytes) return SPGEMM_ERR_INVALID_ARGUMENT;
   *bytes = p->ws_fixed_bytes + (p->bitmaps ? p->bitmaps_bytes : 0) + (p->bm_items ? p->bm_items_bytes : 0) +
-           (p->gtab ? p->gtab_bytes : 0);
+           (p->gtab ? p->gtab_bytes : 0) + (p->long_ws ? p->long_ws_bytes : 0) + (p->acmp_ws ? p->acmp_bytes : 0);
   return SPGEMM_OK;
 }
 
@@ -1075,6 +1296,9 @@ int spgemm_plan_stats(spgemm_plan_t p, spgemm_stats *s) {
   s->workspace_bytes = (int64_t)ws;
   s->kernel_launches = p->launches;
   s->state = p->state;
+  s->nnz_a_walked = p->a_compact ? p->nnz_a_used : p->nnz_a;
+  s->long_rows = p->long_ready ? p->n_long : 0;
+  s->long_entries = p->long_ready ? p->long_tot : 0;
   return rc;
 }
 
@@ -1134,3 +1358,62 @@ int spgemm(const spgemm_csr *A, const spgemm_csr *B, int dtype, unsigned flags, 
 }
 
 }  // extern "C"
+
+namespace sg {
+
+int plan_create_graph(spgemm_plan_s **out, const spgemm_csr *A, const spgemm_csr *B, int dtype, unsigned flags,
+                      cudaStream_t stream, const spgemm_tuning *tuning, const GraphCaps &gc) {
+  if (!out) return SPGEMM_ERR_INVALID_ARGUMENT;
+  *out = nullptr;
+  if (flags & (SPGEMM_TIMING | SPGEMM_COUNT_PROBES)) {
+    set_last_error("a batch graph replays captured kernels: SPGEMM_TIMING and SPGEMM_COUNT_PROBES do not apply");
+    return SPGEMM_ERR_INVALID_ARGUMENT;
+  }
+  if (gc.nnz_cap < 0 || gc.nnz_cap > INT32_MAX) return SPGEMM_ERR_INVALID_ARGUMENT;
+  spgemm_plan_s *p = nullptr;
+  int rc = plan_init(&p, A, B, dtype, flags, stream, tuning, true);
+  if (rc != SPGEMM_OK) return rc;
+  p->total_flop = gc.total_flop;
+  p->max_flop = gc.max_flop;
+  const double per_entry = p->nnz_a > 0 ? (double)gc.total_flop / (double)p->nnz_a : 0.0;
+  p->G = per_entry >= 24 ? 32 : per_entry >= 12 ? 16 : per_entry >= 6 ? 8 : 4;
+  if (p->tune_G) p->G = p->tune_G;
+  p->max_nnz_c = gc.nnz_cap;
+  if (gc.span_cols > 0) p->span_cols = gc.span_cols;
+  // global tables, for the largest heavy row the planning pass saw
+  const int64_t sym_slots = gc.max_bound > kBlockSymMax ? std::max<int64_t>(64, pow2_above(gc.max_bound)) : 0;
+  const int64_t num_slots =
+      gc.max_nnz > p->caps.cap[8] ? std::max<int64_t>(64, pow2_above(gc.max_nnz * 4 / 3)) : 0;
+  const int64_t slots = std::max(sym_slots, num_slots);
+  p->gcap_bound = p->gcap_nnz = slots;
+  if (slots > 0) rc = alloc_gtab(p, slots, 4 + value_size(dtype), 2 * (int64_t)sm_count());
+  if (rc == SPGEMM_OK && use_side_streams(p)) {
+    const cudaError_t e = acquire_side(p);  // before any capture
+    if (e != cudaSuccess) rc = fail_cuda(e, "side streams");
+  }
+  if (rc != SPGEMM_OK) {
+    plan_free(p);
+    return rc;
+  }
+  p->state = 1;
+  *out = p;
+  return SPGEMM_OK;
+}
+
+cudaError_t plan_enqueue_graph(spgemm_plan_s *p, int32_t *c_rp, int32_t *c_ci, void *c_v) {
+  cudaError_t e = enqueue_flop(p);
+  if (e == cudaSuccess) e = enqueue_sym_scatter(p);
+  if (e == cudaSuccess) e = enqueue_symbolic(p, c_rp);
+  if (e == cudaSuccess) e = enqueue_num_scatter(p);
+  if (e == cudaSuccess && p->m > 0) e = numeric_launch(p, c_rp, c_ci, c_v);
+  return e;
+}
+
+void plan_free(spgemm_plan_s *p) {
+  if (!p) return;
+  free_ws(p);
+  delete p->hc;
+  delete p;
+}
+
+}  // namespace sg

@@ -70,25 +70,28 @@ __device__ __forceinline__ int insert_key(int32_t *tab, uint32_t mask, int32_t c
 
 template <int S>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, 8)
-    k_sym_warp(Args a, const int32_t *__restrict__ rows, int64_t nrows, int32_t *__restrict__ nnz_row) {
+    k_sym_warp(Args a, BinRows br, int32_t *__restrict__ nnz_row) {
   extern __shared__ int32_t sm_sym_warp[];
   __shared__ Entry<int32_t> s_ent[kWarpsPerBlock][32];
   __shared__ int s_next[kWarpsPerBlock];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
-  if (w >= nrows) return;  // whole warp leaves; no block barrier below
+  const long long o0 = br.off[br.bin], nrows = br.off[br.bin + 1] - o0;
   int32_t *tab = sm_sym_warp + warp * S;
-  for (int s = lane; s < S; s += 32) tab[s] = kEmpty;
-  __syncwarp();
-  const int32_t i = rows[w];
   const int G = a.G;
-  int cnt = 0;
   Stage<int32_t> st{s_ent[warp], &s_next[warp], nullptr};
-  warp_row_products<kU, false, int32_t>(a.arp[i], a.arp[i + 1], G, a.aci, (const int32_t *)nullptr, a.brp, a.bci,
-                                        (const int32_t *)nullptr, (int32_t)a.k, a.err, st,
-                                        [&](int32_t c, int32_t, int32_t) { cnt += insert_key<false>(tab, S - 1, c, a.err, a.probe, a.probe_ctr); });
-  cnt = warp_sum(cnt);
-  if (lane == 0) nnz_row[i] = cnt;
+  // one warp per row (no block barrier below)
+  for (int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + warp; w < nrows; w += (int64_t)gridDim.x * kWarpsPerBlock) {
+    for (int s = lane; s < S; s += 32) tab[s] = kEmpty;
+    __syncwarp();
+    const int32_t i = br.perm[o0 + w];
+    int cnt = 0;
+    warp_row_products<kU, false, int32_t>(a.arp[i], a.arp[i + 1], G, a.aci, (const int32_t *)nullptr, a.brp, a.bci,
+                                          (const int32_t *)nullptr, (int32_t)a.k, a.err, st,
+                                          [&](int32_t c, int32_t, int32_t) { cnt += insert_key<false>(tab, S - 1, c, a.err, a.probe, a.probe_ctr); });
+    cnt = warp_sum(cnt);
+    if (lane == 0) nnz_row[i] = cnt;
+    __syncwarp();
+  }
 }
 
 // Threads of the block bins (as kSymBins) and blocks per SM: a key table of
@@ -98,38 +101,46 @@ template <int S> constexpr int sym_block_min_blocks() { return S <= 2048 ? 8 : S
 
 template <int S>
 __global__ void __launch_bounds__(sym_block_threads<S>(), sym_block_min_blocks<S>())
-    k_sym_block(Args a, const int32_t *__restrict__ rows, int32_t *__restrict__ nnz_row) {
+    k_sym_block(Args a, BinRows br, int32_t *__restrict__ nnz_row) {
   extern __shared__ int32_t sm_sym_block[];
   __shared__ int red[33];
   __shared__ Entry<int32_t> s_ent[kStageN];
   __shared__ long long s_wsum[8];
   __shared__ int s_next;
   int32_t *tab = sm_sym_block;
-  for (int s = threadIdx.x; s < S; s += blockDim.x) tab[s] = kEmpty;
-  __syncthreads();
-  const int32_t i = rows[blockIdx.x];
+  const long long o0 = br.off[br.bin], nrows = br.off[br.bin + 1] - o0;
   const int G = a.G;
-  int cnt = 0;
-  block_row_products<kU, false, int32_t>(a.arp[i], a.arp[i + 1], G, a.aci, (const int32_t *)nullptr,
-                                         a.brp, a.bci, (const int32_t *)nullptr, (int32_t)a.k, a.err,
-                                         Stage<int32_t>{s_ent, &s_next, s_wsum},
-                                       [&](int32_t c, int32_t, int32_t) { cnt += insert_key<false>(tab, S - 1, c, a.err, a.probe, a.probe_ctr); });
-  cnt = block_sum(cnt, red);
-  if (threadIdx.x == 0) nnz_row[i] = cnt;
+  for (int64_t b = blockIdx.x; b < nrows; b += gridDim.x) {  // one block per row
+    for (int s = threadIdx.x; s < S; s += blockDim.x) tab[s] = kEmpty;
+    __syncthreads();
+    const int32_t i = br.perm[o0 + b];
+    int cnt = 0;
+    block_row_products<kU, false, int32_t>(a.arp[i], a.arp[i + 1], G, a.aci, (const int32_t *)nullptr,
+                                           a.brp, a.bci, (const int32_t *)nullptr, (int32_t)a.k, a.err,
+                                           Stage<int32_t>{s_ent, &s_next, s_wsum},
+                                           [&](int32_t c, int32_t, int32_t) { cnt += insert_key<false>(tab, S - 1, c, a.err, a.probe, a.probe_ctr); });
+    cnt = block_sum(cnt, red);  // ends with a barrier: the table may be cleared again
+    if (threadIdx.x == 0) nnz_row[i] = cnt;
+  }
 }
 
 // Heavy rows with a bitmap over the columns of B.  words = ceil(k / 32).
+// A stored a_ik whose row of B is a long row (lr.map) sets that row's
+// columns by ORing its saved bitmap, word by word, into the row's bitmap
+// (thread t owns words t, t + NT, ...), instead of one atomic per entry.
 template <int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
     k_sym_bitmap(Args a, const int32_t *__restrict__ rows, const int4 *__restrict__ items,
                  int32_t *__restrict__ nnz_row, uint32_t *__restrict__ bitmaps, int words,
-                 unsigned *__restrict__ tickets) {
+                 unsigned *__restrict__ tickets, LongRows lr) {
   extern __shared__ uint32_t sm_bm[];
   __shared__ int red[33];
   __shared__ Entry<int32_t> s_ent[kStageN];
   __shared__ long long s_wsum[8];
   __shared__ int s_next;
   __shared__ int s_last;
+  __shared__ int s_lidx[kStageN];
+  __shared__ int s_lcnt[kStageN / 32];
   // block b is row b of the bin, or, for split rows, work item b (row t of
   // the bin, part `part` of `parts`)
   int t = blockIdx.x, part = 0, parts = 1;
@@ -145,11 +156,32 @@ __global__ void __launch_bounds__(NT, MINB)
   if (parts > 1) part_range(a, i, part, parts, &j_lo, &j_hi);
   __syncthreads();
   const int G = a.G;
-  block_row_products<kU, false, int32_t>(j_lo, j_hi, G, a.aci, (const int32_t *)nullptr,
-                                         a.brp, a.bci, (const int32_t *)nullptr, (int32_t)a.k, a.err,
-                                         Stage<int32_t>{s_ent, &s_next, s_wsum},
-                                       [&](int32_t c, int32_t, int32_t) { atomicOr(sm_bm + (c >> 5), 1u << (c & 31)); });
-  __syncthreads();
+  block_row_products_long<kU, false, true, int32_t>(
+      j_lo, j_hi, G, a.aci, (const int32_t *)nullptr, a.brp, a.bci, (const int32_t *)nullptr, (int32_t)a.k, a.err,
+      lr.map, Stage<int32_t>{s_ent, &s_next, s_wsum, s_lidx, s_lcnt},
+      [&](const int32_t (&c)[kU], const int32_t (&)[kU], const int32_t (&)[kU], const bool (&ok)[kU]) {
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+          if (ok[u]) atomicOr(sm_bm + (c[u] >> 5), 1u << (c[u] & 31));
+      },
+      [&](int nlong, const int *lidx) {
+        // this thread's words, 4 at a time: OR of the round's long rows
+        for (int w0 = threadIdx.x; w0 < words; w0 += 4 * NT) {
+          uint32_t x[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) x[q] = 0u;
+#pragma unroll 8
+          for (int l = 0; l < nlong; ++l) {
+            const uint32_t *bw = lr.bits + (size_t)s_ent[lidx[l]].off * words;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (w0 + q * NT < words) x[q] |= __ldg(bw + w0 + q * NT);
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (w0 + q * NT < words && x[q]) sm_bm[w0 + q * NT] |= x[q];
+        }
+      });
   uint32_t *out = bitmaps + (size_t)t * words;
   if (parts == 1) {
     int cnt = 0;
@@ -196,8 +228,7 @@ __global__ void __launch_bounds__(256)
 // Heavy rows, hash table in global memory: block b owns tables[b*S .. b*S+S)
 // and walks rows b, b+gridDim.x, ...
 __global__ void __launch_bounds__(1024, 1)
-    k_sym_global(Args a, const int32_t *__restrict__ rows, int64_t nrows, int32_t *__restrict__ nnz_row,
-                 int32_t *__restrict__ tables, int64_t S) {
+    k_sym_global(Args a, BinRows br, int32_t *__restrict__ nnz_row, int32_t *__restrict__ tables, int64_t S) {
   __shared__ int red[33];
   __shared__ Entry<int32_t> s_ent[kStageN];
   __shared__ long long s_wsum[8];
@@ -205,10 +236,11 @@ __global__ void __launch_bounds__(1024, 1)
   int32_t *tab = tables + (size_t)blockIdx.x * S;
   const uint32_t mask = (uint32_t)(S - 1);
   const int G = a.G;
+  const long long o0 = br.off[br.bin], nrows = br.off[br.bin + 1] - o0;
   for (int64_t r = blockIdx.x; r < nrows; r += gridDim.x) {
     for (int64_t s = threadIdx.x; s < S; s += blockDim.x) tab[s] = kEmpty;
     __syncthreads();
-    const int32_t i = rows[r];
+    const int32_t i = br.perm[o0 + r];
     int cnt = 0;
     block_row_products<kU, false, int32_t>(a.arp[i], a.arp[i + 1], G, a.aci, (const int32_t *)nullptr,
                                          a.brp, a.bci, (const int32_t *)nullptr, (int32_t)a.k, a.err,
@@ -228,34 +260,35 @@ static cudaError_t prep(K kernel, size_t smem) {
 }
 
 template <int S>
-static cudaError_t sym_warp(spgemm_plan_s *p, cudaStream_t st, const Args &a, const int32_t *rows, int64_t n) {
+static cudaError_t sym_warp(spgemm_plan_s *p, cudaStream_t st, const Args &a, BinRows br, int64_t n) {
   const size_t smem = (size_t)kWarpsPerBlock * S * sizeof(int32_t);
   cudaError_t e = prep(k_sym_warp<S>, smem);
   if (e != cudaSuccess) return e;
-  const int64_t blocks = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  const int64_t blocks = launch_blocks(p, reinterpret_cast<const void *>(k_sym_warp<S>), kWarpsPerBlock * 32, smem,
+                                       (n + kWarpsPerBlock - 1) / kWarpsPerBlock);
   {
     KernelScope ks(p, "sym_warp_" + std::to_string(S), st);
-    k_sym_warp<S><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, st>>>(a, rows, n, p->nnz_row);
+    k_sym_warp<S><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, st>>>(a, br, p->nnz_row);
   }
   return cudaGetLastError();
 }
 
 template <int S>
-static cudaError_t sym_block(spgemm_plan_s *p, cudaStream_t st, const Args &a, const int32_t *rows, int64_t n,
-                             int threads) {
+static cudaError_t sym_block(spgemm_plan_s *p, cudaStream_t st, const Args &a, BinRows br, int64_t n, int threads) {
   const size_t smem = (size_t)S * sizeof(int32_t);
   cudaError_t e = prep(k_sym_block<S>, smem);
   if (e != cudaSuccess) return e;
+  const int64_t blocks = launch_blocks(p, reinterpret_cast<const void *>(k_sym_block<S>), threads, smem, n);
   {
     KernelScope ks(p, "sym_block_" + std::to_string(S), st);
-    k_sym_block<S><<<(unsigned)n, threads, smem, st>>>(a, rows, p->nnz_row);
+    k_sym_block<S><<<(unsigned)blocks, threads, smem, st>>>(a, br, p->nnz_row);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_symbolic(spgemm_plan_s *p) {
-  Args a{p->m, p->n, p->k, p->arp, p->aci, p->brp, p->bci, p->av, p->bv, p->G, &p->dc->err,
-         probe_mode(p->flags), (p->flags & SPGEMM_COUNT_PROBES) ? &p->dc->probe_stats[0][0] : nullptr};
+  const Args a = phase_args(p, &p->dc->err, probe_mode(p->flags),
+                            (p->flags & SPGEMM_COUNT_PROBES) ? &p->dc->probe_stats[0][0] : nullptr);
   // heavy bins first, each bin on the next side stream
   static const int order[kNumSymBins] = {kSymBitmapBin, kSymBitmapMidBin, kSymGlobalBin, 9, 8, 7, 6, 5, 4, 3, 2, 1, 0};
   const bool concurrent = use_side_streams(p);
@@ -289,22 +322,24 @@ cudaError_t launch_symbolic(spgemm_plan_s *p) {
   int launched = 0;
   for (int o = 0; o < kNumSymBins && e == cudaSuccess; ++o) {
     const int b = order[o];
-    const int64_t n = p->sym_count[b];
+    // a graph-mode plan launches every bin it may need (counts unknown on the host)
+    const int64_t n = p->ddrive ? ddrive_bin_rows(p, b, true) : p->sym_count[b];
     if (n == 0) continue;
     const int32_t *rows = p->perm + p->sym_off[b];
+    const BinRows br{p->perm, p->d_sym_off, b};
     const BinCfg &c = kSymBins[b];
     cudaStream_t st = concurrent ? bin_stream(p, launched++) : p->stream;
     switch (b) {
-      case 0: e = sym_warp<64>(p, st, a, rows, n); break;
-      case 1: e = sym_warp<128>(p, st, a, rows, n); break;
-      case 2: e = sym_warp<256>(p, st, a, rows, n); break;
-      case 3: e = sym_warp<512>(p, st, a, rows, n); break;
-      case 4: e = sym_warp<1024>(p, st, a, rows, n); break;
-      case 5: e = sym_block<2048>(p, st, a, rows, n, c.threads); break;
-      case 6: e = sym_block<4096>(p, st, a, rows, n, c.threads); break;
-      case 7: e = sym_block<8192>(p, st, a, rows, n, c.threads); break;
-      case 8: e = sym_block<16384>(p, st, a, rows, n, c.threads); break;
-      case 9: e = sym_block<32768>(p, st, a, rows, n, c.threads); break;
+      case 0: e = sym_warp<64>(p, st, a, br, n); break;
+      case 1: e = sym_warp<128>(p, st, a, br, n); break;
+      case 2: e = sym_warp<256>(p, st, a, br, n); break;
+      case 3: e = sym_warp<512>(p, st, a, br, n); break;
+      case 4: e = sym_warp<1024>(p, st, a, br, n); break;
+      case 5: e = sym_block<2048>(p, st, a, br, n, c.threads); break;
+      case 6: e = sym_block<4096>(p, st, a, br, n, c.threads); break;
+      case 7: e = sym_block<8192>(p, st, a, br, n, c.threads); break;
+      case 8: e = sym_block<16384>(p, st, a, br, n, c.threads); break;
+      case 9: e = sym_block<32768>(p, st, a, br, n, c.threads); break;
       case kSymBitmapBin:
       case kSymBitmapMidBin: {
         // bitmaps of both bins are stored in perm order from the first bitmap bin on
@@ -320,7 +355,8 @@ cudaError_t launch_symbolic(spgemm_plan_s *p) {
           uint32_t *bm = p->bitmaps + (size_t)(p->sym_off[b] - p->sym_off[kSymBitmapBin]) * p->bm_words;
           const bool split = b == kSymBitmapBin && p->n_sym_items > 0;
           kern<<<(unsigned)(split ? p->n_sym_items : n), c.threads, smem, st>>>(
-              a, rows, split ? p->sym_items : nullptr, p->nnz_row, bm, p->bm_words, split ? p->sym_tickets : nullptr);
+              a, rows, split ? p->sym_items : nullptr, p->nnz_row, bm, p->bm_words, split ? p->sym_tickets : nullptr,
+              long_rows(p));
         }
         e = cudaGetLastError();
         break;
@@ -328,8 +364,8 @@ cudaError_t launch_symbolic(spgemm_plan_s *p) {
       case kSymGlobalBin: {
         {
           KernelScope ks(p, "sym_global", st);
-          k_sym_global<<<(unsigned)p->gtab_blocks, c.threads, 0, st>>>(a, rows, n, p->nnz_row,
-                                                                              (int32_t *)p->gtab, p->gtab_slots);
+          k_sym_global<<<(unsigned)p->gtab_blocks, c.threads, 0, st>>>(a, br, p->nnz_row, (int32_t *)p->gtab,
+                                                                      p->gtab_slots);
         }
         e = cudaGetLastError();
         break;

@@ -57,6 +57,26 @@ def test_struct_layout_matches_c(tmp_path):
                    S.workspace_bytes.offset, S.num_bin_flop.offset]
 
 
+def test_tuning_layout_matches_c(tmp_path):
+    from paper_1804_01698_gb300 import binding
+    src = tmp_path / "tuning.c"
+    fields = [name for name, _ in binding.Tuning._fields_]
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "spgemm.h"\nint main(void){printf("%zu'
+                   + " %zu" * len(fields) + '\\n", sizeof(spgemm_tuning)'
+                   + "".join(f", offsetof(spgemm_tuning, {f})" for f in fields) + "); return 0;}\n")
+    exe = tmp_path / "tuning"
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    got = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()))
+    T = binding.Tuning
+    assert got == [ctypes.sizeof(T)] + [getattr(T, f).offset for f in fields]
+    S = binding.Stats
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "spgemm.h"\nint main(void){printf("%zu %zu\\n",'
+                   ' sizeof(spgemm_stats), offsetof(spgemm_stats, long_entries)); return 0;}\n')
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    got = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()))
+    assert got == [ctypes.sizeof(S), S.long_entries.offset]
+
+
 def test_status_strings(lib):
     assert lib.spgemm_status_string(0) == b"ok"
     assert b"overflow" in lib.spgemm_status_string(-4)

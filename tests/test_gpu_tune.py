@@ -16,7 +16,9 @@ pytestmark = pytest.mark.gpu
 
 @pytest.mark.parametrize("tuning", [
     {"lanes_per_entry": 4}, {"lanes_per_entry": 32}, {"bitmap_min_bound": 256}, {"bitmap_min_bound": 2048},
-    {"bitmap_min_bound": -1}, {"lanes_per_entry": 8, "bitmap_min_bound": 100000}])
+    {"bitmap_min_bound": -1}, {"lanes_per_entry": 8, "bitmap_min_bound": 100000}, {"long_row_min": 1},
+    {"long_row_min": -1}, {"long_row_min": 32, "bitmap_min_bound": 256}, {"warp_load_pct": 75, "block_load_pct": 90},
+    {"warp_load_pct": 25, "block_load_pct": 50}])
 @pytest.mark.parametrize("sorted_output", [True, False])
 def test_every_tuning_gives_the_same_product(tuning, sorted_output):
     from paper_1804_01698_gb300 import binding as sg
@@ -35,7 +37,9 @@ def test_every_tuning_gives_the_same_product(tuning, sorted_output):
     assert_matches_oracle(C, A, A, sorted_output)
 
 
-@pytest.mark.parametrize("bad", [{"lanes_per_entry": 5}, {"lanes_per_entry": 64}, {"bitmap_min_bound": -2}])
+@pytest.mark.parametrize("bad", [{"lanes_per_entry": 5}, {"lanes_per_entry": 64}, {"bitmap_min_bound": -2},
+                                 {"long_row_min": -2}, {"warp_load_pct": 4}, {"block_load_pct": 96},
+                                 {"warp_load_pct": -1}])
 def test_out_of_range_tuning_is_rejected(bad):
     from paper_1804_01698_gb300 import binding as sg
     dA = sg.to_device(inputs.er_exact(100, 4, seed=112))

@@ -35,5 +35,8 @@ def test_split_defaults_and_tuning_validation():
     assert sg._tuning(None) is None
     t = sg._tuning({})
     assert (t.lanes_per_entry, t.bitmap_min_bound, t.max_nnz_c) == (0, 0, 0)
+    assert (t.long_row_min, t.warp_load_pct, t.block_load_pct) == (0, 0, 0)
+    t = sg._tuning({"long_row_min": 64, "warp_load_pct": 60, "block_load_pct": 80})
+    assert (t.long_row_min, t.warp_load_pct, t.block_load_pct) == (64, 60, 80)
     with pytest.raises(ValueError):
         sg._tuning({"lanes": 8})
