@@ -922,9 +922,9 @@ def main() -> int:
     # same K steps with it; the headline value stays the default plan's
     tuned = None
     if not args.no_variant:
-        from paper_1804_01698_gb300.tune import _split, autotune
+        from paper_1804_01698_gb300.tune import _split, model_autotune
         t0 = time.perf_counter()
-        best, table = autotune(dA, dB, sorted_output, steps=2, stream=stream)
+        best, table, model_meas = model_autotune(dA, dB, sorted_output, top=3, steps=2, stream=stream)
         tune_s = time.perf_counter() - t0
         kw, tuning = _split(best)
         tt = []
@@ -941,8 +941,14 @@ def main() -> int:
             if it > 0:
                 tt.append(e0.elapsed_time(e1))
         tms = sum(tt) / len(tt)
+        default_ms = next(ms for c, _, ms in table if c == {"long_row_min": 0})
         tuned = {"candidate": best, "ms_per_step": tms, "value": 2 * flop / (tms * 1e-3) / 1e9,
-                 "autotune_seconds": tune_s, "candidates": len(table)}
+                 "autotune_seconds": tune_s, "candidates": len(table),
+                 "model": {"kind": "Eq. 2: u[kind] * flop * c + bitmap word cost, calibrated on one default run",
+                           "measured": model_meas,
+                           "table": [{"candidate": c, "predicted_ms": round(pr, 4), "measured_ms": round(ms, 4)}
+                                     for c, pr, ms in table]},
+                 "gain_over_default": default_ms / min(ms for _, _, ms in table)}
 
     variant = None
     if not args.no_variant:

@@ -533,6 +533,38 @@ int plan_group(const spgemm_csr *A, const spgemm_csr *B, int64_t p0, int64_t p1,
   return rc;
 }
 
+// Planning pass of one wave on its packed operands (host-driven, no bitmap
+// rows): the bins' row counts, the largest heavy row, the flop and nnz(C)
+// the graph-mode plan is sized for.  The planning plan is freed.
+int plan_wave(const spgemm_csr *pa, const spgemm_csr *pb, int dtype, unsigned flags, cudaStream_t st,
+              const spgemm_tuning *tuning, GraphCaps *c) {
+  spgemm_tuning t{};
+  if (tuning) t = *tuning;
+  t.bitmap_min_bound = -1;
+  t.long_row_min = -1;
+  t.max_nnz_c = 0;
+  spgemm_plan_t hp = nullptr;
+  int rc = spgemm_plan_create_tuned(&hp, pa, pb, dtype, flags & ~SPGEMM_TIMING, st, &t);
+  if (rc != SPGEMM_OK) return rc;
+  int32_t *rp = nullptr;
+  cudaError_t e = cudaMallocAsync((void **)&rp, (size_t)(pa->nrows + 1) * 4, st);
+  int64_t nnz = 0;
+  if (e != cudaSuccess) rc = SPGEMM_ERR_OUT_OF_MEMORY;
+  if (rc == SPGEMM_OK) rc = spgemm_symbolic(hp, rp, &nnz);
+  if (rc == SPGEMM_OK) {
+    c->total_flop = hp->total_flop;
+    c->max_flop = hp->max_flop;
+    c->max_bound = (int64_t)hp->hc->max_bound_global;
+    c->max_nnz = (int64_t)hp->hc->max_nnz_global;
+    c->nnz_cap = nnz;
+    for (int b = 0; b < sg::kNumSymBins; ++b) c->sym_rows[b] = hp->sym_count[b];
+    for (int b = 0; b < sg::kNumNumBins; ++b) c->num_rows[b] = hp->num_count[b];
+  }
+  if (rp) cudaFreeAsync(rp, st);
+  spgemm_plan_destroy(hp);
+  return rc;
+}
+
 void free_graph(spgemm_bgraph_s *g) {
   if (!g) return;
   if (g->exec) cudaGraphExecDestroy(g->exec);
@@ -693,10 +725,7 @@ int spgemm_bgraph_create(spgemm_bgraph_t *out, int64_t nprod, const spgemm_csr *
         c.total_flop += pl.flop[(size_t)(r - g0)];
         c.span_cols = std::max<int64_t>(c.span_cols, B[r].ncols);
       }
-      c.max_flop = pl.max_flop;
-      c.max_bound = pl.max_bound;
-      c.max_nnz = pl.max_nnz;
-      c.nnz_cap = std::min<int64_t>(INT32_MAX, (int64_t)((double)nnz * (1.0 + pool_slack)) + 1);
+
       waves.push_back({p, q});
       caps.push_back(c);
       p = q;
@@ -714,6 +743,9 @@ int spgemm_bgraph_create(spgemm_bgraph_t *out, int64_t nprod, const spgemm_csr *
     if (rc != SPGEMM_OK) break;
     spgemm_csr pa{gw.b->m, gw.b->bm, gw.b->an, gw.b->arp, gw.b->aci, gw.b->av};
     spgemm_csr pb{gw.b->bm, gw.b->k, gw.b->bn, gw.b->brp, gw.b->bci, gw.b->bv};
+    rc = plan_wave(&pa, &pb, dtype, flags, st, tuning, &caps[w]);
+    if (rc != SPGEMM_OK) break;
+    caps[w].nnz_cap = std::min<int64_t>(INT32_MAX, (int64_t)((double)caps[w].nnz_cap * (1.0 + pool_slack)) + 1);
     rc = sg::plan_create_graph(&gw.plan, &pa, &pb, dtype, flags, st, tuning, caps[w]);
     gw.nnz_cap = caps[w].nnz_cap;
     const size_t o_ci = up256((size_t)(gw.b->m + 1) * 4);

@@ -393,9 +393,9 @@ inline Args phase_args(const spgemm_plan_s *p, uint32_t *err, int probe, unsigne
               c ? (const void *)p->kav : p->av, p->bv, p->G, err, probe, ctr};
 }
 
-// Blocks of a bin launch: `exact` (one per row or per 4 rows) when the host
-// knows the bin's count; in graph mode at most the blocks that stay
-// resident on the GPU at once (the kernels walk their rows grid-stride).
+// Blocks of a bin launch: one per row (or per 4 rows) of the count the host
+// read, or, in graph mode, of the planning pass's count (at least one
+// block: the kernels walk their actual rows grid-stride).
 int64_t launch_blocks(const spgemm_plan_s *p, const void *kernel, int threads, size_t smem, int64_t exact);
 // Graph mode: an upper bound on the rows of bin b (0: the bin never runs).
 int64_t ddrive_bin_rows(const spgemm_plan_s *p, int b, bool symbolic);
@@ -410,6 +410,10 @@ struct GraphCaps {
   int64_t max_nnz;     // largest nnz of a row (global tables above the largest shared table)
   int64_t nnz_cap;     // room for nnz(C)
   int64_t span_cols;   // bound on the column span of a row of C
+  // rows per bin in the planning pass: the launch sizes of the bin kernels
+  // (they walk their actual rows grid-stride, so any count stays correct)
+  int64_t sym_rows[kNumSymBins];
+  int64_t num_rows[kNumNumBins];
 };
 int plan_create_graph(spgemm_plan_s **out, const spgemm_csr *A, const spgemm_csr *B, int dtype, unsigned flags,
                       cudaStream_t stream, const spgemm_tuning *tuning, const GraphCaps &caps);

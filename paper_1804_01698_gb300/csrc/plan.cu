@@ -431,36 +431,21 @@ static int sm_count() {
   return cached[dev];
 }
 
-int64_t launch_blocks(const spgemm_plan_s *p, const void *kernel, int threads, size_t smem, int64_t exact) {
-  if (!p->ddrive) return exact;
-  static std::mutex mu;
-  static std::map<std::pair<const void *, size_t>, int> cache;
-  int per_sm = 0;
-  {
-    std::lock_guard<std::mutex> g(mu);
-    auto it = cache.find({kernel, smem});
-    if (it != cache.end()) per_sm = it->second;
-  }
-  if (per_sm == 0) {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
-      per_sm = 1;
-    std::lock_guard<std::mutex> g(mu);
-    cache[{kernel, smem}] = per_sm;
-  }
-  const int64_t resident = (int64_t)per_sm * sm_count();
-  return std::max<int64_t>(1, std::min<int64_t>(exact, resident));
+int64_t launch_blocks(const spgemm_plan_s *, const void *, int, size_t, int64_t exact) {
+  return std::max<int64_t>(1, exact);
 }
 
 int64_t ddrive_bin_rows(const spgemm_plan_s *p, int b, bool symbolic) {
-  // graph mode has no bitmap rows; the global bin runs only with its tables
+  // graph mode has no bitmap rows; the global bin runs only with its tables;
+  // every other bin runs (one block at least) whatever the planned count
   if (symbolic) {
     if (b == kSymBitmapBin || b == kSymBitmapMidBin) return 0;
-    if (b == kSymGlobalBin) return p->gtab ? p->m : 0;
-    return p->m;
+    if (b == kSymGlobalBin && !p->gtab) return 0;
+    return std::max<int64_t>(1, p->sym_count[b]);
   }
   if (b == kNumBitmapBin || b == kNumBitmapSBin || b == kNumBitmapMBin) return 0;
-  if (b == kNumGlobalBin) return p->gtab ? p->m : 0;
-  return p->m;
+  if (b == kNumGlobalBin && !p->gtab) return 0;
+  return std::max<int64_t>(1, p->num_count[b]);
 }
 
 // Side streams and their fork/join events come from a per-device pool: a
@@ -1380,6 +1365,8 @@ int plan_create_graph(spgemm_plan_s **out, const spgemm_csr *A, const spgemm_csr
   if (p->tune_G) p->G = p->tune_G;
   p->max_nnz_c = gc.nnz_cap;
   if (gc.span_cols > 0) p->span_cols = gc.span_cols;
+  for (int b = 0; b < kNumSymBins; ++b) p->sym_count[b] = gc.sym_rows[b];
+  for (int b = 0; b < kNumNumBins; ++b) p->num_count[b] = gc.num_rows[b];
   // global tables, for the largest heavy row the planning pass saw
   const int64_t sym_slots = gc.max_bound > kBlockSymMax ? std::max<int64_t>(64, pow2_above(gc.max_bound)) : 0;
   const int64_t num_slots =

@@ -61,3 +61,19 @@ def test_autotune_returns_a_candidate():
     mats = [sg.to_device(m) for m in inputs.er_batch(6, seed=114, n_hi=3000)]
     best, table = autotune_batch(mats, mats, True, candidates=cands[:2], steps=2)
     assert best in cands[:2] and len(table) == 2
+
+
+def test_model_seeded_autotune_times_its_best_predictions():
+    from paper_1804_01698_gb300 import binding as sg
+    from paper_1804_01698_gb300.tune import model_autotune
+    dA = sg.to_device(inputs.rmat(12, 16, seed=115))
+    best, table, meas = model_autotune(dA, dA, True, top=2, steps=2)
+    assert meas["c_sym"] >= 1.0 and meas["c_num"] >= 1.0 and 0 < meas["rho"] <= 1.0
+    assert 2 <= len(table) <= 6 and best in [c for c, _, _ in table]
+    assert all(pred > 0 and ms > 0 for _, pred, ms in table)
+    kw, tuning = (lambda t: ({"probe": t.pop("probe", "linear"), "hash": t.pop("hash", "high")}, t))(dict(best))
+    with sg.Plan(dA, dA, True, tuning=tuning, **kw) as p:     # the pick still gives the oracle's product
+        p.symbolic()
+        C = p.numeric()
+    torch.cuda.synchronize()
+    assert_matches_oracle(C, inputs.rmat(12, 16, seed=115), inputs.rmat(12, 16, seed=115), True)
