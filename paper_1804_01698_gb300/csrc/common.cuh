@@ -5,6 +5,7 @@
 
 #include <climits>
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace sg {
@@ -486,9 +487,12 @@ __device__ __forceinline__ void block_row_products(int64_t a0, int64_t a1, int G
     if (keep) st.ent[tid] = Entry<T>{(int)inc, (int)(bs - (inc - len)), av_t};
     __syncthreads();
     const int total = st.ent[n - 1].end;
-    // chunk size: about four chunks per group, between 4 and 32 products per lane
-    long long chunk = ((long long)total + 4LL * ngroups - 1) / (4LL * ngroups);
-    chunk = chunk < 4LL * G ? 4LL * G : chunk > 32LL * G ? 32LL * G : chunk;
+    // chunk size: one chunk per group (every product costs about the same, so
+    // equal shares balance; measured on R-MAT A*A, scale 16, four smaller
+    // chunks per group ran the symbolic bitmap kernels 7-13% slower), at
+    // least 4 products per lane
+    long long chunk = ((long long)total + ngroups - 1) / ngroups;
+    chunk = chunk < 4LL * G ? 4LL * G : chunk;
     chunk = (chunk + G - 1) / G * G;
     const int nchunks = (int)(((long long)total + chunk - 1) / chunk);
     for (;;) {
@@ -516,19 +520,46 @@ __device__ __forceinline__ void process_flat_batch(const Entry<T> *ent, int n, i
                                                    int32_t ncols, uint32_t *err, FB &&fb) {
   if constexpr (!PIPE) {
     // the same without the second set of registers (kernels at 32-40
-    // registers a thread would spill it)
-    process_flat<U, NEED_VAL>(ent, n, p0, p1, G, lig, bci, bv, ncols, err, [&](int32_t c, T a, T b) {
-      int32_t cc[U];
-      T aa[U], bb[U];
+    // registers a thread would spill it): U products loaded, then handed over
+    int p = p0 + lig;
+    if (p >= p1) return;
+    int lo = 0, hi = n - 1;  // first entry e with end[e] > p
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (ent[mid].end > p) hi = mid;
+      else lo = mid + 1;
+    }
+    int e = lo;
+    Entry<T> cur = ent[e];
+    while (p < p1) {
+      int32_t c[U];
+      T au[U], v[U];
       bool ok[U];
-      cc[0] = c;
-      aa[0] = a;
-      bb[0] = b;
-      ok[0] = true;
 #pragma unroll
-      for (int u = 1; u < U; ++u) ok[u] = false, cc[u] = -1, aa[u] = bb[u] = T(0);
-      fb(cc, aa, bb, ok);
-    });
+      for (int u = 0; u < U; ++u) {
+        ok[u] = p < p1;
+        c[u] = -1;
+        au[u] = v[u] = T(0);
+        if (ok[u]) {
+          while (p >= cur.end) cur = ent[++e];
+          const int32_t q = cur.off + p;
+          c[u] = __ldg(bci + q);
+          if (NEED_VAL) {
+            au[u] = cur.a;
+            v[u] = __ldg(bv + q);
+          }
+        }
+        p += G;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (ok[u] && (uint32_t)c[u] >= (uint32_t)ncols) {
+          raise_err(err, kErrCsr);
+          ok[u] = false;
+        }
+      }
+      fb(c, au, v, ok);
+    }
     return;
   }
   int p = p0 + lig;
@@ -586,14 +617,20 @@ __device__ __forceinline__ void process_flat_batch(const Entry<T> *ent, int n, i
   }
 }
 
+// Passed as `flong` below: the caller takes the long entries elsewhere and
+// the loop only leaves them out.
+struct SkipLong {
+  __device__ void operator()(int, const int *) const {}
+};
+
 // Block-wide row loop of the bitmap rows, with long rows of B (lmap[k] >= 0,
 // lmap null: none).  Like block_row_products, except that a staged entry
 // whose row of B is long adds no flat products: its staged record keeps the
 // long-row index in `off` (and a_ik), and after the round's flat products
 // and a barrier every thread calls flong(nlong, lidx), lidx[0..nlong) being
-// the round's long entries in stored order; a barrier follows.  Flat
-// products go to fb (process_flat_batch).  Every thread of the block calls
-// it (blockDim.x >= kStageN).
+// the round's long entries in stored order; a barrier follows (neither with
+// flong = SkipLong).  Flat products go to fb (process_flat_batch).  Every
+// thread of the block calls it (blockDim.x >= kStageN).
 template <int U, bool NEED_VAL, bool PIPE, typename T, typename FB, typename FL>
 __device__ __forceinline__ void block_row_products_long(int64_t a0, int64_t a1, int G,
                                                         const int32_t *__restrict__ aci, const T *__restrict__ av,
@@ -636,13 +673,14 @@ __device__ __forceinline__ void block_row_products_long(int64_t a0, int64_t a1, 
     const int n = __syncthreads_count(keep);
     unsigned lm = 0;
     if (keep) st.ent[tid] = Entry<T>{(int)inc, d < 0 ? (int)(bs - (inc - len)) : d, av_t};
-    if (wid < kStageN / 32) {
+    if (!std::is_same<typename std::decay<FL>::type, SkipLong>::value && wid < kStageN / 32) {
       lm = __ballot_sync(0xffffffffu, keep && d >= 0);
       if (lane == 0) st.lcnt[wid] = __popc(lm);
     }
     __syncthreads();
+    constexpr bool kList = !std::is_same<typename std::decay<FL>::type, SkipLong>::value;
     int nlong = 0;
-    if (lmap) {
+    if (kList && lmap) {
 #pragma unroll
       for (int w = 0; w < kStageN / 32; ++w) {
         if (w == wid && keep && d >= 0) st.lidx[nlong + __popc(lm & ((1u << lane) - 1u))] = tid;
@@ -651,8 +689,8 @@ __device__ __forceinline__ void block_row_products_long(int64_t a0, int64_t a1, 
     }
     const int total = st.ent[n - 1].end;
     if (total > 0) {
-      long long chunk = ((long long)total + 4LL * ngroups - 1) / (4LL * ngroups);
-      chunk = chunk < 4LL * G ? 4LL * G : chunk > 32LL * G ? 32LL * G : chunk;
+      long long chunk = ((long long)total + ngroups - 1) / ngroups;  // as in block_row_products
+      chunk = chunk < 4LL * G ? 4LL * G : chunk;
       chunk = (chunk + G - 1) / G * G;
       const int nchunks = (int)(((long long)total + chunk - 1) / chunk);
       for (;;) {

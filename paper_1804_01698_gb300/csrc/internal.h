@@ -68,6 +68,16 @@ extern const BinCfg kNumBins[kNumNumBins];
 // shared-memory table (3/4 of 32768 keys) use global-memory hash tables.
 constexpr int64_t kBitmapMinBound = 512;
 
+// Launch shapes of the numeric bitmap classes (threads a block, blocks an
+// SM): small, medium, large.  Shared memory per block is sized so that the
+// blocks fit an SM; the registers a thread then gets follow from the shape
+// (small 40, medium 64, large 64).  Measured on R-MAT A*A, scale 16: medium
+// blocks of 512 threads ran 10% faster than 1024 (which spill at 32
+// registers); small blocks of 256 threads 20% slower than 512.
+constexpr int kBmThreadsS = 512, kBmBlocksS = 3;
+constexpr int kBmThreadsM = 512, kBmBlocksM = 2;
+constexpr int kBmThreadsL = 1024;
+
 constexpr int64_t kBitmapMidMax = 24576;
 constexpr int64_t kBlockSymMax = 24576;      // 3/4 of 32768 (global-table inputs)
 constexpr int64_t kBitmapMaxCols = 1 << 18;  // bitmap + prefix <= 64 KB

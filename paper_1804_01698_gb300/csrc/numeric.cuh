@@ -518,17 +518,96 @@ __global__ void __launch_bounds__(256)
 // of smaller ratio the match costs more than the contention it removes.
 constexpr long long kAggregateMinRatio = 32;
 
+// Long pass of a bitmap row, one warp: list[0..nl) holds long entries of
+// the row (long-row index d, A entry j).  The warp adds the products that
+// fall in its own column ranges (kLongRanges / (NT / 32) of them, the same
+// for every long row).  Its work is a sequence of slices, each 32
+// consecutive entries of one long row's part (distinct columns, so distinct
+// ranks); slices are loaded kDepth ahead of the one being added, so the L2
+// latency of the loads overlaps the shared-memory updates, and a __syncwarp
+// after each slice orders the updates of long rows that share a column.  No
+// other warp touches these ranks until the block's next barrier, so the
+// updates are plain loads and stores.
+template <typename T, int NT, typename RF>
+__device__ __forceinline__ void warp_long_pass(const int2 *list, int nl, const T *__restrict__ av,
+                                               const LongRows &lr, T *vals, int span, RF &&rank_of) {
+  constexpr int kNW = NT / 32, kRPW = kLongRanges / kNW, kDepth = 4;
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const LEnt<T> *ent = reinterpret_cast<const LEnt<T> *>(lr.ent);
+  for (int l0 = 0; l0 < nl; l0 += 32) {
+    int s0 = 0, s1 = 0;  // lane l: this warp's part of long entry l0 + l
+    T al = T(0);
+    if (l0 + lane < nl) {
+      const int2 e = list[l0 + lane];
+      const int32_t *o = lr.off + (size_t)e.x * (kLongRanges + 1) + wid * kRPW;
+      s0 = __ldg(o);
+      s1 = __ldg(o + kRPW);
+      al = __ldg(av + e.y);
+    }
+    unsigned pend = __ballot_sync(full, s1 > s0);  // lanes whose part is not empty, not yet started
+    if (pend == 0u) continue;
+    // next slice to load (warp-uniform): the part of lane ij, entries [ib, ie)
+    int ij = __ffs(pend) - 1;
+    pend &= pend - 1u;
+    int ib = __shfl_sync(full, s0, ij), ie = __shfl_sync(full, s1, ij);
+    int jq[kDepth];
+    int32_t cq[kDepth];
+    T vq[kDepth];
+    auto issue = [&](int k) {
+      jq[k] = ij;
+      cq[k] = -1;
+      vq[k] = T(0);
+      if (ij >= 0) {
+        if (ib + lane < ie) load_lent(ent + ib + lane, &cq[k], &vq[k]);
+        ib += 32;
+        if (ib >= ie) {
+          if (pend != 0u) {
+            ij = __ffs(pend) - 1;
+            pend &= pend - 1u;
+            ib = __shfl_sync(full, s0, ij);
+            ie = __shfl_sync(full, s1, ij);
+          } else {
+            ij = -1;
+          }
+        }
+      }
+    };
+#pragma unroll
+    for (int k = 0; k < kDepth; ++k) issue(k);
+    bool more = true;
+    while (more) {
+#pragma unroll
+      for (int k = 0; k < kDepth; ++k) {
+        if (!more) continue;
+        if (jq[k] < 0) {
+          more = false;
+          continue;
+        }
+        const T a = __shfl_sync(full, al, jq[k]);
+        if (cq[k] >= 0) {
+          const int r = rank_of(cq[k]);
+          if ((unsigned)r < (unsigned)span) vals[r] = Val<T>::mad(vals[r], a, vq[k]);
+        }
+        __syncwarp();
+        issue(k);
+      }
+    }
+  }
+}
+
 // Heavy rows with a saved column bitmap.  Item (t, wdw, part, parts): bitmap
 // t of the symbolic bitmap bin (row bm_rows[t]), output ranks
 // [wdw*cap, (wdw+1)*cap), products of the part'th of `parts` ranges of the
 // row's stored a_ik.  A row in one part stores its values; a split row's
 // parts add theirs into C (zeroed by k_bm_zero_split) and part 0 stores
 // the columns.
-// Products of long rows of B (lr.map) are taken from their column-sorted
-// copies: warp w owns its share of the column ranges of every long row,
-// hence the output ranks of those columns, and adds into them with plain
-// shared-memory loads and stores; the other products go through
-// compare-and-swap accumulation (f64) or atomic adds.
+// In the medium and small classes, products of long rows of B (lr.map) are
+// taken first, from their column-sorted copies (warp_long_pass): warp w owns
+// its share of the column ranges of every long row, hence the output ranks
+// of those columns, and adds into them with plain shared-memory loads and
+// stores.  After a barrier the other products (all products, in the large
+// class) go through compare-and-swap accumulation (f64) or atomic adds.
 template <typename T, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
     k_num_bitmap(Args a, const int32_t *__restrict__ bm_rows, const int4 *__restrict__ items,
@@ -541,8 +620,6 @@ __global__ void __launch_bounds__(NT, MINB)
   __shared__ Entry<T> s_ent[kStageN];
   __shared__ long long s_wsum[8];
   __shared__ int s_next;
-  __shared__ int s_lidx[kStageN];
-  __shared__ int s_lcnt[kStageN / 32];
   T *vals = reinterpret_cast<T *>(sm_num_bm);
   // word w of the row's column bitmap and the number of set bits before it
   uint2 *rk = reinterpret_cast<uint2 *>(sm_num_bm + (size_t)cap * sizeof(T));
@@ -555,6 +632,21 @@ __global__ void __launch_bounds__(NT, MINB)
   const int32_t lo = item.y * cap;
   const int32_t hi = min(nnz, lo + cap);
   const uint32_t *src = bitmaps + (size_t)item.x * words;
+  int32_t j_lo = a.arp[i], j_hi = a.arp[i + 1];
+  if (parts > 1) part_range(a, i, part, parts, &j_lo, &j_hi);
+  // A entries listed per round of the long pass: as many (d, j) pairs as
+  // the staging area holds (it is free until the other products start)
+  constexpr int kListCap = (int)(sizeof(Entry<T>) * kStageN / sizeof(int2));
+  constexpr int kListN = kListCap < NT ? kListCap : NT;
+  // Long rows of B in the medium and small classes only.  Measured on R-MAT
+  // A*A, scale 16: the long pass ran the medium class 12% faster and the
+  // large class (one block per SM, whose barriers no other block covers)
+  // 11% slower.
+  const int32_t *lmap = MINB > 1 ? lr.map : nullptr;
+  // the first round's long-row indexes, loaded alongside the bitmap
+  int32_t d_next = -1;
+  if (lmap != nullptr && threadIdx.x < kListN && j_lo + (int32_t)threadIdx.x < j_hi)
+    d_next = __ldg(lmap + __ldg(a.aci + j_lo + threadIdx.x));
   const int per = (words + blockDim.x - 1) / blockDim.x;
   const int w0 = threadIdx.x * per, w1 = min(words, w0 + per);
   int local = 0;
@@ -570,27 +662,43 @@ __global__ void __launch_bounds__(NT, MINB)
     run += __popc(rk[w].x);
   }
   for (int r = threadIdx.x; r < hi - lo; r += blockDim.x) vals[r] = T(0);
-  int32_t j_lo = a.arp[i], j_hi = a.arp[i + 1];
-  if (parts > 1) part_range(a, i, part, parts, &j_lo, &j_hi);
   __syncthreads();
-  const int G = a.G;
   const int span = hi - lo;
   // rank of column c among the row's columns, relative to the window
   auto rank_of = [&](int32_t c) {
     const uint2 word = rk[c >> 5];
     return (int)word.y + __popc(word.x & ((1u << (c & 31)) - 1u)) - lo;
   };
-  // The large class (one block per SM) runs without long rows; the medium
-  // and small classes (more resident warps) take long rows whole.  Measured
-  // on R-MAT A*A, scale 16: long rows made the large class 35% slower and the
-  // medium class 6% faster; loading the next products before the current
-  // ones' updates (as the symbolic bitmap kernels do) made the large class 8%
-  // slower, the others spill it.
-  constexpr bool kLarge = MINB == 1;
+  // Long rows of B first, in rounds of kListN A entries: the block lists the
+  // round's long entries, the warps add their products without a block
+  // barrier (each owns its ranks), and a barrier ends the round.
+  if (lmap != nullptr) {
+    int2 *list = reinterpret_cast<int2 *>(s_ent);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int32_t jb = j_lo; jb < j_hi; jb += kListN) {
+      const int32_t d = d_next;
+      const unsigned m = __ballot_sync(0xffffffffu, d >= 0);
+      if (lane == 0) red[wid] = __popc(m);
+      __syncthreads();
+      int base = 0, nl = 0;
+#pragma unroll
+      for (int v = 0; v < NT / 32; ++v) {
+        const int c = red[v];
+        base += v < wid ? c : 0;
+        nl += c;
+      }
+      if (d >= 0) list[base + __popc(m & ((1u << lane) - 1u))] = make_int2(d, jb + (int32_t)threadIdx.x);
+      __syncthreads();
+      d_next = -1;
+      if (threadIdx.x < kListN && jb + kListN + (int32_t)threadIdx.x < j_hi)
+        d_next = __ldg(lmap + __ldg(a.aci + jb + kListN + threadIdx.x));
+      warp_long_pass<T, NT>(list, nl, (const T *)a.av, lr, vals, span, rank_of);
+      __syncthreads();
+    }
+  }
   block_row_products_long<kUN, true, false, T>(
-      j_lo, j_hi, G, a.aci, (const T *)a.av, a.brp, a.bci, (const T *)a.bv, (int32_t)a.k, a.err,
-      kLarge ? nullptr : lr.map,
-      Stage<T>{s_ent, &s_next, s_wsum, s_lidx, s_lcnt},
+      j_lo, j_hi, a.G, a.aci, (const T *)a.av, a.brp, a.bci, (const T *)a.bv, (int32_t)a.k, a.err, lmap,
+      Stage<T>{s_ent, &s_next, s_wsum},
       [&](const int32_t (&c)[kUN], const T (&av)[kUN], const T (&bv)[kUN], const bool (&ok)[kUN]) {
         int r[kUN];
         bool act[kUN];
@@ -623,80 +731,7 @@ __global__ void __launch_bounds__(NT, MINB)
           if (!Val<T>::acc_shared(vals + r[u], av[u], bv[u])) raise_err(a.err, kErrRetry);
         }
       },
-      [&](int nlong, const int *lidx) {
-        // Warp w owns column ranges [w*kRPW, (w+1)*kRPW) of every long row.
-        // Its work is a sequence of slices: 32 consecutive entries of one long
-        // row's part in those ranges (distinct columns), long rows in stored
-        // order.  Slices are loaded kDepth ahead of the one being added, so the
-        // L2 latency of the loads overlaps the shared-memory updates; a
-        // __syncwarp after each slice orders the updates of long rows that
-        // share a column.
-        constexpr int kNW = NT / 32, kRPW = kLongRanges / kNW, kDepth = 4;
-        const unsigned full = 0xffffffffu;
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        const LEnt<T> *ent = reinterpret_cast<const LEnt<T> *>(lr.ent);
-        for (int l0 = 0; l0 < nlong; l0 += 32) {
-          const int cnt = min(32, nlong - l0);
-          int s0 = 0, s1 = 0;  // lane l: this warp's part of long entry l0 + l
-          T al = T(0);
-          if (lane < cnt) {
-            const Entry<T> st_e = s_ent[lidx[l0 + lane]];
-            const int32_t *o = lr.off + (size_t)st_e.off * (kLongRanges + 1) + wid * kRPW;
-            s0 = __ldg(o);
-            s1 = __ldg(o + kRPW);
-            al = st_e.a;
-          }
-          // next slice to load (warp-uniform): long entry ij, entries [ib, ie)
-          int ij = 0, ib = __shfl_sync(full, s0, 0), ie = __shfl_sync(full, s1, 0);
-          while (ij < cnt && ib >= ie) {
-            ++ij;
-            if (ij < cnt) {
-              ib = __shfl_sync(full, s0, ij);
-              ie = __shfl_sync(full, s1, ij);
-            }
-          }
-          int jq[kDepth];
-          int32_t cq[kDepth];
-          T vq[kDepth];
-          auto issue = [&](int k) {
-            jq[k] = -1;
-            cq[k] = -1;
-            vq[k] = T(0);
-            if (ij < cnt) {
-              jq[k] = ij;
-              if (ib + lane < ie) load_lent(ent + ib + lane, &cq[k], &vq[k]);
-              ib += 32;
-              while (ij < cnt && ib >= ie) {
-                ++ij;
-                if (ij < cnt) {
-                  ib = __shfl_sync(full, s0, ij);
-                  ie = __shfl_sync(full, s1, ij);
-                }
-              }
-            }
-          };
-#pragma unroll
-          for (int k = 0; k < kDepth; ++k) issue(k);
-          bool more = true;
-          while (more) {
-#pragma unroll
-            for (int k = 0; k < kDepth; ++k) {
-              if (!more) continue;
-              if (jq[k] < 0) {
-                more = false;
-                continue;
-              }
-              const T a = __shfl_sync(full, al, jq[k]);
-              if (cq[k] >= 0) {
-                const int r = rank_of(cq[k]);
-                if ((unsigned)r < (unsigned)span) vals[r] = Val<T>::mad(vals[r], a, vq[k]);
-              }
-              __syncwarp();
-              issue(k);
-            }
-          }
-        }
-      });
+      SkipLong{});
   __syncthreads();
   // Store ranks [lo, hi).  vals[] is already in rank order, so the block
   // copies it out with coalesced writes (a split row's parts add theirs).
@@ -924,11 +959,10 @@ cudaError_t launch_numeric_t(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_c
       case kNumBitmapBin: {
         const int cls = b == kNumBitmapSBin ? 0 : b == kNumBitmapMBin ? 1 : 2;
         const size_t smem = (size_t)p->bm_cap[cls] * sizeof(T) + (size_t)p->bm_words * 8;
-        // register budgets that let each class keep its shared-memory occupancy:
-        // small 3 x 512 threads per SM (40 registers), medium 2 x 1024 (32),
-        // large 1 x 1024 (64).  Measured: the spills this costs in the small and
-        // medium forms are outweighed by the extra resident warps.
-        auto kern = cls == 0 ? k_num_bitmap<T, 512, 3> : cls == 1 ? k_num_bitmap<T, 1024, 2> : k_num_bitmap<T, 1024, 1>;
+        // register budgets that let each class keep its shared-memory occupancy
+        auto kern = cls == 0   ? k_num_bitmap<T, kBmThreadsS, kBmBlocksS>
+                    : cls == 1 ? k_num_bitmap<T, kBmThreadsM, kBmBlocksM>
+                               : k_num_bitmap<T, kBmThreadsL, 1>;
         e = prep_num(kern, smem);
         if (e != cudaSuccess) break;
         {

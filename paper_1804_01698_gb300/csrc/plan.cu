@@ -41,9 +41,9 @@ const BinCfg kNumBins[kNumNumBins] = {
     {kWarp, 256, kWarpsPerBlock * 32, 128},    {kWarp, 512, kWarpsPerBlock * 32, 256},
     {kWarp, 1024, kWarpsPerBlock * 32, 512},   {kBlock, 2048, 256, 1536},
     {kBlock, 4096, 512, 3072},                 {kBlock, 8192, 1024, 6144},
-    {kBlock, 16384, 1024, 12288},              {kBitmap, 0, 1024, INT64_MAX},
-    {kGlobal, 0, 1024, INT64_MAX},             {kBitmap, 0, 512, INT64_MAX},
-    {kBitmap, 0, 1024, INT64_MAX}};
+    {kBlock, 16384, 1024, 12288},              {kBitmap, 0, kBmThreadsL, INT64_MAX},
+    {kGlobal, 0, 1024, INT64_MAX},             {kBitmap, 0, kBmThreadsS, INT64_MAX},
+    {kBitmap, 0, kBmThreadsM, INT64_MAX}};
 
 cudaError_t launch_numeric_f64(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_ci, void *c_v);
 cudaError_t launch_numeric_f32(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_ci, void *c_v);
