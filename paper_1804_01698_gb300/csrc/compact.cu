@@ -4,14 +4,14 @@
 // to C (Fig. "RowWise_SpGEMM" loops over the entries of the selected row of
 // B), yet every hash-bin kernel would still stage them and read their row
 // bounds.  The plan therefore hands the phases a copy of A holding only the
-// entries whose row of B is not empty, row by row in stored order.
+// entries whose row of B is not empty, row by row (in stored order, but for
+// the parts of a row that several threads share, which may change places).
 //
-//   k_compact_keep  per entry: kept (its row of B is not empty), read from
-//                   the flop pass's prefix of B-row lengths
-//   k_compact_a     from the exclusive scan of the keep flags: the copy's
-//                   row pointers, columns and the source entry of each
+//   (row pointers: the exclusive scan of the flop pass's per-row counts)
+//   k_compact_a     the copy's columns and the source entry of each, by the
+//                   flop pass's merge-path walk over A's row ends and entries
 //   k_compact_vals  values of the copy, before every numeric phase
-// Every kernel runs one thread per entry or per row, so a hub row of
+// Every kernel runs a fixed number of items per thread, so a hub row of
 // thousands of entries costs no more than as many short rows.
 #include <algorithm>
 
@@ -20,28 +20,31 @@
 
 namespace sg {
 
-// keep[j] = 1 when P[j + 1] > P[j] (P: exclusive prefix of the B-row lengths).
-__global__ void __launch_bounds__(256)
-    k_compact_keep(const long long *__restrict__ P, int64_t nnz_a, int32_t *__restrict__ keep) {
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nnz_a; j += (int64_t)gridDim.x * blockDim.x)
-    keep[j] = P[j + 1] > P[j] ? 1 : 0;
-}
-
-// pos: exclusive scan of the keep flags (nnz_a + 1 entries).  Row i of the
-// copy starts at pos[rp[i]]; a kept entry j goes to pos[j].
-__global__ void __launch_bounds__(256)
-    k_compact_a(const int32_t *__restrict__ arp, const int32_t *__restrict__ aci, int64_t m, int64_t nnz_a,
-                const int32_t *__restrict__ pos, int32_t *__restrict__ karp, int32_t *__restrict__ kaci,
+// The kept entries of every row (row of B not empty) go to the row's range
+// [karp[i], karp[i + 1]) of the copy, with their source entries.  A row that
+// lies in one thread's items keeps its stored order; the parts of a row
+// spread over several threads take their places in the order the parts
+// reserve them (cursor[i], zeroed first): the products of a row do not
+// depend on the order of its stored a_ik.
+__global__ void __launch_bounds__(kMergeThreads)
+    k_compact_a(Args a, int64_t nnz_a, int64_t nnz_b, const long long *__restrict__ starts,
+                const int32_t *__restrict__ karp, int32_t *__restrict__ cursor, int32_t *__restrict__ kaci,
                 int32_t *__restrict__ asrc) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nnz_a; j += stride) {
-    const int32_t q = pos[j];
-    if (pos[j + 1] > q) {
-      kaci[q] = aci[j];
-      asrc[q] = (int32_t)j;
-    }
-  }
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= m; i += stride) karp[i] = pos[arp[i]];
+  __shared__ int32_t lens[kMergeTile];
+  __shared__ int32_t ends[kMergeTile];
+  __shared__ long long coords[4];
+  merge_tile_walk(a.arp, a.aci, a.brp, a.m, nnz_a, a.n, nnz_b, a.err, starts, lens, ends, coords,
+                  [&](int64_t i, long long, int kp, bool whole, int64_t j, const int32_t *len, int n) {
+                    if (kp == 0) return;
+                    int32_t pos = karp[i] + (whole ? 0 : atomicAdd(cursor + i, kp));
+                    for (int q = 0; q < n; ++q) {
+                      if (len[q] > 0) {
+                        kaci[pos] = __ldg(a.aci + j + q);
+                        asrc[pos] = (int32_t)(j + q);
+                        ++pos;
+                      }
+                    }
+                  });
 }
 
 template <typename T>
@@ -56,14 +59,11 @@ static unsigned grid_for(int64_t n) {
   return (unsigned)(b < 1 ? 1 : b > 4096 ? 4096 : b);
 }
 
-cudaError_t compact_a_keep(spgemm_plan_s *p, int32_t *pos) {
-  k_compact_keep<<<grid_for(p->nnz_a), 256, 0, p->stream>>>(p->eflop, p->nnz_a, pos);
-  return cudaGetLastError();
-}
-
-cudaError_t compact_a_gather(spgemm_plan_s *p, const int32_t *pos) {
-  k_compact_a<<<grid_for(std::max<int64_t>(p->nnz_a, p->m + 1)), 256, 0, p->stream>>>(
-      p->arp, p->aci, p->m, p->nnz_a, pos, p->karp, p->kaci, p->asrc);
+cudaError_t compact_a_gather(spgemm_plan_s *p) {
+  Args a{p->m, p->n, p->k, p->arp, p->aci, p->brp, p->bci, p->av, p->bv, p->G, &p->dc->err};
+  const int64_t tiles = (p->m + p->nnz_a + kMergeTile - 1) / kMergeTile;
+  k_compact_a<<<(unsigned)tiles, kMergeThreads, 0, p->stream>>>(a, p->nnz_a, p->nnz_b, p->mstarts, p->karp, p->kept,
+                                                                 p->kaci, p->asrc);
   return cudaGetLastError();
 }
 

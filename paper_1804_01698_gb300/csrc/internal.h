@@ -209,6 +209,114 @@ inline int probe_mode(unsigned flags) {
 }
 
 // Kernel arguments common to all phases.
+// Merge-path split of a CSR matrix's rows (Merrill and Garland's merge-based
+// CSR traversal): the items are the m row ends and the nnz stored entries,
+// in the order a row-by-row walk meets them (row i's entries, then its
+// end).  Diagonal d (0 <= d <= m + nnz) of that walk is at row i, entry j
+// with i + j = d: rows below i are finished and entries below j consumed.
+// Threads and items (row ends + entries) per thread of the merge-path kernels.
+constexpr int kMergeThreads = 256, kMergeIPT = 8, kMergeTile = kMergeThreads * kMergeIPT;
+
+// Start (row, entry) of every merge-path tile: row i's entries and end take
+// diagonals [i + rp[i], i + rp[i + 1]], and tile t starts at diagonal
+// t * kMergeTile.  One coalesced pass over the row pointers instead of a
+// binary search per tile; starts[2 * tiles] = (m, nnz) ends the last tile.
+// A malformed row (its range outside [0, m + nnz]) writes nothing, and the
+// walk clamps what it reads.  Also zeroes flop[] and kept[] (null: not) for
+// the atomics of the walk that follows.
+__global__ void __launch_bounds__(256)
+    k_merge_starts(const int32_t *__restrict__ rp, int64_t m, int64_t nnz, int64_t tiles, long long *__restrict__ starts,
+                   int64_t *__restrict__ flop, int32_t *__restrict__ kept);
+
+// One tile of kMergeTile items of a merge-path walk over A, one block (tile
+// blockIdx.x, its start and end read from starts[]): the
+// B-row length of each of the tile's entries is gathered into shared memory
+// (lens[j - j0]; entries whose column is outside B, or whose row of B is
+// malformed, count 0 and raise kErrCsr), the row ends into ends[], and each
+// thread walks kMergeIPT consecutive items.  For every row that ends in its
+// items, the thread calls row(i, sum, kept, whole, j, len, n): the sum of
+// the lengths of the row's entries among the thread's items, how many are
+// non-zero, whether the row lies wholly in the thread's items, the first of
+// those entries (j), their lengths (len[0..n)) and their number; for the row
+// that continues past its items, it calls it with whole false if it met any
+// of the row's entries.  rp must be monotone for the sums to be the rows'
+// (the caller's row check reports it otherwise).  coords: 4 shared words.
+
+template <typename F>
+__device__ __forceinline__ void merge_tile_walk(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                                const int32_t *__restrict__ brp, int64_t m, int64_t nnz, int64_t nb,
+                                                int64_t nnz_b, uint32_t *err, const long long *__restrict__ starts,
+                                                int32_t *lens, int32_t *ends, long long *coords, F &&row) {
+  const int64_t N = m + nnz;
+  const int64_t D0 = (int64_t)blockIdx.x * kMergeTile;
+  const int64_t D1 = D0 + kMergeTile < N ? D0 + kMergeTile : N;
+  if (threadIdx.x < 4) coords[threadIdx.x] = starts[2 * (int64_t)blockIdx.x + threadIdx.x];
+  __syncthreads();
+  // for monotone row pointers both spans lie in A and within the tile;
+  // clamped for any others
+  auto clamp = [](int64_t v, int64_t lo, int64_t hi) { return v < lo ? lo : v > hi ? hi : v; };
+  const int64_t ib0 = clamp(coords[0], 0, m), jb0 = clamp(coords[1], 0, nnz);
+  const int64_t ni = clamp(coords[2] - ib0, 0, m - ib0 < kMergeTile ? m - ib0 : kMergeTile);
+  const int64_t nj = clamp(coords[3] - jb0, 0, nnz - jb0 < kMergeTile ? nnz - jb0 : kMergeTile);
+  for (int64_t t = threadIdx.x; t < nj; t += blockDim.x) {
+    const int32_t kk = __ldg(ci + jb0 + t);
+    int32_t len = 0;
+    if ((uint64_t)(int64_t)kk < (uint64_t)nb) {
+      const int32_t b0 = __ldg(brp + kk), b1 = __ldg(brp + kk + 1);
+      if (0 <= b0 && b0 <= b1 && (int64_t)b1 <= nnz_b) len = b1 - b0;
+      else raise_err(err, kErrCsr);
+    } else {
+      raise_err(err, kErrCsr);
+    }
+    lens[t] = len;
+  }
+  for (int64_t t = threadIdx.x; t < ni; t += blockDim.x) ends[t] = __ldg(rp + ib0 + t + 1);
+  __syncthreads();
+  // this thread's items: diagonals [d0, d1) of the tile, searched in the tile's lists
+  auto local_search = [&](int64_t d, int64_t *i, int64_t *j) {
+    int64_t lo = d - nj > 0 ? d - nj : 0, hi = d < ni ? d : ni;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if ((int64_t)ends[mid] - jb0 <= d - mid - 1) lo = mid + 1;
+      else hi = mid;
+    }
+    *i = lo;
+    *j = d - lo;
+  };
+  const int64_t span = D1 - D0;
+  const int64_t d0 = (int64_t)threadIdx.x * kMergeIPT < span ? (int64_t)threadIdx.x * kMergeIPT : span;
+  const int64_t d1 = d0 + kMergeIPT < span ? d0 + kMergeIPT : span;
+  if (d0 >= d1) return;
+  int64_t i, j, ie, je;
+  local_search(d0, &i, &j);
+  local_search(d1, &ie, &je);
+  // the thread's first row lies wholly in its items when it starts at them
+  bool whole = i < ni && (int64_t)__ldg(rp + ib0 + i) >= jb0 + j;
+  for (; i < ie; ++i) {
+    int64_t e = (int64_t)ends[i] - jb0;
+    e = e < j ? j : e > je ? je : e;
+    const int64_t first = j;
+    long long sum = 0;
+    int kept = 0;
+    for (; j < e; ++j) {
+      sum += lens[j];
+      kept += lens[j] > 0;
+    }
+    row(ib0 + i, sum, kept, whole, jb0 + first, (const int32_t *)lens + first, (int)(e - first));
+    whole = true;
+  }
+  if (j < je && ib0 + i < m) {
+    const int64_t first = j;
+    long long sum = 0;
+    int kept = 0;
+    for (; j < je; ++j) {
+      sum += lens[j];
+      kept += lens[j] > 0;
+    }
+    row(ib0 + i, sum, kept, false, jb0 + first, (const int32_t *)lens + first, (int)(je - first));
+  }
+}
+
 struct Args {
   int64_t m, n, k;
   const int32_t *arp, *aci, *brp, *bci;
@@ -272,9 +380,9 @@ struct spgemm_plan_s {
   bool long_ready;       // built: the plan has bitmap rows and long rows
   // compacted A (entries selecting a non-empty row of B), walked by the
   // phases instead of A when it holds fewer than half of A's entries
-  long long *eflop;      // flop pass: per stored a_ik the length of its row of B, then their
-                         // exclusive prefix (nnz(A) + 1 entries, fixed workspace)
-  long long *epart;      // scan partials of eflop (fixed workspace)
+  int32_t *kept;         // flop pass: per row, its stored a_ik whose row of B is not empty (fixed
+                         // workspace); the compaction's cursor afterwards
+  long long *mstarts;    // merge-path tile starts (row, entry) over A (fixed workspace)
   int64_t nnz_a_used;
   bool a_compact;
   void *acmp_ws;
@@ -393,8 +501,7 @@ size_t long_entry_bytes(int dtype);
 // Compacted A: keep flags of the entries (from the flop pass's prefix),
 // then, from their exclusive scan pos, the copy's row pointers, columns and
 // sources; its values before every numeric phase.
-cudaError_t compact_a_keep(spgemm_plan_s *p, int32_t *pos);
-cudaError_t compact_a_gather(spgemm_plan_s *p, const int32_t *pos);
+cudaError_t compact_a_gather(spgemm_plan_s *p);
 cudaError_t compact_a_values(spgemm_plan_s *p);
 // Arguments of the phase kernels: the compacted A when the plan has one.
 inline Args phase_args(const spgemm_plan_s *p, uint32_t *err, int probe, unsigned long long *ctr) {

@@ -94,53 +94,73 @@ __device__ __forceinline__ int num_bin_of(int64_t nnz, const HashCaps &caps) {
 // wait on its dependent loads row after row, and a hub row of thousands of
 // entries would hold it for len/32 steps).
 
-// elen[j] = nnz(b_k*) for stored entry j (column k); columns outside A or
-// malformed rows of B raise kErrCsr and count 0.  Counts the entries that
-// select a non-empty row of B.
 __global__ void __launch_bounds__(256)
-    k_entry_flop(Args a, int64_t nnz_a, int64_t nnz_b, long long *__restrict__ elen, DevCounters *dc) {
-  __shared__ unsigned long long s_nz;
-  if (threadIdx.x == 0) s_nz = 0;
-  __syncthreads();
-  unsigned long long nz = 0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
-  for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x * 4 + threadIdx.x; j0 < nnz_a; j0 += stride) {
-    int32_t kk[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) kk[u] = j0 + u * blockDim.x < nnz_a ? __ldg(a.aci + j0 + u * blockDim.x) : 0;
-    int64_t b0[4], b1[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const bool in = j0 + u * blockDim.x < nnz_a;
-      const bool ok = in && (uint64_t)(int64_t)kk[u] < (uint64_t)a.n;
-      b0[u] = ok ? __ldg(a.brp + kk[u]) : 0;
-      b1[u] = ok ? __ldg(a.brp + kk[u] + 1) : 0;
-      if (in && !ok) raise_err(a.err, kErrCsr);
+    k_merge_starts(const int32_t *__restrict__ rp, int64_t m, int64_t nnz, int64_t tiles, long long *__restrict__ starts,
+                   int64_t *__restrict__ flop, int32_t *__restrict__ kept) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int64_t i = t0; i < m; i += stride) {
+    if (flop) {
+      flop[i] = 0;
+      kept[i] = 0;
     }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int64_t j = j0 + u * blockDim.x;
-      if (j >= nnz_a) continue;
-      long long len = 0;
-      if (0 <= b0[u] && b0[u] <= b1[u] && b1[u] <= nnz_b) len = b1[u] - b0[u];
-      else raise_err(a.err, kErrCsr);
-      elen[j] = len;
-      nz += len > 0;
+    const int64_t r0 = __ldg(rp + i), r1 = __ldg(rp + i + 1);
+    if (r0 < 0 || r0 > r1 || r1 > nnz) continue;
+    const int64_t hi = i + r1;
+    for (int64_t D = (i + r0 + kMergeTile - 1) / kMergeTile * kMergeTile; D <= hi; D += kMergeTile) {
+      const int64_t t = D / kMergeTile;
+      if (t >= tiles) break;
+      starts[2 * t] = i;
+      starts[2 * t + 1] = D - i;
     }
   }
+  if (t0 == 0) {
+    starts[2 * tiles] = m;
+    starts[2 * tiles + 1] = nnz;
+  }
+}
+
+// flop[i] = sum over the stored a_ik of row i of nnz(b_k*), and kept[i], the
+// number of those a_ik whose row of B is not empty, by a merge-path walk over
+// A's row ends and entries: every thread takes kMergeIPT consecutive items,
+// so a hub row of A is shared by as many threads as its length asks and no
+// per-entry array is written.  A row that lies in one thread's items is
+// stored; the parts of the others are added with atomics into flop and
+// kept, which the caller zeroes first.  Columns outside B and malformed rows
+// of B raise kErrCsr and count 0.  Counts the entries that select a
+// non-empty row of B.
+__global__ void __launch_bounds__(kMergeThreads)
+    k_row_flop(Args a, int64_t nnz_a, int64_t nnz_b, const long long *__restrict__ starts, int64_t *__restrict__ flop,
+               int32_t *__restrict__ kept, DevCounters *dc) {
+  __shared__ int32_t lens[kMergeTile];
+  __shared__ int32_t ends[kMergeTile];
+  __shared__ long long coords[4];
+  __shared__ unsigned long long s_nz;
+  if (threadIdx.x == 0) s_nz = 0;
+  unsigned long long nz = 0;
+  merge_tile_walk(a.arp, a.aci, a.brp, a.m, nnz_a, a.n, nnz_b, a.err, starts, lens, ends, coords,
+                  [&](int64_t i, long long sum, int kp, bool whole, int64_t, const int32_t *, int) {
+                    nz += (unsigned long long)kp;
+                    if (whole) {
+                      flop[i] = sum;
+                      kept[i] = kp;
+                    } else {
+                      if (sum) atomicAdd(reinterpret_cast<unsigned long long *>(flop + i), (unsigned long long)sum);
+                      if (kp) atomicAdd(kept + i, kp);
+                    }
+                  });
   nz = warp_sum(nz);
   if ((threadIdx.x & 31) == 0 && nz) atomicAdd(&s_nz, nz);
   __syncthreads();
   if (threadIdx.x == 0 && s_nz) atomicAdd(&dc->nnz_a_used, s_nz);
 }
 
-// Row i (grid-stride): flop[i] = P[rp[i+1]] - P[rp[i]], its symbolic bin and
-// the plan's counters.  Row pointers must run from 0 to nnz(A) without
+// Row i (grid-stride): its symbolic bin from flop[i] (k_row_flop) and the
+// plan's counters.  Row pointers must run from 0 to nnz(A) without
 // decreasing; a row that breaks it raises kErrCsr and counts no flop.
 __global__ void __launch_bounds__(256)
-    k_row_flop(Args a, int64_t nnz_a, int64_t bitmap_min, HashCaps caps, int64_t gcap,
-               const long long *__restrict__ P, int64_t *__restrict__ flop, uint8_t *__restrict__ rbin,
-               int32_t *__restrict__ nnz_row, DevCounters *dc) {
+    k_row_bin(Args a, int64_t nnz_a, int64_t bitmap_min, HashCaps caps, int64_t gcap, int64_t *__restrict__ flop,
+              uint8_t *__restrict__ rbin, int32_t *__restrict__ nnz_row, DevCounters *dc) {
   __shared__ unsigned int hist[kNumSymBins];
   __shared__ unsigned long long hflop[kNumSymBins];
   __shared__ unsigned long long s_tot, s_max, s_maxg, s_extra;
@@ -156,11 +176,11 @@ __global__ void __launch_bounds__(256)
     const int64_t r0 = a.arp[row], r1 = a.arp[row + 1];
     int64_t f = 0;
     if (0 <= r0 && r0 <= r1 && r1 <= nnz_a && (row > 0 || r0 == 0) && (row < a.m - 1 || r1 == nnz_a)) {
-      f = P[r1] - P[r0];
+      f = flop[row];
     } else {
       raise_err(a.err, kErrCsr);
+      flop[row] = 0;
     }
-    flop[row] = f;
     const int64_t bound = f < a.k ? f : a.k;
     int bin = sym_bin_of(bound, bitmap_min, caps);
     if (bin == kSymGlobalBin && gcap >= 0 && bound >= gcap) {
@@ -269,9 +289,10 @@ __global__ void __launch_bounds__(kScanThreads)
 
 // out[i] = x[0] + ... + x[i-1] for i = 0..m; out may be x itself (each thread
 // reads its elements before it writes them, and the reduce pass is done).
+// With zero_in, x[] is zeroed once read (x not out).
 template <typename InT, typename OutT>
 __global__ void __launch_bounds__(kScanThreads)
-    k_scan_apply(const InT *x, int64_t m, const long long *__restrict__ partial, OutT *out) {
+    k_scan_apply(InT *x, int64_t m, const long long *__restrict__ partial, OutT *out, bool zero_in = false) {
   __shared__ long long red[33];
   const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
   InT v[kScanPer];
@@ -280,6 +301,7 @@ __global__ void __launch_bounds__(kScanThreads)
   for (int u = 0; u < kScanPer; ++u) {
     v[u] = base + u < m ? x[base + u] : 0;
     s += v[u];
+    if (zero_in && base + u < m) x[base + u] = 0;
   }
   long long tot;
   long long run = partial[blockIdx.x] + block_excl_scan(s, red, &tot);
@@ -682,14 +704,13 @@ int alloc_gtab(spgemm_plan_s *p, int64_t slots, size_t entry_bytes, int64_t rows
 // the scan of the counts; the copy's columns and sources are gathered once,
 // its values before every numeric phase.
 int compact_a(spgemm_plan_s *p) {
-  const int64_t m = p->m, nz = p->nnz_a_used, ne = p->nnz_a;
+  const int64_t m = p->m, nz = p->nnz_a_used;
   const size_t vs = value_size(p->dtype);
   const size_t o_rp = 0;
   const size_t o_ci = align_up((size_t)(m + 1) * 4, 256);
   const size_t o_v = o_ci + align_up((size_t)nz * 4, 256);
   const size_t o_src = o_v + align_up((size_t)nz * vs, 256);
-  const size_t o_pos = o_src + align_up((size_t)nz * 4, 256);
-  const size_t bytes = o_pos + align_up((size_t)(ne + 1) * 4, 256);
+  const size_t bytes = o_src + align_up((size_t)nz * 4, 256);
   cudaError_t e = cudaMallocAsync(&p->acmp_ws, bytes, p->stream);
   if (e != cudaSuccess) {
     p->acmp_ws = nullptr;
@@ -701,19 +722,17 @@ int compact_a(spgemm_plan_s *p) {
   p->kaci = reinterpret_cast<int32_t *>(b + o_ci);
   p->kav = b + o_v;
   p->asrc = reinterpret_cast<int32_t *>(b + o_src);
-  int32_t *pos = reinterpret_cast<int32_t *>(b + o_pos);
-  // pos[j] = kept entries before entry j (kept: P[j + 1] > P[j])
-  const int64_t nblk = (ne + kScanTile - 1) / kScanTile;
+  // the copy's row pointers: the exclusive scan of the flop pass's per-row
+  // counts; kept[] then serves as the per-row cursor of the gather
+  const int64_t nblk = (m + kScanTile - 1) / kScanTile;
+  long long *partial = (long long *)((char *)p->perm2 + align_up((size_t)m * 4, 256));
   {
     KernelScope ks(p, "compact_a");
-    e = compact_a_keep(p, pos);
-    if (e == cudaSuccess) {
-      k_scan_reduce<<<(unsigned)nblk, kScanThreads, 0, p->stream>>>(pos, ne, p->epart);
-      k_scan_spine<<<1, kScanThreads, 0, p->stream>>>(p->epart, nblk, INT32_MAX, &p->dc->scan_total, &p->dc->err);
-      k_scan_apply<<<(unsigned)nblk, kScanThreads, 0, p->stream>>>(pos, ne, p->epart, pos);
-      e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) e = compact_a_gather(p, pos);
+    k_scan_reduce<<<(unsigned)nblk, kScanThreads, 0, p->stream>>>(p->kept, m, partial);
+    k_scan_spine<<<1, kScanThreads, 0, p->stream>>>(partial, nblk, INT32_MAX, &p->dc->scan_total, &p->dc->err);
+    k_scan_apply<<<(unsigned)nblk, kScanThreads, 0, p->stream>>>(p->kept, m, partial, p->karp, true);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = compact_a_gather(p);
   }
   if (e != cudaSuccess) return fail_cuda(e, "compacting A");
   p->a_compact = true;
@@ -843,11 +862,10 @@ int plan_init(spgemm_plan_s **out, const spgemm_csr *A, const spgemm_csr *B, int
   off = align_up(off + (size_t)m * 4, 256);
   const size_t o_part = off;
   off = align_up(off + (size_t)nblk * 8, 256);
-  const int64_t nblk_e = (p->nnz_a + kScanTile - 1) / kScanTile + 1;
-  const size_t o_eflop = off;
-  off = align_up(off + (size_t)(p->nnz_a + 1) * 8, 256);
-  const size_t o_epart = off;
-  off = align_up(off + (size_t)nblk_e * 8, 256);
+  const size_t o_kept = off;
+  off = align_up(off + (size_t)m * 4, 256);
+  const size_t o_mstarts = off;
+  off = align_up(off + (size_t)((m + p->nnz_a) / kMergeTile + 2) * 2 * sizeof(long long), 256);
   const size_t o_doff = off;
   off = align_up(off + 2 * 16 * sizeof(long long), 256);
   const size_t o_lmap = off;
@@ -874,8 +892,8 @@ int plan_init(spgemm_plan_s **out, const spgemm_csr *A, const spgemm_csr *B, int
   p->rbin2 = (uint8_t *)(base + o_rbin2);
   p->perm2 = (int32_t *)(base + o_perm2);
   (void)o_part;
-  p->eflop = (long long *)(base + o_eflop);
-  p->epart = (long long *)(base + o_epart);
+  p->kept = (int32_t *)(base + o_kept);
+  p->mstarts = (long long *)(base + o_mstarts);
   p->d_sym_off = (long long *)(base + o_doff);
   p->d_num_off = p->d_sym_off + 16;
   if (p->long_min > 0) {
@@ -900,20 +918,14 @@ cudaError_t enqueue_flop(spgemm_plan_s *p) {
     const int64_t bm_min = !p->bitmap_ok || p->tune_bm_min < 0 ? 0
                            : p->tune_bm_min > 0                 ? p->tune_bm_min
                                                                 : bitmap_min_bound(p->k);
-    const int64_t ne = p->nnz_a;
-    if (ne > 0) {
-      const int64_t nblk = (ne + kScanTile - 1) / kScanTile;
-      const int64_t eb = std::min<int64_t>((ne + 1023) / 1024, 8 * (int64_t)sm_count());
-      k_entry_flop<<<(unsigned)eb, 256, 0, p->stream>>>(a, ne, p->nnz_b, p->eflop, p->dc);
-      k_scan_reduce<<<(unsigned)nblk, kScanThreads, 0, p->stream>>>(p->eflop, ne, p->epart);
-      k_scan_spine<<<1, kScanThreads, 0, p->stream>>>(p->epart, nblk, LLONG_MAX, &p->dc->scan_total, &p->dc->err);
-      k_scan_apply<<<(unsigned)nblk, kScanThreads, 0, p->stream>>>(p->eflop, ne, p->epart, p->eflop);
-    } else {
-      e = cudaMemsetAsync(p->eflop, 0, sizeof(long long), p->stream);
-    }
+    const int64_t tiles = (m + p->nnz_a + kMergeTile - 1) / kMergeTile;
+    k_merge_starts<<<(unsigned)std::min<int64_t>((m + 255) / 256, 8 * (int64_t)sm_count()), 256, 0, p->stream>>>(
+        p->arp, m, p->nnz_a, tiles, p->mstarts, p->flop, p->kept);
+    k_row_flop<<<(unsigned)tiles, kMergeThreads, 0, p->stream>>>(a, p->nnz_a, p->nnz_b, p->mstarts, p->flop, p->kept,
+                                                                 p->dc);
     const int64_t rb = std::min<int64_t>((m + 255) / 256, 8 * (int64_t)sm_count());
-    k_row_flop<<<(unsigned)rb, 256, 0, p->stream>>>(a, p->nnz_a, bm_min, p->caps, p->gcap_bound, p->eflop, p->flop,
-                                                    p->rbin, p->nnz_row, p->dc);
+    k_row_bin<<<(unsigned)rb, 256, 0, p->stream>>>(a, p->nnz_a, bm_min, p->caps, p->gcap_bound, p->flop, p->rbin,
+                                                   p->nnz_row, p->dc);
   }
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e == cudaSuccess) {
