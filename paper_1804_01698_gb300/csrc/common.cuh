@@ -269,6 +269,30 @@ template <typename T> __device__ __forceinline__ T warp_incl_scan(T v) {
   return v;
 }
 
+// Adds one row of flop v to bin b (b < nb; others add nothing) of a block's
+// shared histogram: one shared atomic pair per distinct bin of the warp
+// instead of one per lane, since most rows of a warp share a bin and
+// atomics on one address serialise.  Every lane of the warp calls it.
+__device__ __forceinline__ void warp_hist_add(int b, unsigned long long v, int nb, unsigned int *hist,
+                                              unsigned long long *hflop) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  unsigned pending = __ballot_sync(full, b < nb);
+  while (pending != 0u) {
+    const int leader = __ffs(pending) - 1;
+    const int lb = __shfl_sync(full, b, leader);
+    const unsigned grp = __ballot_sync(full, b == lb);
+    unsigned long long sum = b == lb ? v : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(full, sum, o);
+    if (lane == leader) {
+      atomicAdd(&hist[lb], (unsigned)__popc(grp));
+      if (sum) atomicAdd(&hflop[lb], sum);
+    }
+    pending &= ~grp;
+  }
+}
+
 // Block-wide sum; every thread of the block must call it.  `scratch` holds
 // at least 32 elements and is reused, so callers separate two calls with a
 // barrier (the function ends with one).

@@ -171,30 +171,31 @@ __global__ void __launch_bounds__(256)
   if (threadIdx.x == 0) s_tot = s_max = s_maxg = s_extra = 0;
   __syncthreads();
   unsigned long long tot = 0, mx = 0, mxg = 0, extra = 0;
-  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < a.m;
-       row += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r0 = a.arp[row], r1 = a.arp[row + 1];
-    int64_t f = 0;
-    if (0 <= r0 && r0 <= r1 && r1 <= nnz_a && (row > 0 || r0 == 0) && (row < a.m - 1 || r1 == nnz_a)) {
-      f = flop[row];
-    } else {
-      raise_err(a.err, kErrCsr);
-      flop[row] = 0;
+  // every lane of a warp takes the same number of steps (warp_hist_add)
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.m; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = base + threadIdx.x;
+    int64_t f = 0, bound = 0;
+    int bin = 255;
+    if (row < a.m) {
+      const int64_t r0 = a.arp[row], r1 = a.arp[row + 1];
+      if (0 <= r0 && r0 <= r1 && r1 <= nnz_a && (row > 0 || r0 == 0) && (row < a.m - 1 || r1 == nnz_a)) {
+        f = flop[row];
+      } else {
+        raise_err(a.err, kErrCsr);
+        flop[row] = 0;
+      }
+      bound = f < a.k ? f : a.k;
+      bin = sym_bin_of(bound, bitmap_min, caps);
+      if (bin == kSymGlobalBin && gcap >= 0 && bound >= gcap) {
+        // graph mode: no table was planned for a row this large
+        raise_err(a.err, kErrCapacity);
+        bin = 255;
+      }
+      rbin[row] = (uint8_t)bin;
+      if (bin == 255) nnz_row[row] = 0;
     }
-    const int64_t bound = f < a.k ? f : a.k;
-    int bin = sym_bin_of(bound, bitmap_min, caps);
-    if (bin == kSymGlobalBin && gcap >= 0 && bound >= gcap) {
-      // graph mode: no table was planned for a row this large
-      raise_err(a.err, kErrCapacity);
-      bin = 255;
-    }
-    rbin[row] = (uint8_t)bin;
-    if (bin == 255) {
-      nnz_row[row] = 0;
-    } else {
-      atomicAdd(&hist[bin], 1u);
-      atomicAdd(&hflop[bin], (unsigned long long)f);
-    }
+    warp_hist_add(bin, (unsigned long long)f, kNumSymBins, hist, hflop);
+    if (row >= a.m) continue;
     if (bin == kSymGlobalBin && (unsigned long long)bound > mxg) mxg = (unsigned long long)bound;
     if (bin == kSymBitmapBin && sym_split_parts(f) > 1) extra += (unsigned long long)(sym_split_parts(f) - 1);
     tot += (unsigned long long)f;
@@ -327,8 +328,9 @@ __global__ void __launch_bounds__(256)
   if (threadIdx.x == 0) s_maxg = 0;
   __syncthreads();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int b = 255;
+  unsigned long long f = 0;
   if (i < m) {
-    int b = 255;
     if (!is_bitmap_row(rbin[i])) {
       const int32_t z = nnz_row[i];
       b = num_bin_of(z, caps);
@@ -339,11 +341,9 @@ __global__ void __launch_bounds__(256)
       if (b == kNumGlobalBin) atomicMax(&s_maxg, (unsigned long long)z);
     }
     rbin2[i] = (uint8_t)b;
-    if (b != 255) {
-      atomicAdd(&hist[b], 1u);
-      atomicAdd(&hflop[b], (unsigned long long)flop[i]);
-    }
+    if (b != 255) f = (unsigned long long)flop[i];
   }
+  warp_hist_add(b, f, kNumNumBins, hist, hflop);
   __syncthreads();
   if (threadIdx.x < kNumNumBins && hist[threadIdx.x]) atomicAdd(&dc->num_count[threadIdx.x], hist[threadIdx.x]);
   if (threadIdx.x < kNumNumBins && hflop[threadIdx.x]) atomicAdd(&dc->num_flop[threadIdx.x], hflop[threadIdx.x]);
