@@ -36,7 +36,7 @@ struct BinCfg {
 };
 
 constexpr int kNumHashBins = 10;     // warp 64..1024, block 2048..32768
-constexpr int kSymBitmapBin = 10;    // bitmap rows with bound > kBitmapMidMax (1024 threads)
+constexpr int kSymBitmapBin = 10;    // bitmap rows with bound > kBitmapMidMax (split into parts)
 constexpr int kSymBitmapMidBin = 11; // bitmap rows with bound <= kBitmapMidMax (256 threads)
 constexpr int kSymGlobalBin = 12;
 constexpr int kNumSymBins = 13;

@@ -33,7 +33,7 @@ const BinCfg kSymBins[kNumSymBins] = {
     {kWarp, 1024, kWarpsPerBlock * 32, 512},   {kBlock, 2048, 256, 1536},
     {kBlock, 4096, 512, 3072},                 {kBlock, 8192, 1024, 6144},
     {kBlock, 16384, 1024, 12288},              {kBlock, 32768, 1024, 24576},
-    {kBitmap, 0, 1024, INT64_MAX},             {kBitmap, 0, 256, kBitmapMidMax},
+    {kBitmap, 0, 256, INT64_MAX},              {kBitmap, 0, 256, kBitmapMidMax},
     {kGlobal, 0, 1024, INT64_MAX}};
 
 const BinCfg kNumBins[kNumNumBins] = {

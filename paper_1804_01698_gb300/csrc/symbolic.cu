@@ -344,10 +344,14 @@ cudaError_t launch_symbolic(spgemm_plan_s *p) {
       case kSymBitmapMidBin: {
         // bitmaps of both bins are stored in perm order from the first bitmap bin on
         const size_t smem = (size_t)p->bm_words * sizeof(uint32_t);
-        // heavy rows 2 x 1024 and medium rows 8 x 256 threads per SM: the
-        // register budgets (32 per thread) that let the bitmaps' shared memory
-        // set the occupancy (measured 12% and 22% faster than 64 registers)
-        auto kern = b == kSymBitmapBin ? k_sym_bitmap<1024, 2> : k_sym_bitmap<256, 8>;
+        // heavy and medium rows alike 8 x 256 threads per SM: the register
+        // budget (32 per thread) that lets the bitmaps' shared memory set the
+        // occupancy (measured 22% faster than 64 registers).  The two bins run
+        // side by side on their own streams, and blocks of one shape interleave
+        // on the SMs.  Measured on R-MAT A*A, scale 16: heavy rows at 2 x 1024
+        // threads per SM ran the whole product 8% slower (4.02 against 3.70 ms),
+        // at 4 x 512 1% slower.
+        auto kern = k_sym_bitmap<256, 8>;
         e = prep(kern, smem);
         if (e != cudaSuccess) break;
         {
