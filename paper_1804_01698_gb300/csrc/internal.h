@@ -216,6 +216,9 @@ inline int probe_mode(unsigned flags) {
 // with i + j = d: rows below i are finished and entries below j consumed.
 // Threads and items (row ends + entries) per thread of the merge-path kernels.
 constexpr int kMergeThreads = 256, kMergeIPT = 8, kMergeTile = kMergeThreads * kMergeIPT;
+// Kept entries (row of B not empty) that the flop pass lists per tile for the
+// compaction; a tile with more is walked again.
+constexpr int kKeptListCap = 128;
 
 // Start (row, entry) of every merge-path tile: row i's entries and end take
 // diagonals [i + rp[i], i + rp[i + 1]], and tile t starts at diagonal
@@ -383,6 +386,8 @@ struct spgemm_plan_s {
   int32_t *kept;         // flop pass: per row, its stored a_ik whose row of B is not empty (fixed
                          // workspace); the compaction's cursor afterwards
   long long *mstarts;    // merge-path tile starts (row, entry) over A (fixed workspace)
+  int2 *klist;           // per merge-path tile: its kept entries (row, entry), kKeptListCap at most
+  int32_t *klist_n;      // per tile: the number of them, or -1 when they did not fit
   int64_t nnz_a_used;
   bool a_compact;
   void *acmp_ws;

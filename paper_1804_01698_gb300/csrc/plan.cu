@@ -131,15 +131,20 @@ __global__ void __launch_bounds__(256)
 // non-empty row of B.
 __global__ void __launch_bounds__(kMergeThreads)
     k_row_flop(Args a, int64_t nnz_a, int64_t nnz_b, const long long *__restrict__ starts, int64_t *__restrict__ flop,
-               int32_t *__restrict__ kept, DevCounters *dc) {
+               int32_t *__restrict__ kept, int2 *__restrict__ klist, int32_t *__restrict__ klist_n, DevCounters *dc) {
   __shared__ int32_t lens[kMergeTile];
   __shared__ int32_t ends[kMergeTile];
   __shared__ long long coords[4];
   __shared__ unsigned long long s_nz;
-  if (threadIdx.x == 0) s_nz = 0;
+  __shared__ int s_nk;
+  if (threadIdx.x == 0) {
+    s_nz = 0;
+    s_nk = 0;
+  }
   unsigned long long nz = 0;
+  int2 *list = klist + (size_t)blockIdx.x * kKeptListCap;
   merge_tile_walk(a.arp, a.aci, a.brp, a.m, nnz_a, a.n, nnz_b, a.err, starts, lens, ends, coords,
-                  [&](int64_t i, long long sum, int kp, bool whole, int64_t, const int32_t *, int) {
+                  [&](int64_t i, long long sum, int kp, bool whole, int64_t j, const int32_t *len, int n) {
                     nz += (unsigned long long)kp;
                     if (whole) {
                       flop[i] = sum;
@@ -148,11 +153,19 @@ __global__ void __launch_bounds__(kMergeThreads)
                       if (sum) atomicAdd(reinterpret_cast<unsigned long long *>(flop + i), (unsigned long long)sum);
                       if (kp) atomicAdd(kept + i, kp);
                     }
+                    if (kp > 0) {
+                      const int at = atomicAdd(&s_nk, kp);
+                      for (int q = 0, w = at; q < n && w < kKeptListCap; ++q)
+                        if (len[q] > 0) list[w++] = make_int2((int)i, (int)(j + q));
+                    }
                   });
   nz = warp_sum(nz);
   if ((threadIdx.x & 31) == 0 && nz) atomicAdd(&s_nz, nz);
   __syncthreads();
-  if (threadIdx.x == 0 && s_nz) atomicAdd(&dc->nnz_a_used, s_nz);
+  if (threadIdx.x == 0) {
+    if (s_nz) atomicAdd(&dc->nnz_a_used, s_nz);
+    klist_n[blockIdx.x] = s_nk <= kKeptListCap ? s_nk : -1;
+  }
 }
 
 // Row i (grid-stride): its symbolic bin from flop[i] (k_row_flop) and the
@@ -864,8 +877,13 @@ int plan_init(spgemm_plan_s **out, const spgemm_csr *A, const spgemm_csr *B, int
   off = align_up(off + (size_t)nblk * 8, 256);
   const size_t o_kept = off;
   off = align_up(off + (size_t)m * 4, 256);
+  const int64_t mtiles = (m + p->nnz_a) / kMergeTile + 2;
   const size_t o_mstarts = off;
-  off = align_up(off + (size_t)((m + p->nnz_a) / kMergeTile + 2) * 2 * sizeof(long long), 256);
+  off = align_up(off + (size_t)mtiles * 2 * sizeof(long long), 256);
+  const size_t o_klist = off;
+  off = align_up(off + (size_t)mtiles * kKeptListCap * sizeof(int2), 256);
+  const size_t o_klist_n = off;
+  off = align_up(off + (size_t)mtiles * sizeof(int32_t), 256);
   const size_t o_doff = off;
   off = align_up(off + 2 * 16 * sizeof(long long), 256);
   const size_t o_lmap = off;
@@ -894,6 +912,8 @@ int plan_init(spgemm_plan_s **out, const spgemm_csr *A, const spgemm_csr *B, int
   (void)o_part;
   p->kept = (int32_t *)(base + o_kept);
   p->mstarts = (long long *)(base + o_mstarts);
+  p->klist = (int2 *)(base + o_klist);
+  p->klist_n = (int32_t *)(base + o_klist_n);
   p->d_sym_off = (long long *)(base + o_doff);
   p->d_num_off = p->d_sym_off + 16;
   if (p->long_min > 0) {
@@ -922,7 +942,7 @@ cudaError_t enqueue_flop(spgemm_plan_s *p) {
     k_merge_starts<<<(unsigned)std::min<int64_t>((m + 255) / 256, 8 * (int64_t)sm_count()), 256, 0, p->stream>>>(
         p->arp, m, p->nnz_a, tiles, p->mstarts, p->flop, p->kept);
     k_row_flop<<<(unsigned)tiles, kMergeThreads, 0, p->stream>>>(a, p->nnz_a, p->nnz_b, p->mstarts, p->flop, p->kept,
-                                                                 p->dc);
+                                                                 p->klist, p->klist_n, p->dc);
     const int64_t rb = std::min<int64_t>((m + 255) / 256, 8 * (int64_t)sm_count());
     k_row_bin<<<(unsigned)rb, 256, 0, p->stream>>>(a, p->nnz_a, bm_min, p->caps, p->gcap_bound, p->flop, p->rbin,
                                                    p->nnz_row, p->dc);

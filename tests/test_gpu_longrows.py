@@ -151,6 +151,31 @@ def test_compacted_a_for_frontier_products(dt, sorted_output):
     assert_matches_oracle(C, A, F, sorted_output)
 
 
+@pytest.mark.parametrize("dt", ["f64", "i64"])
+@pytest.mark.parametrize("sorted_output", [True, False])
+def test_compacted_a_with_crowded_tiles(dt, sorted_output):
+    """B's rows are empty but for its 64 lowest, which R-MAT's hub rows of A
+    select again and again: fewer than half of A's entries select a non-empty
+    row of B (so A is compacted), while the tiles of the hub rows hold more
+    kept entries than the flop pass lists per tile (so the compaction walks
+    those tiles again) and hub rows span several tiles."""
+    A = typed(inputs.rmat(12, 16, seed=431), dt, 432)
+    n = A.ncols
+    rows = np.repeat(np.arange(64), 3)
+    cols = inputs.draw_bits(433, 7, np.arange(rows.size, dtype=np.uint64)) % np.uint64(n)
+    rp, ci = inputs.from_coo(n, n, rows, cols.astype(np.int64))
+    Bm = typed(CSR(n, n, rp, ci, np.ones(len(ci))), dt, 434)
+    aci = A.col_idx
+    kept = int((aci < 64).sum())
+    assert 0 < kept < A.nnz // 2
+    rp_a = A.row_ptr.astype(np.int64)
+    in_first_tile = int((aci[: min(A.nnz, 2048)] < 64).sum())
+    assert in_first_tile > 128                      # the first tile's kept entries overflow its list
+    C, st = product(A, Bm, DT[dt], sorted_output, None)
+    assert st["nnz_a_walked"] == kept
+    assert_matches_oracle(C, A, Bm, sorted_output)
+
+
 def test_compacted_a_follows_new_values():
     from paper_1804_01698_gb300 import binding as sg
     A = inputs.rmat(12, 16, seed=418)
