@@ -138,7 +138,8 @@ typedef struct {
     int64_t num_probes, num_inserts;       /* the same for the numeric phase */
     int64_t nnz_a_walked;      /* stored a_ik the phases walk: nnz(A), or fewer when the plan dropped the
                                   entries that select an empty row of B (fewer than half of A's were kept) */
-    int64_t long_rows;         /* long rows of B the bitmap rows take whole (spgemm_tuning::long_row_min) */
+    int64_t long_rows;         /* long rows of B whose bitmaps the symbolic bitmap rows OR in whole
+                                  (spgemm_tuning::long_row_min) */
     int64_t long_entries;      /* their entries */
 } spgemm_stats;
 
@@ -174,11 +175,10 @@ SPGEMM_API int spgemm_plan_create(spgemm_plan_t *out, const spgemm_csr *A, const
  *                     output memory of a product (and lets tests reach the
  *                     overflow path on small inputs).
  *   long_row_min      rows of B with at least this many entries are "long
- *                     rows": inside bitmap rows of A their products are
- *                     taken from a copy of the long row grouped by column
- *                     owner (numeric) and its column bitmap (symbolic)
- *                     instead of one by one: 0 = max(512, k/128); -1 = no
- *                     long rows; otherwise a positive length.
+ *                     rows": inside bitmap rows of A the symbolic phase ORs
+ *                     their saved column bitmaps word by word instead of
+ *                     setting one bit per product: 0 = max(512, k/128);
+ *                     -1 = no long rows; otherwise a positive length.
  *   warp_load_pct     largest key bound of a warp hash table, in percent of
  *                     its slots (Sec. 4.2.1 sizes a table from the row's
  *                     bound; lower loads shorten probes): 0 = 50; else

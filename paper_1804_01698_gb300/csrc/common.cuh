@@ -212,35 +212,6 @@ template <> struct Val<int64_t> {
   }
 };
 
-// ---------------------------------------------------------------------------
-// Entries of the grouped copies of long rows of B: column and value, read
-// with one 16-byte (8-byte for f32) load.
-template <typename T> struct alignas(16) LEnt {
-  int32_t col;
-  int32_t pad;
-  T v;
-};
-template <> struct alignas(8) LEnt<float> {
-  int32_t col;
-  float v;
-};
-
-__device__ __forceinline__ void load_lent(const LEnt<double> *p, int32_t *col, double *v) {
-  const int4 raw = __ldg(reinterpret_cast<const int4 *>(p));
-  *col = raw.x;
-  *v = __hiloint2double(raw.w, raw.z);
-}
-__device__ __forceinline__ void load_lent(const LEnt<int64_t> *p, int32_t *col, int64_t *v) {
-  const int4 raw = __ldg(reinterpret_cast<const int4 *>(p));
-  *col = raw.x;
-  *v = (int64_t)(((unsigned long long)(unsigned)raw.w << 32) | (unsigned)raw.z);
-}
-__device__ __forceinline__ void load_lent(const LEnt<float> *p, int32_t *col, float *v) {
-  const int2 raw = __ldg(reinterpret_cast<const int2 *>(p));
-  *col = raw.x;
-  *v = __int_as_float(raw.y);
-}
-
 
 // ---------------------------------------------------------------------------
 // Reductions and scans.

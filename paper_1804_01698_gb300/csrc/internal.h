@@ -121,16 +121,10 @@ __host__ __device__ inline int bm_split_parts(long long flop, long long nnz) {
   if (parts > kSplitMaxParts) parts = kSplitMaxParts;
   return (int)parts;
 }
-// Long rows of B.  Inside bitmap rows of A, the products of a row k of B
-// with at least long_row_min entries are not taken one by one: the symbolic
-// phase ORs k's saved column bitmap into the row's bitmap, and the numeric
-// phase reads a copy of row k sorted by column, split into kLongRanges
-// column ranges of equal mass over all long rows; warp w of a block of NW
-// warps owns ranges [w*kLongRanges/NW, (w+1)*kLongRanges/NW) of every long
-// row, and so every column in them, and adds into their sums with plain
-// loads and stores.  The rule below is the default threshold
-// (spgemm_tuning).
-constexpr int kLongRanges = 32;
+// Long rows of B.  Inside bitmap rows of A, the symbolic phase does not take
+// the products of a row k of B with at least long_row_min entries one by
+// one: it ORs k's saved column bitmap into the row's bitmap.  The rule below
+// is the default threshold (spgemm_tuning).
 // Measured on R-MAT A*A, scale 16 (k = 2^16): thresholds 256, 512 and 1024
 // gave 4.26, 4.23 and 4.25 ms per product; 64 and 128 were 10-30% slower.
 inline int64_t long_row_min_default(int64_t k) {
@@ -142,8 +136,6 @@ inline int64_t long_row_min_default(int64_t k) {
 struct LongRows {
   const int32_t *map;    // per row of B: its long-row index d, or -1
   const uint32_t *bits;  // column bitmap of long row d: bits[d * words + w]
-  const int32_t *off;    // off[d * (kLongRanges + 1) + r]: first entry of range r (absolute index)
-  const void *ent;       // entries {column, value}, each long row sorted by column (LEnt<T>)
 };
 
 // Rows of one bin: perm[off[bin]] .. perm[off[bin + 1] - 1].  The offsets
@@ -370,16 +362,13 @@ struct spgemm_plan_s {
   sg::HashCaps caps;     // hash-bin key caps (spgemm_tuning load factors)
   // long rows of B (spgemm_tuning::long_row_min; long_min 0: none)
   int64_t long_min;
-  int64_t long_cap;      // room in lrow/lbase: nnz(B) / long_min + 1
+  int64_t long_cap;      // room in lrow: nnz(B) / long_min + 1
   int64_t n_long, long_tot;
   int32_t *lmap;         // per row of B (fixed workspace)
-  int32_t *lrow, *lbase; // per long row: row of B, first entry (fixed workspace)
-  void *long_ws;         // bitmaps, group offsets, entries, entry sources
+  int32_t *lrow;         // per long row: its row of B (fixed workspace)
+  void *long_ws;         // the long rows' bitmaps
   size_t long_ws_bytes;
   uint32_t *lbits;
-  int32_t *loff;
-  void *lent;
-  int32_t *lsrc;
   bool long_ready;       // built: the plan has bitmap rows and long rows
   // compacted A (entries selecting a non-empty row of B), walked by the
   // phases instead of A when it holds fewer than half of A's entries
@@ -493,16 +482,13 @@ cudaStream_t bin_stream(spgemm_plan_s *p, int i);
 cudaError_t join(spgemm_plan_s *p);
 
 // Long rows: marks the long rows of B (before the flop pass's counters are
-// read), then builds their bitmaps and owner groups (when bitmap rows
-// exist), and refreshes the grouped copies' values before a numeric phase.
+// read), then builds their bitmaps (when bitmap rows exist).
 cudaError_t long_rows_mark(spgemm_plan_s *p);
 cudaError_t long_rows_build(spgemm_plan_s *p);
-cudaError_t long_rows_values(spgemm_plan_s *p);
 inline LongRows long_rows(const spgemm_plan_s *p) {
-  if (!p->long_ready) return LongRows{nullptr, nullptr, nullptr, nullptr};
-  return LongRows{p->lmap, p->lbits, p->loff, p->lent};
+  if (!p->long_ready) return LongRows{nullptr, nullptr};
+  return LongRows{p->lmap, p->lbits};
 }
-size_t long_entry_bytes(int dtype);
 // Compacted A: keep flags of the entries (from the flop pass's prefix),
 // then, from their exclusive scan pos, the copy's row pointers, columns and
 // sources; its values before every numeric phase.

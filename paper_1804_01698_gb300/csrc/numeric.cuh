@@ -518,103 +518,20 @@ __global__ void __launch_bounds__(256)
 // of smaller ratio the match costs more than the contention it removes.
 constexpr long long kAggregateMinRatio = 32;
 
-// Long pass of a bitmap row, one warp: list[0..nl) holds long entries of
-// the row (long-row index d, A entry j).  The warp adds the products that
-// fall in its own column ranges (kLongRanges / (NT / 32) of them, the same
-// for every long row).  Its work is a sequence of slices, each 32
-// consecutive entries of one long row's part (distinct columns, so distinct
-// ranks); slices are loaded kDepth ahead of the one being added, so the L2
-// latency of the loads overlaps the shared-memory updates, and a __syncwarp
-// after each slice orders the updates of long rows that share a column.  No
-// other warp touches these ranks until the block's next barrier, so the
-// updates are plain loads and stores.
-template <typename T, int NT, typename RF>
-__device__ __forceinline__ void warp_long_pass(const int2 *list, int nl, const T *__restrict__ av,
-                                               const LongRows &lr, T *vals, int span, RF &&rank_of) {
-  constexpr int kNW = NT / 32, kRPW = kLongRanges / kNW, kDepth = 4;
-  const unsigned full = 0xffffffffu;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const LEnt<T> *ent = reinterpret_cast<const LEnt<T> *>(lr.ent);
-  for (int l0 = 0; l0 < nl; l0 += 32) {
-    int s0 = 0, s1 = 0;  // lane l: this warp's part of long entry l0 + l
-    T al = T(0);
-    if (l0 + lane < nl) {
-      const int2 e = list[l0 + lane];
-      const int32_t *o = lr.off + (size_t)e.x * (kLongRanges + 1) + wid * kRPW;
-      s0 = __ldg(o);
-      s1 = __ldg(o + kRPW);
-      al = __ldg(av + e.y);
-    }
-    unsigned pend = __ballot_sync(full, s1 > s0);  // lanes whose part is not empty, not yet started
-    if (pend == 0u) continue;
-    // next slice to load (warp-uniform): the part of lane ij, entries [ib, ie)
-    int ij = __ffs(pend) - 1;
-    pend &= pend - 1u;
-    int ib = __shfl_sync(full, s0, ij), ie = __shfl_sync(full, s1, ij);
-    int jq[kDepth];
-    int32_t cq[kDepth];
-    T vq[kDepth];
-    auto issue = [&](int k) {
-      jq[k] = ij;
-      cq[k] = -1;
-      vq[k] = T(0);
-      if (ij >= 0) {
-        if (ib + lane < ie) load_lent(ent + ib + lane, &cq[k], &vq[k]);
-        ib += 32;
-        if (ib >= ie) {
-          if (pend != 0u) {
-            ij = __ffs(pend) - 1;
-            pend &= pend - 1u;
-            ib = __shfl_sync(full, s0, ij);
-            ie = __shfl_sync(full, s1, ij);
-          } else {
-            ij = -1;
-          }
-        }
-      }
-    };
-#pragma unroll
-    for (int k = 0; k < kDepth; ++k) issue(k);
-    bool more = true;
-    while (more) {
-#pragma unroll
-      for (int k = 0; k < kDepth; ++k) {
-        if (!more) continue;
-        if (jq[k] < 0) {
-          more = false;
-          continue;
-        }
-        const T a = __shfl_sync(full, al, jq[k]);
-        if (cq[k] >= 0) {
-          const int r = rank_of(cq[k]);
-          if ((unsigned)r < (unsigned)span) vals[r] = Val<T>::mad(vals[r], a, vq[k]);
-        }
-        __syncwarp();
-        issue(k);
-      }
-    }
-  }
-}
-
 // Heavy rows with a saved column bitmap.  Item (t, wdw, part, parts): bitmap
 // t of the symbolic bitmap bin (row bm_rows[t]), output ranks
 // [wdw*cap, (wdw+1)*cap), products of the part'th of `parts` ranges of the
 // row's stored a_ik.  A row in one part stores its values; a split row's
 // parts add theirs into C (zeroed by k_bm_zero_split) and part 0 stores
 // the columns.
-// In the medium and small classes, products of long rows of B (lr.map) are
-// taken first, from their column-sorted copies (warp_long_pass): warp w owns
-// its share of the column ranges of every long row, hence the output ranks
-// of those columns, and adds into them with plain shared-memory loads and
-// stores.  After a barrier the other products (all products, in the large
-// class) go through compare-and-swap accumulation (f64) or atomic adds.
+// Every product goes through compare-and-swap accumulation (f64) or atomic
+// adds into the rank-indexed values.
 template <typename T, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
     k_num_bitmap(Args a, const int32_t *__restrict__ bm_rows, const int4 *__restrict__ items,
                  const int64_t *__restrict__ flop, const uint32_t *__restrict__ bitmaps, int words, int cap,
                  const int32_t *__restrict__ c_rp,
-                 int32_t *__restrict__ c_ci, T *__restrict__ c_v, LongRows lr) {
-  static_assert(kLongRanges % (NT / 32) == 0, "every warp owns whole column ranges of a long row");
+                 int32_t *__restrict__ c_ci, T *__restrict__ c_v) {
   extern __shared__ __align__(16) unsigned char sm_num_bm[];
   __shared__ int red[33];
   __shared__ Entry<T> s_ent[kStageN];
@@ -634,19 +551,6 @@ __global__ void __launch_bounds__(NT, MINB)
   const uint32_t *src = bitmaps + (size_t)item.x * words;
   int32_t j_lo = a.arp[i], j_hi = a.arp[i + 1];
   if (parts > 1) part_range(a, i, part, parts, &j_lo, &j_hi);
-  // A entries listed per round of the long pass: as many (d, j) pairs as
-  // the staging area holds (it is free until the other products start)
-  constexpr int kListCap = (int)(sizeof(Entry<T>) * kStageN / sizeof(int2));
-  constexpr int kListN = kListCap < NT ? kListCap : NT;
-  // Long rows of B in the medium and small classes only.  Measured on R-MAT
-  // A*A, scale 16: the long pass ran the medium class 12% faster and the
-  // large class (one block per SM, whose barriers no other block covers)
-  // 11% slower.
-  const int32_t *lmap = MINB > 1 ? lr.map : nullptr;
-  // the first round's long-row indexes, loaded alongside the bitmap
-  int32_t d_next = -1;
-  if (lmap != nullptr && threadIdx.x < kListN && j_lo + (int32_t)threadIdx.x < j_hi)
-    d_next = __ldg(lmap + __ldg(a.aci + j_lo + threadIdx.x));
   const int per = (words + blockDim.x - 1) / blockDim.x;
   const int w0 = threadIdx.x * per, w1 = min(words, w0 + per);
   int local = 0;
@@ -669,35 +573,8 @@ __global__ void __launch_bounds__(NT, MINB)
     const uint2 word = rk[c >> 5];
     return (int)word.y + __popc(word.x & ((1u << (c & 31)) - 1u)) - lo;
   };
-  // Long rows of B first, in rounds of kListN A entries: the block lists the
-  // round's long entries, the warps add their products without a block
-  // barrier (each owns its ranks), and a barrier ends the round.
-  if (lmap != nullptr) {
-    int2 *list = reinterpret_cast<int2 *>(s_ent);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int32_t jb = j_lo; jb < j_hi; jb += kListN) {
-      const int32_t d = d_next;
-      const unsigned m = __ballot_sync(0xffffffffu, d >= 0);
-      if (lane == 0) red[wid] = __popc(m);
-      __syncthreads();
-      int base = 0, nl = 0;
-#pragma unroll
-      for (int v = 0; v < NT / 32; ++v) {
-        const int c = red[v];
-        base += v < wid ? c : 0;
-        nl += c;
-      }
-      if (d >= 0) list[base + __popc(m & ((1u << lane) - 1u))] = make_int2(d, jb + (int32_t)threadIdx.x);
-      __syncthreads();
-      d_next = -1;
-      if (threadIdx.x < kListN && jb + kListN + (int32_t)threadIdx.x < j_hi)
-        d_next = __ldg(lmap + __ldg(a.aci + jb + kListN + threadIdx.x));
-      warp_long_pass<T, NT>(list, nl, (const T *)a.av, lr, vals, span, rank_of);
-      __syncthreads();
-    }
-  }
   block_row_products_long<kUN, true, false, T>(
-      j_lo, j_hi, a.G, a.aci, (const T *)a.av, a.brp, a.bci, (const T *)a.bv, (int32_t)a.k, a.err, lmap,
+      j_lo, j_hi, a.G, a.aci, (const T *)a.av, a.brp, a.bci, (const T *)a.bv, (int32_t)a.k, a.err, nullptr,
       Stage<T>{s_ent, &s_next, s_wsum},
       [&](const int32_t (&c)[kUN], const T (&av)[kUN], const T (&bv)[kUN], const bool (&ok)[kUN]) {
         int r[kUN];
@@ -926,7 +803,6 @@ cudaError_t launch_numeric_t(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_c
   cudaError_t e = cudaSuccess;
   const int64_t nbm = p->sym_count[kSymBitmapBin] + p->sym_count[kSymBitmapMidBin];
   if (p->a_compact) e = compact_a_values(p);
-  if (e == cudaSuccess && p->long_ready && p->bm_item_off[3] > 0) e = long_rows_values(p);
   if (e == cudaSuccess && nbm > 0 && p->bm_item_off[3] > 0) {
     // before the fork: every bitmap launch adds into the zeroed split rows
     KernelScope ks(p, "bm_zero_split");
@@ -969,7 +845,7 @@ cudaError_t launch_numeric_t(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_c
           KernelScope ks(p, cls == 0 ? "num_bitmap_s" : cls == 1 ? "num_bitmap_m" : "num_bitmap_l", st);
           kern<<<(unsigned)n, p->bm_threads[cls], smem, st>>>(
               a, p->perm + p->sym_off[kSymBitmapBin], p->bm_items + p->bm_item_off[cls], p->flop, p->bitmaps, p->bm_words,
-              (int)p->bm_cap[cls], c_rp, c_ci, c_v, long_rows(p));
+              (int)p->bm_cap[cls], c_rp, c_ci, c_v);
         }
         e = cudaGetLastError();
         break;

@@ -890,8 +890,6 @@ int plan_init(spgemm_plan_s **out, const spgemm_csr *A, const spgemm_csr *B, int
   if (p->long_min > 0) off = align_up(off + (size_t)p->n * 4, 256);
   const size_t o_lrow = off;
   if (p->long_min > 0) off = align_up(off + (size_t)p->long_cap * 4, 256);
-  const size_t o_lbase = off;
-  if (p->long_min > 0) off = align_up(off + (size_t)p->long_cap * 4, 256);
   e = cudaMallocAsync(&p->ws_fixed, off, p->stream);
   if (e != cudaSuccess) {
     p->ws_fixed = nullptr;
@@ -919,7 +917,6 @@ int plan_init(spgemm_plan_s **out, const spgemm_csr *A, const spgemm_csr *B, int
   if (p->long_min > 0) {
     p->lmap = (int32_t *)(base + o_lmap);
     p->lrow = (int32_t *)(base + o_lrow);
-    p->lbase = (int32_t *)(base + o_lbase);
   }
 
   *out = p;

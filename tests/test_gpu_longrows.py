@@ -1,8 +1,7 @@
 """GPU parity of two paths that change which entries the kernels visit, never
 the product: long rows of B taken whole inside bitmap rows of A (their
-column bitmaps ORed in the symbolic phase, their column-sorted copies read
-by column range in the numeric phase), and the compacted A that leaves out
-the stored a_ik whose row of B is empty.
+column bitmaps ORed in the symbolic phase), and the compacted A that leaves
+out the stored a_ik whose row of B is empty.
 
 Every case is compared with the CPU oracle element by element (int64
 bit-exact, FP within the stated tolerance), sorted and unsorted, and the
@@ -97,9 +96,10 @@ def test_long_rows_with_rank_windows_and_split_rows(dt, shape):
 
 
 @pytest.mark.parametrize("dt", ["f64", "i64"])
-def test_long_rows_with_repeated_columns_keep_the_atomic_path(dt):
+def test_long_rows_with_repeated_columns(dt):
     """Repeated columns inside a row of B (a precondition violation both sides
-    sum): such long rows are left to the atomic path, the others stay long."""
+    sum): the symbolic phase's bitmap OR counts such a column once, as the
+    hash tables do, and the numeric phase adds every product."""
     rng = np.random.default_rng(409)
     n, k = 300, 4000
     rows, cols = [], []
@@ -118,7 +118,7 @@ def test_long_rows_with_repeated_columns_keep_the_atomic_path(dt):
     A, B = typed(A, dt, 410), typed(B, dt, 411)
     for sorted_output in (True, False):
         C, st = product(A, B, DT[dt], sorted_output, {"long_row_min": 1})
-        assert st["long_rows"] == n                        # counted before the repeated ones are set aside
+        assert st["long_rows"] == n
         assert_matches_oracle(C, A, B, sorted_output)
 
 
