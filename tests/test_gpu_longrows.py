@@ -95,6 +95,30 @@ def test_long_rows_with_rank_windows_and_split_rows(dt, shape):
         assert_matches_oracle(C, A, B, sorted_output)
 
 
+@pytest.mark.parametrize("b_order", ["sorted", "shuffled"])
+def test_rank_windows_with_sorted_and_unsorted_rows_of_b(b_order):
+    """A heavy row of A whose output spans several rank windows, each window
+    reading every product and keeping those of its ranks, with B's rows
+    sorted by column and in shuffled order: both give the oracle's C."""
+    B = inputs.er_exact(3000, 40, seed=441, ncols=60000)      # row 0 of A: about 52K distinct columns
+    if b_order == "shuffled":
+        rng = np.random.default_rng(442)
+        ci, v = B.col_idx.copy(), B.vals.copy()
+        for k in range(B.nrows):
+            a, b = B.row_ptr[k], B.row_ptr[k + 1]
+            perm = rng.permutation(b - a)
+            ci[a:b], v[a:b] = ci[a:b][perm], v[a:b][perm]
+        B = CSR(B.nrows, B.ncols, B.row_ptr, ci, v)
+    rows = np.concatenate([np.zeros(3000, np.int64), [1, 1, 2]])
+    cols = np.concatenate([np.arange(3000), [5, 9, 7]])
+    rp, aci = inputs.from_coo(3, B.nrows, rows, cols)
+    A = CSR(3, B.nrows, rp, aci, np.random.default_rng(443).uniform(-1, 1, len(aci)))
+    for sorted_output in (True, False):
+        C, st = product(A, B, torch.float64, sorted_output, None)
+        assert st["num_bin_rows"][9] >= 2                               # large class: >= 2 rank windows
+        assert_matches_oracle(C, A, B, sorted_output)
+
+
 @pytest.mark.parametrize("dt", ["f64", "i64"])
 def test_long_rows_with_repeated_columns(dt):
     """Repeated columns inside a row of B (a precondition violation both sides
