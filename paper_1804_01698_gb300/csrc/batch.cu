@@ -7,9 +7,10 @@
 // A's columns by the rows of B before, B's columns by the columns of B
 // before, values copied), the regular plan runs the whole batch with the
 // same number of kernel launches and host synchronisations as one product,
-// and k_batch_unpack turns C's column indices back into each product's own
-// columns.  Product p's rows of C are rows row_off[p] .. row_off[p+1]-1 of
-// the packed C.
+// and the numeric kernels store each row's columns less its product's
+// column offset (cbase, written by k_batch_pack), so C holds every
+// product's own columns.  Product p's rows of C are rows row_off[p] ..
+// row_off[p+1]-1 of the packed C.
 #include <cstring>
 #include <new>
 #include <string>
@@ -96,7 +97,8 @@ __device__ __forceinline__ void pack_operand(const spgemm_csr &m, int64_t c, lon
 __global__ void __launch_bounds__(256)
     k_batch_pack(const BatchDev *__restrict__ d, int64_t nprod, int vsize, int32_t *__restrict__ arp,
                  int32_t *__restrict__ aci, unsigned char *__restrict__ av, int32_t *__restrict__ brp,
-                 int32_t *__restrict__ bci, unsigned char *__restrict__ bv, uint32_t *err) {
+                 int32_t *__restrict__ bci, unsigned char *__restrict__ bv, int32_t *__restrict__ cbase,
+                 uint32_t *err) {
   const int64_t blk = blockIdx.x;
   int64_t lo = 0, hi = nprod - 1;  // last product whose first chunk is <= blk
   while (lo < hi) {
@@ -113,27 +115,11 @@ __global__ void __launch_bounds__(256)
     pack_operand<uint32_t>(p.a, c, p.a_row, p.a_nnz, p.b_row, arp, aci, av, err);
     pack_operand<uint32_t>(p.b, c, p.b_row, p.b_nnz, p.b_col, brp, bci, bv, err);
   }
+  // the rows of C this product's rows of A produce store its own columns
+  const int64_t r0 = c * kPackChunk, r1 = r0 + kPackChunk < p.a.nrows ? r0 + kPackChunk : p.a.nrows;
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) cbase[p.a_row + r] = (int32_t)p.b_col;
 }
 
-// One warp per row of C: subtract the column offset of the row's product.
-__global__ void __launch_bounds__(256)
-    k_batch_unpack(const int32_t *__restrict__ c_rp, int32_t *__restrict__ c_ci, int64_t m,
-                   const long long *__restrict__ row_off, const long long *__restrict__ col_off, int64_t nprod,
-                   const uint32_t *abort) {
-  const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (row >= m) return;
-  // graph mode: C did not fit its pool, so neither its row pointers nor its columns are valid
-  if (abort && (*(volatile const uint32_t *)abort & (kErrOverflow | kErrCapacity))) return;
-  int64_t lo = 0, hi = nprod - 1;  // last product whose first row is <= row
-  while (lo < hi) {
-    const int64_t mid = (lo + hi + 1) >> 1;
-    if (row_off[mid] <= row) lo = mid;
-    else hi = mid - 1;
-  }
-  const int32_t off = (int32_t)col_off[lo];
-  for (int32_t j = c_rp[row] + lane; j < c_rp[row + 1]; j += 32) c_ci[j] -= off;
-}
 
 }  // namespace sg
 
@@ -148,6 +134,7 @@ struct spgemm_batch_s {
   int32_t *arp, *aci, *brp, *bci;
   void *av, *bv;
   long long *d_row_off, *d_col_off;
+  int32_t *cbase;           // per packed row: the column offset of its product (Args::col_base)
   uint32_t *d_err;
   std::vector<long long> row_off;  // host copy, nprod + 1
   int64_t m, k;
@@ -236,6 +223,8 @@ int batch_pack(spgemm_batch_s **out, int64_t nprod, const spgemm_csr *A, const s
   off = up256(off + 4);
   const size_t o_arp = off;
   off = up256(off + 4 * ((size_t)am + 1));
+  const size_t o_cbase = off;
+  off = up256(off + 4 * (size_t)am);
   const size_t o_aci = off;
   off = up256(off + 4 * (size_t)an);
   const size_t o_av = off;
@@ -258,6 +247,7 @@ int batch_pack(spgemm_batch_s **out, int64_t nprod, const spgemm_csr *A, const s
   b->d_col_off = (long long *)(w + o_coff);
   b->d_err = (uint32_t *)(w + o_err);
   b->arp = (int32_t *)(w + o_arp);
+  b->cbase = (int32_t *)(w + o_cbase);
   b->aci = (int32_t *)(w + o_aci);
   b->av = w + o_av;
   b->brp = (int32_t *)(w + o_brp);
@@ -275,7 +265,7 @@ int batch_pack(spgemm_batch_s **out, int64_t nprod, const spgemm_csr *A, const s
   if (e == cudaSuccess) {
     k_batch_pack<<<(unsigned)chunks, 256, 0, b->stream>>>(d_desc, nprod, vsize, b->arp, b->aci,
                                                            (unsigned char *)b->av, b->brp, b->bci,
-                                                           (unsigned char *)b->bv, b->d_err);
+                                                           (unsigned char *)b->bv, b->cbase, b->d_err);
     e = cudaGetLastError();
   }
   uint32_t err = 0;
@@ -310,7 +300,7 @@ cudaError_t batch_repack(spgemm_batch_s *b, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   k_batch_pack<<<(unsigned)b->chunks, 256, 0, st>>>(b->d_desc, b->nprod, b->vsize, b->arp, b->aci,
                                                       (unsigned char *)b->av, b->brp, b->bci, (unsigned char *)b->bv,
-                                                      b->d_err);
+                                                      b->cbase, b->d_err);
   return cudaGetLastError();
 }
 
@@ -345,6 +335,7 @@ int spgemm_batch_create_tuned(spgemm_batch_t *out, int64_t nprod, const spgemm_c
   // a row of the packed C spans at most its own product's columns: the block
   // bins' sort window is sized from the widest product, not the packed k
   b->plan->span_cols = b->widest;
+  b->plan->col_base = b->cbase;
   b->state = 0;
   *out = b;
   return SPGEMM_OK;
@@ -366,16 +357,6 @@ int spgemm_batch_numeric(spgemm_batch_t b, const int32_t *c_row_ptr, int32_t *c_
   if (b->state != 1) return SPGEMM_ERR_BAD_STATE;
   int rc = spgemm_numeric(b->plan, c_row_ptr, c_col_idx, c_vals);
   if (rc != SPGEMM_OK) return rc;
-  if (b->m > 0 && c_col_idx) {
-    KernelScope ks(b->plan, "batch_unpack");
-    k_batch_unpack<<<(unsigned)((b->m + 7) / 8), 256, 0, b->stream>>>(c_row_ptr, c_col_idx, b->m, b->d_row_off,
-                                                                      b->d_col_off, b->nprod, nullptr);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) {
-      set_last_error(std::string("batch unpack: ") + cudaGetErrorString(e));
-      return SPGEMM_ERR_DEVICE;
-    }
-  }
   b->state = 2;
   return SPGEMM_OK;
 }
@@ -397,8 +378,9 @@ int spgemm_batch_destroy(spgemm_batch_t b) {
 // graph-mode plan (sized by a planning pass at creation: no host reads of
 // counts while it runs) and its pool for C.  The graph holds, for every
 // wave: the packing of its products, the flop pass, the symbolic bins, the
-// row_ptr scan, the numeric bins, the column unpacking and the copy of the
-// per-product entry counts and error words to pinned host memory.  A launch
+// row_ptr scan, the numeric bins (storing every product's own columns) and
+// the copy of the per-product entry counts and error words to pinned host
+// memory.  A launch
 // is one cudaGraphLaunch on the caller's stream, with no host
 // synchronisation until the caller waits for it; it recomputes every
 // product from the current contents of the operands, so new values, or a
@@ -621,15 +603,10 @@ int bgraph_capture(spgemm_bgraph_s *g) {
   cudaError_t el = cudaSuccess;
   for (size_t i = 0; i < g->waves.size() && e == cudaSuccess && el == cudaSuccess; ++i) {
     GraphWave &w = g->waves[i];
-    const int64_t np = w.p1 - w.p0, m = w.b->m;
+    const int64_t np = w.p1 - w.p0;
     const uint32_t *abort = &w.plan->dc->err;
     el = sg::batch_repack(w.b, cap);
     if (el == cudaSuccess) el = sg::plan_enqueue_graph(w.plan, w.c_rp, w.c_ci, w.c_v);
-    if (el == cudaSuccess && m > 0) {
-      sg::k_batch_unpack<<<(unsigned)((m + 7) / 8), 256, 0, cap>>>(w.c_rp, w.c_ci, m, w.b->d_row_off,
-                                                                   w.b->d_col_off, np, abort);
-      el = cudaGetLastError();
-    }
     if (el == cudaSuccess) {
       sg::k_wave_prod_nnz<<<(unsigned)((np + 256) / 256), 256, 0, cap>>>(w.c_rp, w.b->d_row_off, np, abort,
                                                                           w.d_pnnz);
@@ -747,6 +724,7 @@ int spgemm_bgraph_create(spgemm_bgraph_t *out, int64_t nprod, const spgemm_csr *
     if (rc != SPGEMM_OK) break;
     caps[w].nnz_cap = std::min<int64_t>(INT32_MAX, (int64_t)((double)caps[w].nnz_cap * (1.0 + pool_slack)) + 1);
     rc = sg::plan_create_graph(&gw.plan, &pa, &pb, dtype, flags, st, tuning, caps[w]);
+    if (rc == SPGEMM_OK) gw.plan->col_base = gw.b->cbase;
     gw.nnz_cap = caps[w].nnz_cap;
     const size_t o_ci = up256((size_t)(gw.b->m + 1) * 4);
     const size_t o_v = o_ci + up256((size_t)gw.nnz_cap * 4);

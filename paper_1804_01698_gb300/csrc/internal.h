@@ -324,6 +324,10 @@ struct Args {
   // graph mode: the plan's error word; a numeric kernel returns at once when
   // it holds kErrOverflow or kErrCapacity (C would not fit its buffers)
   const uint32_t *abort = nullptr;
+  // per row of C, a column offset that the numeric kernels subtract from the
+  // columns they store (a packed batch's rows store their product's own
+  // columns); null: none
+  const int32_t *col_base = nullptr;
 };
 
 // A numeric kernel of a graph-mode plan skips its work when the symbolic
@@ -370,6 +374,7 @@ struct spgemm_plan_s {
   size_t long_ws_bytes;
   uint32_t *lbits;
   bool long_ready;       // built: the plan has bitmap rows and long rows
+  const int32_t *col_base;  // Args::col_base of the numeric phase (a packed batch's), or null
   // compacted A (entries selecting a non-empty row of B), walked by the
   // phases instead of A when it holds fewer than half of A's entries
   int32_t *kept;         // flop pass: per row, its stored a_ik whose row of B is not empty (fixed
@@ -497,8 +502,10 @@ cudaError_t compact_a_values(spgemm_plan_s *p);
 // Arguments of the phase kernels: the compacted A when the plan has one.
 inline Args phase_args(const spgemm_plan_s *p, uint32_t *err, int probe, unsigned long long *ctr) {
   const bool c = p->a_compact;
-  return Args{p->m, p->n, p->k, c ? p->karp : p->arp, c ? p->kaci : p->aci, p->brp, p->bci,
-              c ? (const void *)p->kav : p->av, p->bv, p->G, err, probe, ctr};
+  Args a{p->m, p->n, p->k, c ? p->karp : p->arp, c ? p->kaci : p->aci, p->brp, p->bci,
+         c ? (const void *)p->kav : p->av, p->bv, p->G, err, probe, ctr};
+  a.col_base = p->col_base;
+  return a;
 }
 
 // Blocks of a bin launch: one per row (or per 4 rows) of the count the host

@@ -149,7 +149,7 @@ __device__ __forceinline__ void reg_stage(uint32_t (&k)[R], T (&v)[R], int kk) {
 // stored.
 template <typename T, int R>
 __device__ __forceinline__ void warp_sort_store(const int32_t *keys, const T *vals, int nnz, int lane,
-                                                int32_t *__restrict__ out_ci, T *__restrict__ out_v) {
+                                                int32_t *__restrict__ out_ci, T *__restrict__ out_v, int32_t cb) {
   uint32_t k[R];
   T v[R];
 #pragma unroll
@@ -189,7 +189,7 @@ __device__ __forceinline__ void warp_sort_store(const int32_t *keys, const T *va
   for (int r = 0; r < R; ++r) {
     const int e = r * 32 + lane;
     if (e < nnz) {
-      out_ci[e] = (int32_t)k[r];
+      out_ci[e] = (int32_t)k[r] - cb;
       out_v[e] = v[r];
     }
   }
@@ -211,7 +211,7 @@ constexpr int kMaxBucket = 32;
 
 template <typename T, int S>
 __device__ __forceinline__ bool bucket_sort_store(int32_t *keys, T *vals, int cnt, int lane,
-                                                  int32_t *__restrict__ out_ci, T *__restrict__ out_v) {
+                                                  int32_t *__restrict__ out_ci, T *__restrict__ out_v, int32_t cb) {
   static_assert(S >= 64, "warp tables hold at least 64 slots");
   int32_t *bcnt = keys + S / 2;
   int32_t *grp = reinterpret_cast<int32_t *>(vals + S / 2);
@@ -264,7 +264,7 @@ __device__ __forceinline__ bool bucket_sort_store(int32_t *keys, T *vals, int cn
     const int b1 = bcnt[b];
     int r = b > 0 ? bcnt[b - 1] : 0;
     for (int t = r; t < b1; ++t) r += keys[grp[t]] < c;
-    out_ci[r] = c;
+    out_ci[r] = c - cb;
     out_v[r] = vals[e];
   }
   return true;
@@ -288,6 +288,7 @@ __device__ __forceinline__ void num_warp_row(const Args &a, int32_t i, int32_t *
   __syncwarp();
   const int32_t rp = c_rp[i];
   const int32_t nnz = c_rp[i + 1] - rp;
+  const int32_t cb = a.col_base ? a.col_base[i] : 0;
   if (sorted) {
     // Compact the occupied slots to the front (in place: chunk by chunk, every
     // lane reads its slot before any lane writes, and a chunk only writes
@@ -309,11 +310,11 @@ __device__ __forceinline__ void num_warp_row(const Args &a, int32_t i, int32_t *
       __syncwarp();
     }
     const int cnt = min(base, nnz);
-    if (cnt <= 32) warp_sort_store<T, 1>(keys, vals, cnt, lane, c_ci + rp, c_v + rp);
-    else if (cnt <= S / 2 && bucket_sort_store<T, S>(keys, vals, cnt, lane, c_ci + rp, c_v + rp)) {
-    } else if (cnt <= 64) warp_sort_store<T, 2>(keys, vals, cnt, lane, c_ci + rp, c_v + rp);
-    else if (cnt <= 128) warp_sort_store<T, 4>(keys, vals, cnt, lane, c_ci + rp, c_v + rp);
-    else if (cnt <= 256) warp_sort_store<T, 8>(keys, vals, cnt, lane, c_ci + rp, c_v + rp);
+    if (cnt <= 32) warp_sort_store<T, 1>(keys, vals, cnt, lane, c_ci + rp, c_v + rp, cb);
+    else if (cnt <= S / 2 && bucket_sort_store<T, S>(keys, vals, cnt, lane, c_ci + rp, c_v + rp, cb)) {
+    } else if (cnt <= 64) warp_sort_store<T, 2>(keys, vals, cnt, lane, c_ci + rp, c_v + rp, cb);
+    else if (cnt <= 128) warp_sort_store<T, 4>(keys, vals, cnt, lane, c_ci + rp, c_v + rp, cb);
+    else if (cnt <= 256) warp_sort_store<T, 8>(keys, vals, cnt, lane, c_ci + rp, c_v + rp, cb);
     else {
       // longer rows: the same network in shared memory (measured faster here)
       int P = 512;
@@ -322,7 +323,7 @@ __device__ __forceinline__ void num_warp_row(const Args &a, int32_t i, int32_t *
       __syncwarp();
       bitonic_sort(reinterpret_cast<uint32_t *>(keys), vals, P, lane, 32, [] { __syncwarp(); });
       for (int r = lane; r < cnt; r += 32) {
-        c_ci[rp + r] = keys[r];
+        c_ci[rp + r] = keys[r] - cb;
         c_v[rp + r] = vals[r];
       }
     }
@@ -336,7 +337,7 @@ __device__ __forceinline__ void num_warp_row(const Args &a, int32_t i, int32_t *
       const unsigned m = __ballot_sync(0xffffffffu, occ);
       const int pos = base + __popc(m & ((1u << lane) - 1u));
       if (occ && pos < nnz) {
-        c_ci[rp + pos] = kk;
+        c_ci[rp + pos] = kk - cb;
         c_v[rp + pos] = vals[s];
       }
       base += __popc(m);
@@ -398,10 +399,11 @@ __device__ __forceinline__ void num_block_row(const Args &a, int32_t i, const in
   __syncthreads();
   const int32_t rp = c_rp[i];
   const int32_t nnz = c_rp[i + 1] - rp;
+  const int32_t cb = a.col_base ? a.col_base[i] : 0;
   if (sort_mode == 1) {
     bitonic_sort(reinterpret_cast<uint32_t *>(keys), vals, S, (int)threadIdx.x, (int)blockDim.x, [] { __syncthreads(); });
     for (int r = threadIdx.x; r < nnz; r += blockDim.x) {
-      c_ci[rp + r] = keys[r];
+      c_ci[rp + r] = keys[r] - cb;
       c_v[rp + r] = vals[r];
     }
   } else if (sort_mode == 2) {
@@ -448,7 +450,7 @@ __device__ __forceinline__ void num_block_row(const Args &a, int32_t i, const in
           const int o = kk - base;
           const int r = pre[o >> 5] + __popc(bm[o >> 5] & ((1u << (o & 31)) - 1u));
           if (r < nnz) {
-            c_ci[rp + r] = kk;
+            c_ci[rp + r] = kk - cb;
             c_v[rp + r] = vals[s];
           }
         }
@@ -458,7 +460,7 @@ __device__ __forceinline__ void num_block_row(const Args &a, int32_t i, const in
       bitonic_sort(reinterpret_cast<uint32_t *>(keys), vals, S, (int)threadIdx.x, (int)blockDim.x,
                    [] { __syncthreads(); });
       for (int r = threadIdx.x; r < nnz; r += blockDim.x) {
-        c_ci[rp + r] = keys[r];
+        c_ci[rp + r] = keys[r] - cb;
         c_v[rp + r] = vals[r];
       }
     }
@@ -474,7 +476,7 @@ __device__ __forceinline__ void num_block_row(const Args &a, int32_t i, const in
       base = __shfl_sync(0xffffffffu, base, 0);
       const int pos = base + __popc(m & ((1u << lane) - 1u));
       if (occ && pos < nnz) {
-        c_ci[rp + pos] = kk;
+        c_ci[rp + pos] = kk - cb;
         c_v[rp + pos] = vals[s];
       }
     }
@@ -546,6 +548,7 @@ __global__ void __launch_bounds__(NT, MINB)
   const bool agg = flop[i] >= kAggregateMinRatio * (c_rp[i + 1] - c_rp[i]);
   const int32_t rp = c_rp[i];
   const int32_t nnz = c_rp[i + 1] - rp;
+  const int32_t cb = a.col_base ? a.col_base[i] : 0;
   const int32_t lo = item.y * cap;
   const int32_t hi = min(nnz, lo + cap);
   const uint32_t *src = bitmaps + (size_t)item.x * words;
@@ -635,7 +638,7 @@ __global__ void __launch_bounds__(NT, MINB)
         if (r >= lo && r < hi) cols[r - lo] = w * 32 + __ffs(bits) - 1;
     }
     __syncthreads();
-    for (int r = threadIdx.x; r < hi - lo; r += blockDim.x) c_ci[rp + lo + r] = cols[r];
+    for (int r = threadIdx.x; r < hi - lo; r += blockDim.x) c_ci[rp + lo + r] = cols[r] - cb;
   }
   if (threadIdx.x == 0 && tot != nnz) raise_err(a.err, kErrProbe);
 }
@@ -676,6 +679,7 @@ __global__ void __launch_bounds__(1024, 1)
     __syncthreads();
     const int32_t rp = c_rp[i];
     const int32_t nnz = c_rp[i + 1] - rp;
+    const int32_t cb = a.col_base ? a.col_base[i] : 0;
     if (!sorted) {
       for (int64_t s0 = (int64_t)warp * 32; s0 < S; s0 += (int64_t)nw * 32) {
         const int64_t s = s0 + lane;
@@ -687,7 +691,7 @@ __global__ void __launch_bounds__(1024, 1)
         base = __shfl_sync(0xffffffffu, base, 0);
         const int pos = base + __popc(m & ((1u << lane) - 1u));
         if (occ && pos < nnz) {
-          c_ci[rp + pos] = kk;
+          c_ci[rp + pos] = kk - cb;
           c_v[rp + pos] = vals[s];
         }
       }
@@ -726,7 +730,7 @@ __global__ void __launch_bounds__(1024, 1)
             const int32_t o = (int32_t)(kk - c0);
             const int rr = base + pre[o >> 5] + __popc(bm[o >> 5] & ((1u << (o & 31)) - 1u));
             if (rr < nnz) {
-              c_ci[rp + rr] = kk;
+              c_ci[rp + rr] = kk - cb;
               c_v[rp + rr] = vals[s];
             }
           }
