@@ -133,41 +133,6 @@ template <> struct Val<double> {
   }
   static __device__ __forceinline__ void acc_global(double *p, double a, double b) { atomicAdd(p, a * b); }
   static __device__ __forceinline__ void add_global(double *p, double v) { atomicAdd(p, v); }
-  // U accumulations vals[r[u]] += a[u]*b[u] (where act[u]) at once: every
-  // slot is read, every FMA done and every compare-and-swap issued before
-  // any result is checked, so the U dependent chains (load, FMA, CAS)
-  // overlap instead of running one after another; a failed swap (another
-  // thread, or an earlier u of this lane, changed the slot) retries with the
-  // value it found.
-  template <int U>
-  static __device__ __forceinline__ void acc_shared_batch(double *vals, const int (&r)[U], const double (&a)[U],
-                                                          const double (&b)[U], const bool (&act)[U], uint32_t *err) {
-    unsigned long long old[U];
-    bool pend[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      pend[u] = act[u];
-      old[u] = pend[u] ? *reinterpret_cast<volatile unsigned long long *>(vals + r[u]) : 0ull;
-    }
-    for (int it = 0; it < kMaxCasRetries; ++it) {
-      bool any = false;
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (pend[u]) {
-          const double nv = fma(a[u], b[u], __longlong_as_double((long long)old[u]));
-          const unsigned long long got = atomicCAS(reinterpret_cast<unsigned long long *>(vals + r[u]), old[u],
-                                                   (unsigned long long)__double_as_longlong(nv));
-          pend[u] = got != old[u];
-          old[u] = got;
-          any |= pend[u];
-        }
-      }
-      if (!any) return;
-    }
-    raise_err(err, kErrRetry);
-  }
-  // owner-only update (no other thread touches the slot): c + a*b
-  static __device__ __forceinline__ double mad(double c, double a, double b) { return fma(a, b, c); }
 };
 
 template <> struct Val<float> {
@@ -177,14 +142,6 @@ template <> struct Val<float> {
   }
   static __device__ __forceinline__ void acc_global(float *p, float a, float b) { atomicAdd(p, a * b); }
   static __device__ __forceinline__ void add_global(float *p, float v) { atomicAdd(p, v); }
-  template <int U>
-  static __device__ __forceinline__ void acc_shared_batch(float *vals, const int (&r)[U], const float (&a)[U],
-                                                          const float (&b)[U], const bool (&act)[U], uint32_t *) {
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (act[u]) atomicAdd(vals + r[u], a[u] * b[u]);
-  }
-  static __device__ __forceinline__ float mad(float c, float a, float b) { return fmaf(a, b, c); }
 };
 
 template <> struct Val<int64_t> {
@@ -198,20 +155,7 @@ template <> struct Val<int64_t> {
   static __device__ __forceinline__ void add_global(int64_t *p, int64_t v) {
     atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
   }
-  template <int U>
-  static __device__ __forceinline__ void acc_shared_batch(int64_t *vals, const int (&r)[U], const int64_t (&a)[U],
-                                                          const int64_t (&b)[U], const bool (&act)[U], uint32_t *) {
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (act[u])
-        atomicAdd(reinterpret_cast<unsigned long long *>(vals + r[u]),
-                  (unsigned long long)a[u] * (unsigned long long)b[u]);
-  }
-  static __device__ __forceinline__ int64_t mad(int64_t c, int64_t a, int64_t b) {
-    return (int64_t)((unsigned long long)c + (unsigned long long)a * (unsigned long long)b);
-  }
 };
-
 
 // ---------------------------------------------------------------------------
 // Reductions and scans.
@@ -506,9 +450,10 @@ __device__ __forceinline__ void block_row_products(int64_t a0, int64_t a1, int G
 
 // Processes flat products [p0, p1) like process_flat, but hands each lane's
 // U gathered products to fb(c, a, b, ok) at once (ok[u]: product u exists
-// and its column is inside B).  Software-pipelined: the loads of the next U
-// products are issued before fb works on the current ones, so their L2
-// latency overlaps fb's shared-memory updates.
+// and its column is inside B).  With PIPE, software-pipelined: the loads of
+// the next U products are issued before fb works on the current ones, so
+// their L2 latency overlaps fb's shared-memory updates (a second set of
+// registers, which kernels at 32-40 registers a thread would spill).
 template <int U, bool NEED_VAL, bool PIPE, typename T, typename FB>
 __device__ __forceinline__ void process_flat_batch(const Entry<T> *ent, int n, int p0, int p1, int G, int lig,
                                                    const int32_t *__restrict__ bci, const T *__restrict__ bv,
