@@ -157,6 +157,28 @@ template <> struct Val<int64_t> {
   }
 };
 
+// After every block of a grid has added into count[0..nbins): the last block
+// to finish writes off[b] = count[0] + ... + count[b-1] for b = 0..nbins
+// (ticket: a counter zeroed before the launch).  Every thread of every block
+// calls it, at the end of the kernel.
+__device__ __forceinline__ void last_block_offsets(const unsigned long long *count, int nbins, long long *off,
+                                                   unsigned int *ticket) {
+  __shared__ bool s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
+    __threadfence();
+    long long run = 0;
+    for (int b = 0; b < nbins; ++b) {
+      off[b] = run;
+      run += (long long)*reinterpret_cast<const volatile unsigned long long *>(count + b);
+    }
+    off[nbins] = run;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Reductions and scans.
 template <typename T> __device__ __forceinline__ T warp_sum(T v) {

@@ -190,6 +190,8 @@ struct DevCounters {
   // each spread over kProbeSlots counters to limit atomic contention
   unsigned long long probe_stats[4][kProbeSlots];
   unsigned int err;
+  unsigned int sym_ticket;  // blocks of k_row_bin done (the last one writes the symbolic bin offsets)
+  unsigned int num_ticket;  // the same for k_num_classify and the numeric bin offsets
   unsigned int pad;
 };
 
@@ -219,9 +221,31 @@ constexpr int kKeptListCap = 128;
 // A malformed row (its range outside [0, m + nnz]) writes nothing, and the
 // walk clamps what it reads.  Also zeroes flop[] and kept[] (null: not) for
 // the atomics of the walk that follows.
+// Long rows of B (see longrows.cu): row k of B is long when it has at least
+// long_min entries; long rows get an index d (lmap[k] = d, lrow[d] = k).
+struct LongMark {
+  const int32_t *brp;
+  int64_t n, nnz_b, long_min, cap;
+  int32_t *lmap, *lrow;
+};
+__device__ __forceinline__ void long_mark_row(const LongMark &lm, int64_t k, DevCounters *dc) {
+  const int64_t b0 = lm.brp[k], b1 = lm.brp[k + 1];
+  int32_t d = -1;
+  // a malformed row is never long (the flop pass reports it when A selects it)
+  if (0 <= b0 && b0 <= b1 && b1 <= lm.nnz_b && b1 - b0 >= lm.long_min) {
+    const unsigned long long idx = atomicAdd(&dc->n_long, 1ull);
+    if ((int64_t)idx < lm.cap) {
+      d = (int32_t)idx;
+      lm.lrow[d] = (int32_t)k;
+      atomicAdd(&dc->long_tot, (unsigned long long)(b1 - b0));
+    }
+  }
+  lm.lmap[k] = d;
+}
+
 __global__ void __launch_bounds__(256)
     k_merge_starts(const int32_t *__restrict__ rp, int64_t m, int64_t nnz, int64_t tiles, long long *__restrict__ starts,
-                   int64_t *__restrict__ flop, int32_t *__restrict__ kept);
+                   int64_t *__restrict__ flop, int32_t *__restrict__ kept, LongMark lm, DevCounters *dc);
 
 // One tile of kMergeTile items of a merge-path walk over A, one block (tile
 // blockIdx.x, its start and end read from starts[]): the
@@ -486,9 +510,8 @@ inline bool use_side_streams(const spgemm_plan_s *p) {
 cudaStream_t bin_stream(spgemm_plan_s *p, int i);
 cudaError_t join(spgemm_plan_s *p);
 
-// Long rows: marks the long rows of B (before the flop pass's counters are
-// read), then builds their bitmaps (when bitmap rows exist).
-cudaError_t long_rows_mark(spgemm_plan_s *p);
+// Long rows: marked with the flop pass (k_merge_starts), then their bitmaps
+// are built (when bitmap rows exist).
 cudaError_t long_rows_build(spgemm_plan_s *p);
 inline LongRows long_rows(const spgemm_plan_s *p) {
   if (!p->long_ready) return LongRows{nullptr, nullptr};

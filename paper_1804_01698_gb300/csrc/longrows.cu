@@ -9,8 +9,8 @@
 // paper's symbolic phase defines (Fig. "Hash_SpGEMM"): the distinct columns
 // of the row's products.
 //
-//   k_long_mark     per row of B: long (entries >= long_min) or not; long
-//                   rows get an index d
+//   long_mark_row   per row of B (in the flop pass's k_merge_starts): long
+//                   (entries >= long_min) or not; long rows get an index d
 //   k_long_build    per long row: its column bitmap
 #include <algorithm>
 
@@ -18,25 +18,6 @@
 #include "internal.h"
 
 namespace sg {
-
-__global__ void __launch_bounds__(256)
-    k_long_mark(const int32_t *__restrict__ brp, int64_t n, int64_t nnz_b, int64_t long_min, int64_t cap,
-                int32_t *__restrict__ lmap, int32_t *__restrict__ lrow, DevCounters *dc) {
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  const int64_t b0 = brp[k], b1 = brp[k + 1];
-  int32_t d = -1;
-  // a malformed row is never long (the flop pass reports it when A selects it)
-  if (0 <= b0 && b0 <= b1 && b1 <= nnz_b && b1 - b0 >= long_min) {
-    const unsigned long long idx = atomicAdd(&dc->n_long, 1ull);
-    if ((int64_t)idx < cap) {
-      d = (int32_t)idx;
-      lrow[d] = (int32_t)k;
-      atomicAdd(&dc->long_tot, (unsigned long long)(b1 - b0));
-    }
-  }
-  lmap[k] = d;
-}
 
 // One block per long row d: its column bitmap.  Columns outside B raise
 // kErrCsr and are left out.
@@ -60,14 +41,6 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   uint32_t *bw = bits + (size_t)d * words;
   for (int w = threadIdx.x; w < words; w += blockDim.x) bw[w] = sm_lbits[w];
-}
-
-cudaError_t long_rows_mark(spgemm_plan_s *p) {
-  if (p->long_min <= 0 || p->n == 0) return cudaSuccess;
-  KernelScope ks(p, "long_mark");
-  k_long_mark<<<(unsigned)((p->n + 255) / 256), 256, 0, p->stream>>>(p->brp, p->n, p->nnz_b, p->long_min,
-                                                                      p->long_cap, p->lmap, p->lrow, p->dc);
-  return cudaGetLastError();
 }
 
 cudaError_t long_rows_build(spgemm_plan_s *p) {

@@ -96,9 +96,12 @@ __device__ __forceinline__ int num_bin_of(int64_t nnz, const HashCaps &caps) {
 
 __global__ void __launch_bounds__(256)
     k_merge_starts(const int32_t *__restrict__ rp, int64_t m, int64_t nnz, int64_t tiles, long long *__restrict__ starts,
-                   int64_t *__restrict__ flop, int32_t *__restrict__ kept) {
+                   int64_t *__restrict__ flop, int32_t *__restrict__ kept, LongMark lm, DevCounters *dc) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // long rows of B (long_min 0: none), in the same launch
+  if (lm.long_min > 0)
+    for (int64_t k = t0; k < lm.n; k += stride) long_mark_row(lm, k, dc);
   for (int64_t i = t0; i < m; i += stride) {
     if (flop) {
       flop[i] = 0;
@@ -173,7 +176,8 @@ __global__ void __launch_bounds__(kMergeThreads)
 // decreasing; a row that breaks it raises kErrCsr and counts no flop.
 __global__ void __launch_bounds__(256)
     k_row_bin(Args a, int64_t nnz_a, int64_t bitmap_min, HashCaps caps, int64_t gcap, int64_t *__restrict__ flop,
-              uint8_t *__restrict__ rbin, int32_t *__restrict__ nnz_row, DevCounters *dc) {
+              uint8_t *__restrict__ rbin, int32_t *__restrict__ nnz_row, long long *__restrict__ sym_off,
+              DevCounters *dc) {
   __shared__ unsigned int hist[kNumSymBins];
   __shared__ unsigned long long hflop[kNumSymBins];
   __shared__ unsigned long long s_tot, s_max, s_maxg, s_extra;
@@ -235,18 +239,10 @@ __global__ void __launch_bounds__(256)
     if (s_max) atomicMax(&dc->max_flop, s_max);
     if (s_maxg) atomicMax(&dc->max_bound_global, s_maxg);
   }
+  // the symbolic bins' offsets on the device (bin kernels find their rows by them)
+  last_block_offsets(dc->sym_count, kNumSymBins, sym_off, &dc->sym_ticket);
 }
 
-// off[b] = rows of bins below b (off[0] = 0 .. off[nbins]), on the device.
-__global__ void k_bin_offsets(const unsigned long long *__restrict__ count, int nbins, long long *__restrict__ off) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  long long run = 0;
-  for (int b = 0; b < nbins; ++b) {
-    off[b] = run;
-    run += (long long)count[b];
-  }
-  off[nbins] = run;
-}
 
 // Rows i with bin_of[i] != 255 go to perm[off[bin] + arbitrary rank].
 __global__ void __launch_bounds__(256)
@@ -330,7 +326,7 @@ __global__ void __launch_bounds__(kScanThreads)
 __global__ void __launch_bounds__(256)
     k_num_classify(const int32_t *__restrict__ nnz_row, const uint8_t *__restrict__ rbin,
                    const int64_t *__restrict__ flop, int64_t m, HashCaps caps, int64_t gcap,
-                   uint8_t *__restrict__ rbin2, DevCounters *dc) {
+                   uint8_t *__restrict__ rbin2, long long *__restrict__ num_off, DevCounters *dc) {
   __shared__ unsigned int hist[kNumNumBins];
   __shared__ unsigned long long hflop[kNumNumBins];
   __shared__ unsigned long long s_maxg;
@@ -361,6 +357,7 @@ __global__ void __launch_bounds__(256)
   if (threadIdx.x < kNumNumBins && hist[threadIdx.x]) atomicAdd(&dc->num_count[threadIdx.x], hist[threadIdx.x]);
   if (threadIdx.x < kNumNumBins && hflop[threadIdx.x]) atomicAdd(&dc->num_flop[threadIdx.x], hflop[threadIdx.x]);
   if (threadIdx.x == 0 && s_maxg) atomicMax(&dc->max_nnz_global, s_maxg);
+  last_block_offsets(dc->num_count, kNumNumBins, num_off, &dc->num_ticket);
 }
 
 struct BmCaps {
@@ -936,20 +933,18 @@ cudaError_t enqueue_flop(spgemm_plan_s *p) {
                            : p->tune_bm_min > 0                 ? p->tune_bm_min
                                                                 : bitmap_min_bound(p->k);
     const int64_t tiles = (m + p->nnz_a + kMergeTile - 1) / kMergeTile;
-    k_merge_starts<<<(unsigned)std::min<int64_t>((m + 255) / 256, 8 * (int64_t)sm_count()), 256, 0, p->stream>>>(
-        p->arp, m, p->nnz_a, tiles, p->mstarts, p->flop, p->kept);
+    const LongMark lm{p->brp, p->n, p->nnz_b, p->long_min, p->long_cap, p->lmap, p->lrow};
+    const int64_t items = std::max<int64_t>(m, p->long_min > 0 ? p->n : 0);
+    k_merge_starts<<<(unsigned)std::min<int64_t>((items + 255) / 256, 8 * (int64_t)sm_count()), 256, 0, p->stream>>>(
+        p->arp, m, p->nnz_a, tiles, p->mstarts, p->flop, p->kept, lm, p->dc);
     k_row_flop<<<(unsigned)tiles, kMergeThreads, 0, p->stream>>>(a, p->nnz_a, p->nnz_b, p->mstarts, p->flop, p->kept,
                                                                  p->klist, p->klist_n, p->dc);
     const int64_t rb = std::min<int64_t>((m + 255) / 256, 8 * (int64_t)sm_count());
     k_row_bin<<<(unsigned)rb, 256, 0, p->stream>>>(a, p->nnz_a, bm_min, p->caps, p->gcap_bound, p->flop, p->rbin,
-                                                   p->nnz_row, p->dc);
+                                                   p->nnz_row, p->d_sym_off, p->dc);
   }
   if (e == cudaSuccess) e = cudaGetLastError();
-  if (e == cudaSuccess) {
-    k_bin_offsets<<<1, 32, 0, p->stream>>>(p->dc->sym_count, kNumSymBins, p->d_sym_off);
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess) e = long_rows_mark(p);
+  if (e == cudaSuccess) e = cudaGetLastError();
   return e;
 }
 
@@ -980,8 +975,7 @@ cudaError_t enqueue_symbolic(spgemm_plan_s *p, int32_t *c_row_ptr) {
     {
       KernelScope ks(p, "num_classify");
       k_num_classify<<<(unsigned)((m + 255) / 256), 256, 0, p->stream>>>(p->nnz_row, p->rbin, p->flop, m, p->caps,
-                                                                         p->gcap_nnz, p->rbin2, p->dc);
-      k_bin_offsets<<<1, 32, 0, p->stream>>>(p->dc->num_count, kNumNumBins, p->d_num_off);
+                                                                         p->gcap_nnz, p->rbin2, p->d_num_off, p->dc);
     }
     const int64_t nbm = p->sym_count[kSymBitmapBin] + p->sym_count[kSymBitmapMidBin];
     if (nbm > 0) {
