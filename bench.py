@@ -192,6 +192,24 @@ def kernel_units(name: str, stats: dict) -> tuple[int, str]:
     return 0, "other"
 
 
+def planning_bytes(name: str, A, B, stats: dict) -> tuple[int, str]:
+    """Algorithmic bytes of one launch of a planning scope: what it must read
+    and write at least once.  row_flop (the flop pass): A's row pointers and
+    columns, the pair of B row pointers each stored a_ik selects, and the
+    per-row flop, count and bin; compact_a: the per-row counts, the compacted
+    row pointers, and per kept entry its column read and its column and
+    source written."""
+    m, nnz_a = A.nrows, A.nnz
+    if name.startswith("row_flop"):
+        b = (m + 1) * 4 + nnz_a * 4 + nnz_a * 8 + m * (8 + 4 + 1)
+        return b, f"{b} B: A's structure, 8 B of B's row pointers per stored a_ik, 13 B per row"
+    if name.startswith("compact_a"):
+        kept = int(stats.get("nnz_a_walked", nnz_a))
+        b = m * 4 + (m + 1) * 4 + kept * 12
+        return b, f"{b} B: per-row counts and row pointers, 12 B per kept a_ik"
+    return 0, "no algorithmic byte count for this step"
+
+
 # ---------------------------------------------------------------------------- reference arm
 
 def workload_config(name: str, A, B, flop: int, nnz_c: int, sorted_output: bool, replicas: int) -> dict:
@@ -888,6 +906,12 @@ def main() -> int:
                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz x 2",
                     "work_per_launch": f"{units_per_launch:.0f} multiply-adds (FP64 FMA)"}
+    elif phase == "other":
+        # a planning step: its algorithmic bytes (per launch of its scope)
+        bytes_l, what = planning_bytes(dom_name, A, B, stats)
+        achieved_b = bytes_l / (dom_ms * 1e-3) / 1e9
+        roofline = {"kernel": dom_name, "bound": "hbm", "achieved": achieved_b, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved_b / hbm_peak, "peak_source": hbm_src, "work_per_launch": what}
     else:
         # bytes that kernel must move: the B entries it reads once per product
         # are L2 hits; its HBM share is bounded by its output and input rows.
