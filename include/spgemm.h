@@ -225,6 +225,21 @@ SPGEMM_API int spgemm_symbolic(spgemm_plan_t plan, int32_t *c_row_ptr, int64_t *
 SPGEMM_API int spgemm_numeric(spgemm_plan_t plan, const int32_t *c_row_ptr, int32_t *c_col_idx, void *c_vals);
 
 /*
+ * The numeric phase of rows row_begin .. row_end-1 of C only.  Rows of C
+ * are independent (Fig. "RowWise_SpGEMM"), so calls over disjoint row
+ * ranges that cover 0 .. m-1 give the result of one spgemm_numeric, and
+ * each call writes nothing but its own rows' entries, c_row_ptr[row_begin]
+ * .. c_row_ptr[row_end]-1 of c_col_idx and c_vals.  It lets a caller move
+ * finished rows elsewhere (to the host, say) while later rows are computed.
+ * Arguments, buffers, state and asynchrony as for spgemm_numeric; every
+ * call launches the kernels of all bins, whose blocks skip the rows outside
+ * the range.  SPGEMM_ERR_INVALID_ARGUMENT unless 0 <= row_begin <= row_end
+ * <= m; an empty range does nothing.
+ */
+SPGEMM_API int spgemm_numeric_rows(spgemm_plan_t plan, int64_t row_begin, int64_t row_end, const int32_t *c_row_ptr,
+                                   int32_t *c_col_idx, void *c_vals);
+
+/*
  * The numeric phase as a CUDA graph.  The first call after a spgemm_numeric
  * on this plan captures the plan's numeric kernels (all bins, their side
  * streams and joins) for these output buffers and launches the graph; later
@@ -378,20 +393,19 @@ SPGEMM_API int spgemm_bgraph_destroy(spgemm_bgraph_t graph);
  * symbolic phase: row_ptr ((m+1)*4 bytes), col_idx (nnz*4) and vals
  * (nnz*sizeof(value)); the caller owns what it returns, also on error.
  *
- * The call copies A and B to the device, runs the flop pass and splits A's
- * rows into `row_blocks` contiguous blocks by flop (the partition of
- * Sec. 4.1, Fig. "RowsToThreads", steps 1-2), block r taking a share of the
- * flop proportional to 2^min(r, 6): the first block, whose numeric phase
- * no copy hides, is small, and each later block's numeric phase fits under
- * the copy of the block before it.  Every block is
- * a product of its own (one plan each).  The symbolic phases of all blocks
- * give nnz(C); C is then allocated through `host_alloc`, and the numeric
- * phases run block after block on `stream` while a second stream copies
- * each finished block's columns and values to the host, so the copy of
- * block b overlaps the numeric phase of block b+1.  The result is the same
- * for every row_blocks.  row_blocks <= 0 picks a default (3 blocks from
- * 2^26 flop, else 1: every block is a product of its own and costs a plan
- * and a symbolic phase); it is capped at m.  flags as for
+ * The call copies A and B to the device and runs the flop pass and the
+ * symbolic phase of the whole product (one plan), which give C's row
+ * pointers and nnz(C); C is then allocated through `host_alloc`.  The rows
+ * are split into `row_blocks` contiguous blocks by C's entries (the
+ * partition of Sec. 4.1, Fig. "RowsToThreads", steps 1-2), block r taking
+ * a share proportional to 2^min(r, 6): the first block, whose numeric
+ * phase no copy hides, is small, and each later block's numeric phase fits
+ * under the copy of the block before it.  The numeric phase runs block
+ * after block on `stream` (spgemm_numeric_rows) while a second stream
+ * copies each finished block's columns and values to the host, so the copy
+ * of block b overlaps the numeric phase of block b+1.  The result is the
+ * same for every row_blocks.  row_blocks <= 0 picks a default (4 blocks
+ * from 2^26 flop, else 1); it is capped at m.  flags as for
  * spgemm_plan_create, without SPGEMM_TIMING.
  *
  * Returns when C is complete in host memory.  The device memory it used is

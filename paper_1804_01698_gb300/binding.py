@@ -99,7 +99,7 @@ EXPORTED = ("spgemm_plan_create", "spgemm_symbolic", "spgemm_numeric", "spgemm_p
             "spgemm_batch_numeric", "spgemm_batch_destroy", "spgemm_plan_create_tuned", "spgemm_batch_create_tuned",
             "spgemm_numeric_graph", "spgemm_host", "spgemm_bgraph_create", "spgemm_bgraph_launch",
             "spgemm_bgraph_wait", "spgemm_bgraph_product_nnz", "spgemm_bgraph_product_copy", "spgemm_bgraph_info",
-            "spgemm_bgraph_destroy")
+            "spgemm_bgraph_destroy", "spgemm_numeric_rows")
 
 
 def library_path() -> str:
@@ -124,6 +124,7 @@ def library():
     lib.spgemm_symbolic.argtypes = [P, P, ctypes.POINTER(I64)]
     lib.spgemm_numeric.argtypes = [P, P, P, P]
     lib.spgemm_numeric_graph.argtypes = [P, P, P, P]
+    lib.spgemm_numeric_rows.argtypes = [P, I64, I64, P, P, P]
     lib.spgemm_plan_destroy.argtypes = [P]
     lib.spgemm_plan_workspace_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
     lib.spgemm_plan_stats.argtypes = [P, ctypes.POINTER(Stats)]
@@ -325,6 +326,19 @@ class Plan:
                                            c_vals.data_ptr() if self.nnz_c else None), "spgemm_numeric")
         c.after(self.c_row_ptr, c_col_idx, c_vals)
         return DeviceCSR(self.A.nrows, self.B.ncols, self.c_row_ptr, c_col_idx, c_vals)
+
+    def numeric_rows(self, row_begin: int, row_end: int, C: DeviceCSR) -> DeviceCSR:
+        """Numeric phase of rows row_begin .. row_end-1 only, into C's buffers
+        (from an earlier numeric() or allocated for nnz_c entries); every other
+        row's entries are left as they are."""
+        c = _Caller(self.stream)
+        c.before()
+        with torch.cuda.device(self.device):
+            _check(self.lib.spgemm_numeric_rows(self.handle, row_begin, row_end, self.c_row_ptr.data_ptr(),
+                                                C.col_idx.data_ptr() if self.nnz_c else None,
+                                                C.vals.data_ptr() if self.nnz_c else None), "spgemm_numeric_rows")
+        c.after(C.col_idx, C.vals)
+        return C
 
     def numeric_graph(self, C: DeviceCSR) -> DeviceCSR:
         """Numeric phase again into C's buffers through a CUDA graph (captured

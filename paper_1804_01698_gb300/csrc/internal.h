@@ -354,7 +354,13 @@ struct Args {
   // columns they store (a packed batch's rows store their product's own
   // columns); null: none
   const int32_t *col_base = nullptr;
+  // numeric phase: only rows row_lo <= i < row_hi of C are computed and
+  // written (spgemm_numeric_rows); the symbolic phase takes every row
+  int32_t row_lo = 0, row_hi = INT32_MAX;
 };
+
+// Row i is inside the numeric phase's row range.
+__device__ __forceinline__ bool in_rows(const Args &a, int32_t i) { return i >= a.row_lo && i < a.row_hi; }
 
 // A numeric kernel of a graph-mode plan skips its work when the symbolic
 // phase found that C does not fit the planned buffers.
@@ -401,6 +407,7 @@ struct spgemm_plan_s {
   uint32_t *lbits;
   bool long_ready;       // built: the plan has bitmap rows and long rows
   const int32_t *col_base;  // Args::col_base of the numeric phase (a packed batch's), or null
+  int32_t row_lo = 0, row_hi = INT32_MAX;  // Args::row_lo / row_hi of the numeric kernels (spgemm_numeric_rows)
   // compacted A (entries selecting a non-empty row of B), walked by the
   // phases instead of A when it holds fewer than half of A's entries
   int32_t *kept;         // flop pass: per row, its stored a_ik whose row of B is not empty (fixed
@@ -530,6 +537,8 @@ inline Args phase_args(const spgemm_plan_s *p, uint32_t *err, int probe, unsigne
   Args a{p->m, p->n, p->k, c ? p->karp : p->arp, c ? p->kaci : p->aci, p->brp, p->bci,
          c ? (const void *)p->kav : p->av, p->bv, p->G, err, probe, ctr};
   a.col_base = p->col_base;
+  a.row_lo = p->row_lo;
+  a.row_hi = p->row_hi;
   return a;
 }
 

@@ -360,7 +360,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 8)
   T *vals = reinterpret_cast<T *>(sm_num_warp + (size_t)kWarpsPerBlock * S * sizeof(int32_t)) + warp * S;
   // one warp per row (no block barrier below)
   for (int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + warp; w < nrows; w += (int64_t)gridDim.x * kWarpsPerBlock) {
-    num_warp_row<T, S>(a, br.perm[o0 + w], keys, vals, s_ent[warp], &s_next[warp], c_rp, c_ci, c_v, sorted, lane);
+    const int32_t i = br.perm[o0 + w];
+    if (!in_rows(a, i)) continue;
+    num_warp_row<T, S>(a, i, keys, vals, s_ent[warp], &s_next[warp], c_rp, c_ci, c_v, sorted, lane);
     __syncwarp();
   }
 }
@@ -492,7 +494,9 @@ __global__ void __launch_bounds__(num_block_threads<S>(), num_block_min_blocks<S
   if (aborted(a)) return;
   const long long o0 = br.off[br.bin], nrows = br.off[br.bin + 1] - o0;
   for (int64_t b = blockIdx.x; b < nrows; b += gridDim.x) {  // one block per row
-    num_block_row<T, S>(a, br.perm[o0 + b], c_rp, c_ci, c_v, sort_mode, words);
+    const int32_t i = br.perm[o0 + b];
+    if (!in_rows(a, i)) continue;
+    num_block_row<T, S>(a, i, c_rp, c_ci, c_v, sort_mode, words);
     __syncthreads();  // the shared table is cleared for the next row
   }
 }
@@ -502,10 +506,11 @@ __global__ void __launch_bounds__(num_block_threads<S>(), num_block_min_blocks<S
 template <typename T>
 __global__ void __launch_bounds__(256)
     k_bm_zero_split(const int32_t *__restrict__ bm_rows, int64_t nbm, const int64_t *__restrict__ flop,
-                    const int32_t *__restrict__ c_rp, T *__restrict__ c_v) {
+                    const int32_t *__restrict__ c_rp, T *__restrict__ c_v, int32_t row_lo, int32_t row_hi) {
   const int64_t t = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   if (t >= nbm) return;
   const int32_t i = bm_rows[t];
+  if (i < row_lo || i >= row_hi) return;
   const int32_t rp = c_rp[i], nnz = c_rp[i + 1] - rp;
   if (bm_split_parts(flop[i], nnz) < 2) return;
   for (int32_t r = threadIdx.x & 31; r < nnz; r += 32) c_v[rp + r] = T(0);
@@ -544,6 +549,7 @@ __global__ void __launch_bounds__(NT, MINB)
   uint2 *rk = reinterpret_cast<uint2 *>(sm_num_bm + (size_t)cap * sizeof(T));
   const int4 item = items[blockIdx.x];
   const int32_t i = bm_rows[item.x];
+  if (!in_rows(a, i)) return;
   const int part = item.z, parts = item.w;
   const bool agg = flop[i] >= kAggregateMinRatio * (c_rp[i + 1] - c_rp[i]);
   const int32_t rp = c_rp[i];
@@ -666,6 +672,7 @@ __global__ void __launch_bounds__(1024, 1)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const long long o0 = br.off[br.bin], nrows = br.off[br.bin + 1] - o0;
   for (int64_t r = blockIdx.x; r < nrows; r += gridDim.x) {
+    if (!in_rows(a, br.perm[o0 + r])) continue;
     for (int64_t s = threadIdx.x; s < S; s += blockDim.x) {
       keys[s] = kEmpty;
       vals[s] = T(0);
@@ -811,7 +818,7 @@ cudaError_t launch_numeric_t(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_c
     // before the fork: every bitmap launch adds into the zeroed split rows
     KernelScope ks(p, "bm_zero_split");
     k_bm_zero_split<T><<<(unsigned)((nbm + 7) / 8), 256, 0, p->stream>>>(p->perm + p->sym_off[kSymBitmapBin], nbm,
-                                                                         p->flop, c_rp, c_v);
+                                                                         p->flop, c_rp, c_v, a.row_lo, a.row_hi);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && concurrent) e = fork(p);

@@ -1149,22 +1149,41 @@ static cudaError_t numeric_launch(spgemm_plan_t p, const int32_t *c_row_ptr, int
   }
 }
 
-int spgemm_numeric(spgemm_plan_t p, const int32_t *c_row_ptr, int32_t *c_col_idx, void *c_vals) {
-  NvtxRange nvtx("spgemm_numeric");
-  if (!p || !c_row_ptr) return SPGEMM_ERR_INVALID_ARGUMENT;
+// The numeric kernels of rows [lo, hi) (every row: 0, INT32_MAX).
+static int numeric_run(spgemm_plan_t p, const int32_t *c_row_ptr, int32_t *c_col_idx, void *c_vals, int32_t lo,
+                       int32_t hi) {
   if (p->state != 1 && p->state != 2) return SPGEMM_ERR_BAD_STATE;
   if (p->nnz_c > 0 && (!c_col_idx || !c_vals)) return SPGEMM_ERR_INVALID_ARGUMENT;
   g_last_error.clear();
   if (p->nnz_c > 0) {
+    if (lo >= hi) return SPGEMM_OK;  // no rows: the plan's state is unchanged
     if (p->state == 1) {
       const int rc = numeric_prepare(p);
       if (rc != SPGEMM_OK) return rc;
+      p->state = 2;
     }
+    p->row_lo = lo;
+    p->row_hi = hi;
     const cudaError_t e = numeric_launch(p, c_row_ptr, c_col_idx, c_vals);
+    p->row_lo = 0;
+    p->row_hi = INT32_MAX;
     if (e != cudaSuccess) return fail_cuda(e, "numeric kernels");
   }
   p->state = 2;
   return SPGEMM_OK;
+}
+
+int spgemm_numeric(spgemm_plan_t p, const int32_t *c_row_ptr, int32_t *c_col_idx, void *c_vals) {
+  NvtxRange nvtx("spgemm_numeric");
+  if (!p || !c_row_ptr) return SPGEMM_ERR_INVALID_ARGUMENT;
+  return numeric_run(p, c_row_ptr, c_col_idx, c_vals, 0, INT32_MAX);
+}
+
+int spgemm_numeric_rows(spgemm_plan_t p, int64_t row_begin, int64_t row_end, const int32_t *c_row_ptr,
+                        int32_t *c_col_idx, void *c_vals) {
+  NvtxRange nvtx("spgemm_numeric_rows");
+  if (!p || !c_row_ptr || row_begin < 0 || row_end < row_begin || row_end > p->m) return SPGEMM_ERR_INVALID_ARGUMENT;
+  return numeric_run(p, c_row_ptr, c_col_idx, c_vals, (int32_t)row_begin, (int32_t)row_end);
 }
 
 int spgemm_numeric_graph(spgemm_plan_t p, const int32_t *c_row_ptr, int32_t *c_col_idx, void *c_vals) {
