@@ -397,14 +397,16 @@ SPGEMM_API int spgemm_bgraph_destroy(spgemm_bgraph_t graph);
  * symbolic phase of the whole product (one plan), which give C's row
  * pointers and nnz(C); C is then allocated through `host_alloc`.  The rows
  * are split into `row_blocks` contiguous blocks by C's entries (the
- * partition of Sec. 4.1, Fig. "RowsToThreads", steps 1-2), block r taking
- * a share proportional to 2^min(r, 6): the first block, whose numeric
- * phase no copy hides, is small, and each later block's numeric phase fits
- * under the copy of the block before it.  The numeric phase runs block
- * after block on `stream` (spgemm_numeric_rows) while a second stream
- * copies each finished block's columns and values to the host, so the copy
- * of block b overlaps the numeric phase of block b+1.  The result is the
- * same for every row_blocks.  row_blocks <= 0 picks a default (4 blocks
+ * partition of Sec. 4.1, Fig. "RowsToThreads", steps 1-2), the r-th block
+ * to run taking a share proportional to 2^min(r, 6): the first block, whose
+ * numeric phase no copy hides, is small, and each later block's numeric
+ * phase fits under the copy of the block before it.  The blocks are cut
+ * from the first row on or from the last row back, whichever gives the
+ * first block more rows (more rows keep more of the GPU busy).  The
+ * numeric phase runs block after block on `stream` (spgemm_numeric_rows)
+ * while a second stream copies each finished block's columns and values to
+ * the host, so the copy of block b overlaps the numeric phase of block b+1.  The result is the
+ * same for every row_blocks.  row_blocks <= 0 picks a default (6 blocks
  * from 2^26 flop, else 1); it is capped at m.  flags as for
  * spgemm_plan_create, without SPGEMM_TIMING.
  *

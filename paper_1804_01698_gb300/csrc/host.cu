@@ -39,30 +39,41 @@ bool host_desc_ok(const spgemm_csr *c) {
 
 size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
-// First row of each of `parts` row blocks; offs[parts] = m.  Block r gets
-// a share of C's entries proportional to 2^min(r, kShareCap): the shares
-// double, so the first block, whose numeric phase no copy hides, is small,
-// and every later block's numeric phase (at most twice the entries of the
-// block before it) still runs under the copy of the block before it, which
-// moves C about 3 times slower than the numeric phase writes it on GB300.
-// Block r starts at the first row whose entry offset c_rp[row] reaches its
-// cumulative share (a lower-bound search over C's row pointers, as
-// Fig. "RowsToThreads" searches the flop prefix for threads); empty blocks
-// are possible and skipped by the caller.
+// The row blocks, in the order they run: `parts` contiguous ranges of
+// rows, the r-th to run holding a share of C's entries proportional to
+// 2^min(r, kShareCap).  The shares double, so the first block, whose numeric
+// phase no copy hides, is small, and every later block's numeric phase (at
+// most twice the entries of the block before it) still runs under the copy
+// of the block before it, which moves C about 3 times slower than the
+// numeric phase writes it on GB300.  The blocks are cut from the first row
+// on or from the last row back, whichever gives the first block more rows:
+// a first block of a few heavy rows keeps few SMs busy (in R-MAT the
+// heaviest rows come first).  Each cut is a lower-bound search of its
+// cumulative share over C's row pointers (as Fig. "RowsToThreads" searches
+// the flop prefix for threads); empty blocks are possible and skipped by
+// the caller.
 constexpr int kShareCap = 6;
 
-std::vector<int64_t> nnz_blocks(const int32_t *c_rp, int64_t m, int parts) {
+std::vector<std::pair<int64_t, int64_t>> nnz_blocks(const int32_t *c_rp, int64_t m, int parts) {
   const __int128 total = c_rp[m];
   std::vector<__int128> cum(parts + 1, 0);  // cumulative shares
   for (int r = 0; r < parts; ++r) cum[r + 1] = cum[r] + ((__int128)1 << std::min(r, kShareCap));
-  std::vector<int64_t> offs(parts + 1, 0);
-  offs[parts] = m;
+  std::vector<int64_t> fwd(parts + 1, 0), bwd(parts + 1, 0);  // boundaries in running order
+  fwd[0] = 0;
+  fwd[parts] = m;
+  bwd[0] = m;
+  bwd[parts] = 0;
   for (int r = 1; r < parts; ++r) {
-    const int64_t target = (int64_t)(total * cum[r] / cum[parts]);
-    offs[r] = std::lower_bound(c_rp, c_rp + m, (int32_t)target) - c_rp;
-    offs[r] = std::max(offs[r], offs[r - 1]);
+    const int64_t head = (int64_t)(total * cum[r] / cum[parts]);
+    fwd[r] = std::max<int64_t>(std::lower_bound(c_rp, c_rp + m, (int32_t)head) - c_rp, fwd[r - 1]);
+    const int64_t tail = (int64_t)(total - total * cum[r] / cum[parts]);
+    bwd[r] = std::min<int64_t>(std::lower_bound(c_rp, c_rp + m, (int32_t)tail) - c_rp, bwd[r - 1]);
   }
-  return offs;
+  std::vector<std::pair<int64_t, int64_t>> out;
+  const bool from_end = parts > 1 && bwd[0] - bwd[1] > fwd[1] - fwd[0];
+  for (int r = 0; r < parts; ++r)
+    out.push_back(from_end ? std::make_pair(bwd[r + 1], bwd[r]) : std::make_pair(fwd[r], fwd[r + 1]));
+  return out;
 }
 
 // Everything the call holds on the device, released in one place.
@@ -84,7 +95,7 @@ struct HostCall {
   }
 };
 
-constexpr int kDefaultRowBlocks = 4;
+constexpr int kDefaultRowBlocks = 6;
 constexpr int64_t kRowBlockMinFlop = int64_t(1) << 26;
 
 }  // namespace
@@ -221,10 +232,10 @@ static int spgemm_host_impl(const spgemm_csr *A, const spgemm_csr *B, int dtype,
   if (e != cudaSuccess) return cuda_fail(e, "copying row pointers");
   int parts = row_blocks > 0 ? row_blocks : (ws.total_flop >= kRowBlockMinFlop ? kDefaultRowBlocks : 1);
   parts = (int)std::max<int64_t>(1, std::min<int64_t>(parts, m));
-  const std::vector<int64_t> offs = m > 0 ? nnz_blocks(h_rp, m, parts) : std::vector<int64_t>{0, 0};
-  std::vector<std::pair<int64_t, int64_t>> blocks;  // [r0, r1) of every non-empty block
-  for (size_t r = 0; r + 1 < offs.size(); ++r)
-    if (offs[r + 1] > offs[r]) blocks.push_back({offs[r], offs[r + 1]});
+  std::vector<std::pair<int64_t, int64_t>> blocks;  // [r0, r1) of every non-empty block, in running order
+  if (m > 0)
+    for (const auto &bk : nnz_blocks(h_rp, m, parts))
+      if (bk.second > bk.first) blocks.push_back(bk);
   const int nb = (int)blocks.size();
 
   // 4. C's columns and values: on the host through the callback, and on the device
