@@ -123,6 +123,21 @@ __host__ __device__ inline int bm_split_parts(long long flop, long long nnz) {
   if (parts > kSplitMaxParts) parts = kSplitMaxParts;
   return (int)parts;
 }
+// Numeric bitmap work items run heaviest first within each class: an item
+// of a row with flop f in `parts` parts walks f / parts products, and the
+// items go to kBmBuckets buckets by that weight (bucket 0: 2^20 products
+// and more, each next bucket half the weight of the one before, the last
+// every lighter item).  Blocks start roughly in index order, so a heavy
+// item no longer starts near the end of the launch while the other SMs run
+// dry (longest processing time first, bucketed).
+constexpr int kBmBuckets = 8;
+__host__ __device__ inline int bm_bucket_of(long long flop, int parts) {
+  const long long w = flop / (parts > 0 ? parts : 1);
+  int lg = 0;
+  while (lg < 62 && (w >> (lg + 1)) > 0) ++lg;  // floor(log2(w)), 0 for w <= 1
+  const int b = 20 - lg;
+  return b < 0 ? 0 : b > kBmBuckets - 1 ? kBmBuckets - 1 : b;
+}
 // Long rows of B.  Inside bitmap rows of A, the symbolic phase does not take
 // the products of a row k of B with at least long_row_min entries one by
 // one: it ORs k's saved column bitmap into the row's bitmap.  The rule below
@@ -180,7 +195,8 @@ struct DevCounters {
   unsigned long long nnz_c;
   unsigned long long max_nnz_global;    // largest nnz in the numeric global bin
   unsigned long long bm_items[3];       // numeric bitmap work items per class (small, medium, large)
-  unsigned long long bm_cursor[3];
+  unsigned long long bm_bucket[3][kBmBuckets];  // the same per weight bucket (bm_bucket_of)
+  unsigned long long bm_cursor[3][kBmBuckets];
   unsigned long long bm_flop[3];        // flop of the rows of each class
   unsigned long long sym_split_extra;   // heavy symbolic bitmap rows: parts beyond one per row
   unsigned long long sym_item_cursor;
@@ -466,6 +482,7 @@ struct spgemm_plan_s {
   int64_t bm_cap[3];      // values per numeric bitmap window, per class
   int bm_threads[3];       // threads per block, per class
   int64_t bm_item_off[4];  // item offsets per class
+  int64_t bm_bucket_off[3][sg::kBmBuckets];  // item offsets per class and weight bucket
   int32_t launches;
   const int32_t *c_rp;
 

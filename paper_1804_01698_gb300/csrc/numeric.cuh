@@ -501,19 +501,22 @@ __global__ void __launch_bounds__(num_block_threads<S>(), num_block_min_blocks<S
   }
 }
 
-// Values of the split bitmap rows start at zero: their parts add into them.
-// One warp per bitmap row.
+// Values that the bitmap kernels add into C start at zero: every value of a
+// split row (its parts add theirs), and the ranks from cap_l on of a row
+// with more entries than the large class's shared array holds (their
+// products are added straight into C).  One warp per bitmap row.
 template <typename T>
 __global__ void __launch_bounds__(256)
     k_bm_zero_split(const int32_t *__restrict__ bm_rows, int64_t nbm, const int64_t *__restrict__ flop,
-                    const int32_t *__restrict__ c_rp, T *__restrict__ c_v, int32_t row_lo, int32_t row_hi) {
+                    const int32_t *__restrict__ c_rp, T *__restrict__ c_v, int32_t row_lo, int32_t row_hi,
+                    int64_t cap_l) {
   const int64_t t = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   if (t >= nbm) return;
   const int32_t i = bm_rows[t];
   if (i < row_lo || i >= row_hi) return;
   const int32_t rp = c_rp[i], nnz = c_rp[i + 1] - rp;
-  if (bm_split_parts(flop[i], nnz) < 2) return;
-  for (int32_t r = threadIdx.x & 31; r < nnz; r += 32) c_v[rp + r] = T(0);
+  const int32_t z0 = bm_split_parts(flop[i], nnz) >= 2 ? 0 : nnz > cap_l ? (int32_t)cap_l : nnz;
+  for (int32_t r = z0 + (threadIdx.x & 31); r < nnz; r += 32) c_v[rp + r] = T(0);
 }
 
 // Rows whose flop is at least kAggregateMinRatio times their output size
@@ -527,10 +530,13 @@ constexpr long long kAggregateMinRatio = 32;
 
 // Heavy rows with a saved column bitmap.  Item (t, wdw, part, parts): bitmap
 // t of the symbolic bitmap bin (row bm_rows[t]), output ranks
-// [wdw*cap, (wdw+1)*cap), products of the part'th of `parts` ranges of the
-// row's stored a_ik.  A row in one part stores its values; a split row's
-// parts add theirs into C (zeroed by k_bm_zero_split) and part 0 stores
-// the columns.
+// [wdw*cap, (wdw+1)*cap) in shared memory, products of the part'th of
+// `parts` ranges of the row's stored a_ik.  A row in one part stores its
+// values; a split row's parts add theirs into C (zeroed by k_bm_zero_split)
+// and part 0 stores the columns.  The items of a row with more than cap
+// entries (window 0) add the products of ranks from cap on straight into C
+// (zeroed there by k_bm_zero_split) with global atomics, and part 0 stores
+// every column of the row.
 // Every product goes through compare-and-swap accumulation (f64) or atomic
 // adds into the rank-indexed values.
 template <typename T, int NT, int MINB>
@@ -557,6 +563,9 @@ __global__ void __launch_bounds__(NT, MINB)
   const int32_t cb = a.col_base ? a.col_base[i] : 0;
   const int32_t lo = item.y * cap;
   const int32_t hi = min(nnz, lo + cap);
+  // ranks [hi, nnz) are added straight into C (rows with more than cap entries)
+  const bool ovf = lo == 0 && hi < nnz;
+  T *const c_row = c_v + rp;
   const uint32_t *src = bitmaps + (size_t)item.x * words;
   int32_t j_lo = a.arp[i], j_hi = a.arp[i + 1];
   if (parts > 1) part_range(a, i, part, parts, &j_lo, &j_hi);
@@ -592,6 +601,7 @@ __global__ void __launch_bounds__(NT, MINB)
         for (int u = 0; u < kUN; ++u) {
           r[u] = ok[u] ? rank_of(c[u]) : -1;
           act[u] = ok[u] && (unsigned)r[u] < (unsigned)span;
+          if (ovf && ok[u] && r[u] >= span && r[u] < nnz) Val<T>::acc_global(c_row + r[u], av[u], bv[u]);
         }
         if (!agg) {
           // one product after another (measured: issuing the kUN swaps together
@@ -636,12 +646,16 @@ __global__ void __launch_bounds__(NT, MINB)
   if (part == 0) {
     __syncthreads();
     int32_t *cols = reinterpret_cast<int32_t *>(vals);
+    const int32_t top = ovf ? nnz : hi;  // ranks [hi, top) go straight to C
     for (int w = threadIdx.x; w < words; w += blockDim.x) {
       const uint2 wd = rk[w];
       int r = (int)wd.y;
-      if (r >= hi || r + __popc(wd.x) <= lo) continue;
-      for (unsigned bits = wd.x; bits != 0u; bits &= bits - 1u, ++r)
-        if (r >= lo && r < hi) cols[r - lo] = w * 32 + __ffs(bits) - 1;
+      if (r >= top || r + __popc(wd.x) <= lo) continue;
+      for (unsigned bits = wd.x; bits != 0u; bits &= bits - 1u, ++r) {
+        const int32_t col = w * 32 + __ffs(bits) - 1;
+        if (r >= lo && r < hi) cols[r - lo] = col;
+        else if (r >= hi && r < top) c_ci[rp + r] = col - cb;
+      }
     }
     __syncthreads();
     for (int r = threadIdx.x; r < hi - lo; r += blockDim.x) c_ci[rp + lo + r] = cols[r] - cb;
@@ -817,8 +831,8 @@ cudaError_t launch_numeric_t(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_c
   if (e == cudaSuccess && nbm > 0 && p->bm_item_off[3] > 0) {
     // before the fork: every bitmap launch adds into the zeroed split rows
     KernelScope ks(p, "bm_zero_split");
-    k_bm_zero_split<T><<<(unsigned)((nbm + 7) / 8), 256, 0, p->stream>>>(p->perm + p->sym_off[kSymBitmapBin], nbm,
-                                                                         p->flop, c_rp, c_v, a.row_lo, a.row_hi);
+    k_bm_zero_split<T><<<(unsigned)((nbm + 7) / 8), 256, 0, p->stream>>>(
+        p->perm + p->sym_off[kSymBitmapBin], nbm, p->flop, c_rp, c_v, a.row_lo, a.row_hi, p->bm_cap[2]);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && concurrent) e = fork(p);

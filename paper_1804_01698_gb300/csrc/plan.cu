@@ -361,33 +361,29 @@ __global__ void __launch_bounds__(256)
 }
 
 struct BmCaps {
-  long long cap[3];  // small, medium, large (0 = class unused)
-  long long off[3];  // item offsets of the classes (fill only)
+  long long cap[3];              // small, medium, large (0 = class unused)
+  long long off[3][kBmBuckets];  // item offsets of the classes' weight buckets (fill only)
 };
 
-// Class of a bitmap row with nnz entries and its number of work items.
+// Class of a bitmap row with nnz entries and its number of rank windows
+// (work items per part): one, or none for an empty row.  A large-class row
+// with more entries than its shared array holds keeps the first cap[2]
+// ranks there and adds the products of its other ranks straight into C
+// (k_num_bitmap), so it needs no second window walking all its products
+// again.
 __device__ __forceinline__ int bm_class(long long nnz, const BmCaps &c, long long *windows) {
-  if (nnz <= 0) {
-    *windows = 0;
-    return 0;
-  }
-  if (nnz <= c.cap[0]) {
-    *windows = 1;
-    return 0;
-  }
-  if (nnz <= c.cap[1]) {
-    *windows = 1;
-    return 1;
-  }
-  *windows = (nnz + c.cap[2] - 1) / c.cap[2];
+  *windows = nnz > 0 ? 1 : 0;
+  if (nnz <= c.cap[0]) return 0;
+  if (nnz <= c.cap[1]) return 1;
   return 2;
 }
 
 __global__ void __launch_bounds__(256)
     k_bm_items_count(const int32_t *__restrict__ rows, int64_t n, const int32_t *__restrict__ nnz_row,
                      const int64_t *__restrict__ flop, BmCaps caps, DevCounters *dc) {
-  __shared__ unsigned long long s_items[3], s_flop[3];
+  __shared__ unsigned long long s_items[3], s_flop[3], s_bucket[3 * kBmBuckets];
   if (threadIdx.x < 3) s_items[threadIdx.x] = s_flop[threadIdx.x] = 0;
+  if (threadIdx.x < 3 * kBmBuckets) s_bucket[threadIdx.x] = 0;
   __syncthreads();
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) {
@@ -395,8 +391,10 @@ __global__ void __launch_bounds__(256)
     long long w;
     const int c = bm_class(nnz_row[i], caps, &w);
     if (w > 0) {
-      w *= bm_split_parts(flop[i], nnz_row[i]);
+      const int parts = bm_split_parts(flop[i], nnz_row[i]);
+      w *= parts;
       atomicAdd(&s_items[c], (unsigned long long)w);
+      atomicAdd(&s_bucket[c * kBmBuckets + bm_bucket_of(flop[i], parts)], (unsigned long long)w);
       atomicAdd(&s_flop[c], (unsigned long long)flop[i]);
     }
   }
@@ -405,6 +403,8 @@ __global__ void __launch_bounds__(256)
     atomicAdd(&dc->bm_items[threadIdx.x], s_items[threadIdx.x]);
     atomicAdd(&dc->bm_flop[threadIdx.x], s_flop[threadIdx.x]);
   }
+  if (threadIdx.x < 3 * kBmBuckets && s_bucket[threadIdx.x])
+    atomicAdd(&dc->bm_bucket[threadIdx.x / kBmBuckets][threadIdx.x % kBmBuckets], s_bucket[threadIdx.x]);
 }
 
 __global__ void __launch_bounds__(256)
@@ -417,7 +417,8 @@ __global__ void __launch_bounds__(256)
   const int c = bm_class(nnz_row[i], caps, &w);
   if (w == 0) return;
   const int parts = bm_split_parts(flop[i], nnz_row[i]);
-  const unsigned long long base = caps.off[c] + atomicAdd(&dc->bm_cursor[c], (unsigned long long)(w * parts));
+  const int q = bm_bucket_of(flop[i], parts);
+  const unsigned long long base = caps.off[c][q] + atomicAdd(&dc->bm_cursor[c][q], (unsigned long long)(w * parts));
   for (int q = 0; q < (int)w; ++q)
     for (int pt = 0; pt < parts; ++pt) items[base + (unsigned long long)q * parts + pt] = make_int4((int)t, q, pt, parts);
 }
@@ -980,7 +981,7 @@ cudaError_t enqueue_symbolic(spgemm_plan_s *p, int32_t *c_row_ptr) {
     const int64_t nbm = p->sym_count[kSymBitmapBin] + p->sym_count[kSymBitmapMidBin];
     if (nbm > 0) {
       KernelScope ks(p, "bm_items_count");
-      BmCaps caps{{p->bm_cap[0], p->bm_cap[1], p->bm_cap[2]}, {0, 0, 0}};
+      BmCaps caps{{p->bm_cap[0], p->bm_cap[1], p->bm_cap[2]}, {}};
       k_bm_items_count<<<(unsigned)((nbm + 255) / 256), 256, 0, p->stream>>>(
           p->perm + p->sym_off[kSymBitmapBin], nbm, p->nnz_row, p->flop, caps, p->dc);
     }
@@ -1103,6 +1104,11 @@ int spgemm_symbolic(spgemm_plan_t p, int32_t *c_row_ptr, int64_t *nnz_c) {
     p->num_count[bm_bins[c]] = (int64_t)p->hc->bm_items[c];
     p->num_flop[bm_bins[c]] = (int64_t)p->hc->bm_flop[c];
     p->bm_item_off[c + 1] = p->bm_item_off[c] + p->num_count[bm_bins[c]];
+    int64_t at = p->bm_item_off[c];  // heaviest bucket first
+    for (int q = 0; q < kBmBuckets; ++q) {
+      p->bm_bucket_off[c][q] = at;
+      at += (int64_t)p->hc->bm_bucket[c][q];
+    }
   }
   *nnz_c = p->nnz_c;
   p->c_rp = c_row_ptr;
@@ -1125,7 +1131,9 @@ static int numeric_prepare(spgemm_plan_t p) {
     }
     const int64_t nbm = p->sym_count[kSymBitmapBin] + p->sym_count[kSymBitmapMidBin];
     KernelScope ks(p, "bm_items_fill");
-    BmCaps caps{{p->bm_cap[0], p->bm_cap[1], p->bm_cap[2]}, {p->bm_item_off[0], p->bm_item_off[1], p->bm_item_off[2]}};
+    BmCaps caps{{p->bm_cap[0], p->bm_cap[1], p->bm_cap[2]}, {}};
+    for (int c = 0; c < 3; ++c)
+      for (int q = 0; q < kBmBuckets; ++q) caps.off[c][q] = p->bm_bucket_off[c][q];
     k_bm_items_fill<<<(unsigned)((nbm + 255) / 256), 256, 0, p->stream>>>(
         p->perm + p->sym_off[kSymBitmapBin], nbm, p->nnz_row, p->flop, caps, p->dc, p->bm_items);
   }

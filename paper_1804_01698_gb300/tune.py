@@ -92,8 +92,9 @@ def autotune_batch(As, Bs, sorted_output: bool = True, candidates=None, steps: i
 
 # Kernel kinds of the model: per phase, hash tables in a warp or a block,
 # column-bitmap rows in the library's size classes (symbolic: middle and
-# heavy bounds; numeric: small, medium and large value arrays, the large
-# ones split into rank windows), and global-memory tables.
+# heavy bounds; numeric: small, medium and large value arrays, the ranks of
+# a large row beyond its array added straight into C), and global-memory
+# tables.
 SYM_KINDS = ("warp", "block", "bitmap_mid", "bitmap_heavy", "global")
 NUM_KINDS = ("warp", "block", "bitmap_s", "bitmap_m", "bitmap_l", "global")
 HASH_SLOTS = [64 << t for t in range(9)]       # warp tables 64..1024, block tables 2048..16384
@@ -129,8 +130,9 @@ def bitmap_caps(k: int, value_size: int = 8) -> list[int]:
 def bin_kinds(flop, nnz, k: int, cand: dict, value_size: int = 8):
     """Kernel kind of every row in the symbolic phase (index into SYM_KINDS)
     and the numeric phase (NUM_KINDS) under a candidate tuning, -1 for rows
-    without work, and the rank windows of every numeric row (1 but for large
-    bitmap rows)."""
+    without work, and the work items of every numeric row per part (1: a
+    large bitmap row keeps its first ranks in shared memory and adds the
+    others straight into C, in the same pass)."""
     flop = np.asarray(flop, dtype=np.int64)
     nnz = np.asarray(nnz, dtype=np.int64)
     caps = np.array(hash_caps(cand.get("warp_load_pct", 0), cand.get("block_load_pct", 0)), dtype=np.int64)
@@ -147,7 +149,7 @@ def bin_kinds(flop, nnz, k: int, cand: dict, value_size: int = 8):
     bm_cls = np.where(nnz <= bc[0], 2, np.where(nnz <= bc[1], 3, 4))
     num = np.where(bitmap, bm_cls, num)
     num = np.where((nnz <= 0) & ~bitmap, -1, num)
-    windows = np.where(num == 4, -(-nnz // max(bc[2], 1)), 1)
+    windows = np.ones_like(nnz)
     return sym, num, windows
 
 

@@ -69,12 +69,12 @@ def test_long_rows_off_and_default_agree_with_the_oracle():
 
 
 @pytest.mark.parametrize("dt", ["f64", "i64"])
-@pytest.mark.parametrize("shape", ["windows", "parts"])
-def test_long_rows_with_rank_windows_and_split_rows(dt, shape):
-    """Every row of B long: a heavy row of A whose output exceeds one block's
-    rank window (several windows re-read the long rows), or whose flop is
-    large next to its output (split into parts adding into C)."""
-    if shape == "windows":
+@pytest.mark.parametrize("shape", ["wide", "parts"])
+def test_long_rows_with_wide_and_split_rows(dt, shape):
+    """Every row of B long: a heavy row of A whose output exceeds the large
+    class's shared array (the ranks beyond it go straight into C), or whose
+    flop is large next to its output (split into parts adding into C)."""
+    if shape == "wide":
         B = inputs.er_exact(2000, 40, seed=404, ncols=60000)   # row 0 of A: ~44K distinct columns
         rows = np.concatenate([np.zeros(2000, np.int64), [1, 1, 2]])
         cols = np.concatenate([np.arange(2000), [5, 9, 7]])
@@ -90,16 +90,18 @@ def test_long_rows_with_rank_windows_and_split_rows(dt, shape):
     for sorted_output in (True, False):
         C, st = product(A, B, DT[dt], sorted_output, {"long_row_min": 16})
         assert st["long_rows"] == B.nrows
-        if shape == "windows":
-            assert st["num_bin_rows"][9] >= 2                           # large class: >= 2 rank windows
+        if shape == "wide":
+            assert st["num_bin_rows"][9] == 1                           # large class: the one wide row
+            assert int((C.row_ptr[1:] - C.row_ptr[:-1]).max()) > 232448 // 8
         assert_matches_oracle(C, A, B, sorted_output)
 
 
 @pytest.mark.parametrize("b_order", ["sorted", "shuffled"])
-def test_rank_windows_with_sorted_and_unsorted_rows_of_b(b_order):
-    """A heavy row of A whose output spans several rank windows, each window
-    reading every product and keeping those of its ranks, with B's rows
-    sorted by column and in shuffled order: both give the oracle's C."""
+def test_wide_row_with_sorted_and_unsorted_rows_of_b(b_order):
+    """A heavy row of A whose output exceeds the large class's shared array
+    (its first ranks accumulate in shared memory, the others straight into
+    C), with B's rows sorted by column and in shuffled order: both give the
+    oracle's C."""
     B = inputs.er_exact(3000, 40, seed=441, ncols=60000)      # row 0 of A: about 52K distinct columns
     if b_order == "shuffled":
         rng = np.random.default_rng(442)
@@ -115,7 +117,8 @@ def test_rank_windows_with_sorted_and_unsorted_rows_of_b(b_order):
     A = CSR(3, B.nrows, rp, aci, np.random.default_rng(443).uniform(-1, 1, len(aci)))
     for sorted_output in (True, False):
         C, st = product(A, B, torch.float64, sorted_output, None)
-        assert st["num_bin_rows"][9] >= 2                               # large class: >= 2 rank windows
+        assert st["num_bin_rows"][9] == 1                               # large class: the one wide row
+        assert int((C.row_ptr[1:] - C.row_ptr[:-1]).max()) > 232448 // 8
         assert_matches_oracle(C, A, B, sorted_output)
 
 

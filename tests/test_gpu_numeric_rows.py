@@ -7,7 +7,7 @@ sentinels, computes a middle range first and checks it against the oracle
 row by row while every other row still holds its sentinels, then computes
 the rest and compares the whole product.  The inputs reach every kind of
 numeric kernel whose blocks skip rows outside the range: warp and block
-hash rows (R-MAT scale 13), bitmap rows with rank windows and parts, a
+hash rows (R-MAT scale 13), bitmap rows beyond the shared array, in parts, a
 bitmap row split over blocks whose values are zeroed before its parts add
 into them, and rows in global-memory tables."""
 from __future__ import annotations
@@ -56,7 +56,7 @@ def _global_rows():
 CASES = {
     "rmat13": lambda: (inputs.rmat(13, 16, seed=inputs.SEED_BASE + 81),) * 2,
     "split_row": _split_row_product,
-    "windows_and_parts": lambda: _heavy_rows(3, 2048, 65536, 1000, seed=72),
+    "wide_rows_in_parts": lambda: _heavy_rows(3, 2048, 65536, 1000, seed=72),
     "global_tables": _global_rows,
 }
 

@@ -4,7 +4,7 @@ Covers every step of the path: the row flop pass (bit-exact), the row bins
 (a permutation obeying the bin rule), the symbolic counts and row_ptr
 (bit-exact), the numeric values (int64 bit-exact, FP within tolerance) in
 sorted and unsorted mode, on the named workloads at full size and on edge
-cases: empty shapes, empty rows, heavy rows split into several windows,
+cases: empty shapes, empty rows, heavy rows beyond the shared array,
 heavy rows on global-memory tables, unsorted inputs, structural zeros,
 int64 wrap-around and invalid input.
 """
@@ -183,33 +183,47 @@ def _heavy_rows(nrows_a, entries, ncols_b, b_row_len, seed):
     return A, B
 
 
+# More FP64 values than any block's shared memory holds (227 KB per block).
+SHARED_F64_MAX = 232448 // 8
+
+
+def _widest_row(C) -> int:
+    return int((C.row_ptr[1:] - C.row_ptr[:-1]).max())
+
+
 @pytest.mark.parametrize("dt", ["f64", "i64"])
-def test_bitmap_rows_split_into_several_windows(dt):
+def test_bitmap_rows_beyond_the_shared_array(dt):
+    """Rows with more entries than the large class's shared array: the first
+    ranks accumulate in shared memory, the others straight into C."""
     dtype = DT[dt]
-    A, B = _heavy_rows(6, 64, 65536, 1000, seed=61)     # ~40k entries per row: 2 windows
+    A, B = _heavy_rows(6, 64, 65536, 1000, seed=61)     # ~40k entries per row
     if dt == "i64":
         A, B = int_valued(A, 62), int_valued(B, 63)
     A, B = host_vals(A, dtype), host_vals(B, dtype)
     C, st = gpu_product(A, B, dtype, True)
-    assert st["sym_bin_rows"][10] == 6 and st["num_bin_rows"][9] > 6
+    assert st["sym_bin_rows"][10] == 6 and st["num_bin_rows"][9] == 6   # one work item per row
+    assert _widest_row(C) > SHARED_F64_MAX
     assert_matches_oracle(C, A, B, True)
 
 
 @pytest.mark.parametrize("b_order", ["sorted", "shuffled"])
-@pytest.mark.parametrize("shape", ["windows", "windows_and_parts"])
-def test_windowed_rows_with_sorted_and_unsorted_b(b_order, shape):
-    """Rows split into rank windows, with column-sorted and with shuffled rows
-    of B, and rows split both into rank windows and into parts of their
-    stored a_ik (every window block of every part reads the part's products
-    and keeps those of its ranks)."""
-    if shape == "windows":
-        A, B = _heavy_rows(6, 64, 65536, 1000, seed=71)      # ~40k entries per row: 2 windows
+@pytest.mark.parametrize("shape", ["wide", "wide_and_parts"])
+def test_wide_rows_with_sorted_and_unsorted_b(b_order, shape):
+    """Rows beyond the shared array, with column-sorted and with shuffled rows
+    of B, and such rows also split into parts of their stored a_ik (every
+    part adds its shared ranks and its other ranks into C)."""
+    if shape == "wide":
+        A, B = _heavy_rows(6, 64, 65536, 1000, seed=71)      # ~40k entries per row
     else:
-        A, B = _heavy_rows(2, 2048, 65536, 1000, seed=72)    # ~65k entries, 2M flop: windows and parts
+        A, B = _heavy_rows(2, 2048, 65536, 1000, seed=72)    # ~65k entries, 2M flop: also parts
     if b_order == "shuffled":
         B = inputs.shuffle_rows(B, seed=73)
     C, st = gpu_product(A, B, torch.float64, True)
-    assert st["num_bin_rows"][9] > A.nrows
+    assert _widest_row(C) > SHARED_F64_MAX
+    if shape == "wide":
+        assert st["num_bin_rows"][9] == A.nrows
+    else:
+        assert st["num_bin_rows"][9] > A.nrows
     assert_matches_oracle(C, A, B, True)
 
 
@@ -531,7 +545,7 @@ def test_heavy_symbolic_row_split_over_blocks(dt, sorted_output):
     """A heavy bitmap row (bound 65536) with 600,000 products takes four
     symbolic blocks: each ORs its part of the row's columns into the saved
     bitmap and the last one counts them.  Its output (about 65,000 entries)
-    then spans several numeric rank windows."""
+    then exceeds the numeric large class's shared array."""
     rng = np.random.default_rng(151)
     nb, kb = 20000, 1 << 16
     B = inputs.er_exact(nb, 30, seed=152, ncols=kb)
