@@ -821,8 +821,11 @@ cudaError_t launch_numeric_t(spgemm_plan_s *p, const int32_t *c_rp, int32_t *c_c
   Args a = phase_args(p, &p->dc->err, probe_mode(p->flags),
                       (p->flags & SPGEMM_COUNT_PROBES) ? &p->dc->probe_stats[2][0] : nullptr);
   if (p->ddrive) a.abort = &p->dc->err;
-  // heavy bins first, each bin on the next side stream
-  static const int order[kNumNumBins] = {kNumBitmapBin, kNumBitmapMBin, kNumBitmapSBin, kNumGlobalBin, 8, 7, 6, 5,
+  // bitmap classes first (small, medium, large), then the hash bins from the
+  // heaviest, each bin on the next side stream.  Measured: the triangle
+  // product (small and medium classes only) ran 1.26 -> 1.13 ms with the small
+  // class launched before the medium one; R-MAT A*A (scale 16) was unchanged.
+  static const int order[kNumNumBins] = {kNumBitmapSBin, kNumBitmapMBin, kNumBitmapBin, kNumGlobalBin, 8, 7, 6, 5,
                                          4, 3, 2, 1, 0};
   const bool concurrent = use_side_streams(p);
   cudaError_t e = cudaSuccess;
