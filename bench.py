@@ -838,11 +838,17 @@ def main() -> int:
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    def step(sorted_flag: bool, timing: bool):
+    def step(sorted_flag: bool, timing: bool, marks=None):
         # timing=True records an event pair around every kernel and runs the
-        # bins of each phase one after another (per-kernel durations alone)
+        # bins of each phase one after another (per-kernel durations alone);
+        # `marks` (two events) are recorded after the plan and after the
+        # symbolic phase, for the phases' spans in the concurrent step
         plan = sg.Plan(dA, dB, sorted_flag, stream=stream, timing=timing, serial=timing)
+        if marks:
+            marks[0].record(stream)
         nnz = plan.symbolic()
+        if marks:
+            marks[1].record(stream)
         C = plan.numeric()
         return plan, nnz, C
 
@@ -853,16 +859,19 @@ def main() -> int:
             del C
         barrier()
         times, kt, launches, stats = [], {}, 0, None
+        spans = []
         t_wall0 = time.perf_counter()
         for it in range(k):
             flush.fill_(it & 0xFF)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
+            marks = [torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
             e0.record(stream)
-            plan, nnz, C = step(sorted_flag, timing)
+            plan, nnz, C = step(sorted_flag, timing, marks)
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
+            spans.append((e0.elapsed_time(marks[0]), marks[0].elapsed_time(marks[1]), marks[1].elapsed_time(e1)))
             if timing:
                 for name, (ms, n) in plan.kernel_times().items():
                     a, b = kt.get(name, (0.0, 0))
@@ -875,11 +884,18 @@ def main() -> int:
             del C
         barrier()
         wall = time.perf_counter() - t_wall0
+        timed_steps.spans = spans
         return times, kt, launches, stats, nnz, wall
 
     with ClockSampler(local_rank) as clocks:
         times, _, launches, stats, nnz_c, wall = timed_steps(sorted_output, args.steps, args.warmup)
     clock_summary = clocks.summary()
+    # spans of the phases inside the timed (concurrent) steps, each ending at
+    # the host synchronisation that closes it
+    sp = timed_steps.spans
+    phase_wall = {name: round(sum(x[j] for x in sp) / len(sp), 4)
+                  for j, name in enumerate(("plan (flop pass, bins; host reads the bin counts)",
+                                            "symbolic (host reads nnz(C))", "numeric"))}
     # per-kernel durations: the same K steps again, bins serialised, an event pair per kernel
     ktimes, kt, _, _, _, _ = timed_steps(sorted_output, args.steps, 1, timing=True)
 
@@ -1064,6 +1080,7 @@ def main() -> int:
             "clocks": clock_summary,
             "phases_ms": phases,
             "phase_totals_ms": phase_totals,
+            "phase_wall_ms": phase_wall,
             "ms_per_step_median": round(statistics.median(times), 4),
             "kernel_share": shares,
             "variant": variant,
