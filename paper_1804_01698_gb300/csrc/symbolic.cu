@@ -289,7 +289,10 @@ static cudaError_t sym_block(spgemm_plan_s *p, cudaStream_t st, const Args &a, B
 cudaError_t launch_symbolic(spgemm_plan_s *p) {
   const Args a = phase_args(p, &p->dc->err, probe_mode(p->flags),
                             (p->flags & SPGEMM_COUNT_PROBES) ? &p->dc->probe_stats[0][0] : nullptr);
-  // heavy bins first, each bin on the next side stream
+  // heavy bins first.  The two bitmap bins take side streams 0 and 1, the
+  // other bins streams 2 and 3 in turn, so that no hash bin waits behind a
+  // bitmap launch on its stream.  Measured against one bin per next stream:
+  // the triangle product ran 1.07 -> 1.02 ms, R-MAT A*A (scale 16) the same.
   static const int order[kNumSymBins] = {kSymBitmapBin, kSymBitmapMidBin, kSymGlobalBin, 9, 8, 7, 6, 5, 4, 3, 2, 1, 0};
   const bool concurrent = use_side_streams(p);
   cudaError_t e = cudaSuccess;
@@ -328,7 +331,8 @@ cudaError_t launch_symbolic(spgemm_plan_s *p) {
     const int32_t *rows = p->perm + p->sym_off[b];
     const BinRows br{p->perm, p->d_sym_off, b};
     const BinCfg &c = kSymBins[b];
-    cudaStream_t st = concurrent ? bin_stream(p, launched++) : p->stream;
+    const int si = b == kSymBitmapBin ? 0 : b == kSymBitmapMidBin ? 1 : 2 + (launched++ & 1);
+    cudaStream_t st = concurrent ? bin_stream(p, si) : p->stream;
     switch (b) {
       case 0: e = sym_warp<64>(p, st, a, br, n); break;
       case 1: e = sym_warp<128>(p, st, a, br, n); break;
