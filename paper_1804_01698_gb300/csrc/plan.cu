@@ -417,8 +417,8 @@ __global__ void __launch_bounds__(256)
   const int c = bm_class(nnz_row[i], caps, &w);
   if (w == 0) return;
   const int parts = bm_split_parts(flop[i], nnz_row[i]);
-  const int q = bm_bucket_of(flop[i], parts);
-  const unsigned long long base = caps.off[c][q] + atomicAdd(&dc->bm_cursor[c][q], (unsigned long long)(w * parts));
+  const int bk = bm_bucket_of(flop[i], parts);
+  const unsigned long long base = caps.off[c][bk] + atomicAdd(&dc->bm_cursor[c][bk], (unsigned long long)(w * parts));
   for (int q = 0; q < (int)w; ++q)
     for (int pt = 0; pt < parts; ++pt) items[base + (unsigned long long)q * parts + pt] = make_int4((int)t, q, pt, parts);
 }
