@@ -125,7 +125,7 @@ typedef struct {
     int32_t n_sym_bins;        /* number of symbolic bins */
     int32_t n_num_bins;        /* number of numeric bins */
     int64_t sym_bin_rows[SPGEMM_MAX_BINS]; /* rows per symbolic bin */
-    int64_t num_bin_rows[SPGEMM_MAX_BINS]; /* rows (or row windows) per numeric bin */
+    int64_t num_bin_rows[SPGEMM_MAX_BINS]; /* rows per numeric bin (bitmap bins: work items, a row per part) */
     int32_t sym_bin_table[SPGEMM_MAX_BINS]; /* table slots per bin (0 = bitmap or global table) */
     int32_t num_bin_table[SPGEMM_MAX_BINS];
     int64_t workspace_bytes;   /* device workspace currently held by the plan */

@@ -41,8 +41,8 @@ constexpr int kSymBitmapMidBin = 11; // bitmap rows with bound <= kBitmapMidMax 
 constexpr int kSymGlobalBin = 12;
 constexpr int kNumSymBins = 13;
 // numeric bins 0..8 are hash bins; bitmap rows become work items in three
-// classes by row size: small (3 blocks per SM), medium (2), large (1, rank
-// windows for rows longer than one block holds)
+// classes by row size: small (3 blocks per SM), medium (2), large (1; the
+// ranks of a row beyond one block's shared array go straight into C)
 constexpr int kNumBitmapBin = 9;     // large class
 constexpr int kNumGlobalBin = 10;
 constexpr int kNumBitmapSBin = 11;   // small class

@@ -8,11 +8,12 @@
 //                     symbolic phase: the rank of column j among the row's
 //                     columns is its output position, so values accumulate in
 //                     a dense array indexed by rank and come out sorted.  A
-//                     row with more entries than fit in shared memory is
-//                     split into windows of consecutive ranks, and a row
-//                     with much more flop than output into parts of its
-//                     stored a_ik (one block per window and part); three
-//                     size classes, each with its own launch shape.
+//                     row with more entries than fit in shared memory keeps
+//                     its first ranks there and adds the others straight into
+//                     C, and a row with much more flop than output is split
+//                     into parts of its stored a_ik (one block per part);
+//                     three size classes, each with its own launch shape,
+//                     their work items heaviest first.
 //   k_num_global<T>   heavy rows without bitmaps: hash table in global memory.
 //
 // Tables are sized from the exact row count found by the symbolic phase,
