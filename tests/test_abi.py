@@ -101,6 +101,7 @@ def test_argument_validation_before_any_cuda_call(lib):
     assert lib.spgemm_plan_destroy(None) == 0
     assert lib.spgemm_symbolic(None, None, None) == -1
     assert lib.spgemm_numeric(None, None, None, None) == -1
+    assert lib.spgemm_numeric_rows(None, 0, 1, None, None, None) == -1
 
 
 def test_binding_refuses_to_run_without_the_library(monkeypatch, tmp_path):
